@@ -1,0 +1,645 @@
+/*
+ * sslic_oracle.c -- plain single-threaded CPU oracle for Scalable SLIC
+ * (arXiv 1806.08741).  TEST INFRASTRUCTURE ONLY: never linked into, or
+ * called by, the product library.  See sslic_oracle.h for the layout and the
+ * two arithmetic modes.
+ *
+ * Build: cc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no -ffast-math).
+ * -ffp-contract=off keeps every product and sum a separately rounded IEEE
+ * operation, which is what "FP32 canonical" means below.
+ *
+ * Readings of the paper used here (the paper leaves these open):
+ *  R1  seeding lattice: n_d = ceil(N_d/S_d) seeds per axis at
+ *      o_d + j*S_d with o_d = floor((N_d - 1 - (n_d - 1)*S_d)/2); cluster
+ *      index k is the raster index of (j_0..j_{n-1}), j_0 fastest.
+ *  R2  gradient magnitude^2 = sum_c sum_d (I_c(x+e_d) - I_c(x-e_d))^2,
+ *      central differences in index space, neighbours outside the image
+ *      clamped to the border; the 1/2 factor and the square root are dropped
+ *      (neither changes the ordering).
+ *  R3  perturbation: best = the seed itself, then the 3^n offsets in raster
+ *      order (dim 0 fastest) replace it only on a strictly smaller gradient.
+ *  R4  l and d are reset at the start of every iteration.
+ *  R5  window of centre c along axis d: c - S_d <= x_d < c + S_d, evaluated
+ *      as (x_d - S_d) < c && c <= (x_d + S_d) in the mode's precision.
+ *  R6  D^2 evaluation order (FP32 canonical, one rounding per op, no FMA):
+ *      e_c = I_c - C_c; dc = ((e_0^2 + e_1^2) + ...) ; t_d = w_d*(delta_d^2)
+ *      with delta_d = x_d - c_d and w_d = float(m^2/S_d^2 in double);
+ *      ds = ((t_0 + t_1) + ...); D^2 = dc + ds.
+ *  R7  ties go to the lowest k (centres visited in ascending k, strict <).
+ *  R8  voxels covered by no window keep label -1 and are not accumulated.
+ *  R9  integer images: exact int64 sums, centre = float(double(sum)/double(n));
+ *      float images: double sums; empty clusters keep their previous centre.
+ *  R10 residual = mean over non-empty clusters of sqrt(D^2(C_prev, C_new))
+ *      in double with w_d = m^2/S_d^2; stop after the iteration in which it
+ *      falls below a positive threshold.
+ *  R11 connectivity uses face adjacency (2n neighbours).
+ *  R12 phase 1 seed: p = round-half-up(c_k) clamped; if l(p) == k use p,
+ *      else the raster-first voxel of label k in the box of offsets
+ *      -floor(S_d/2) .. ceil(S_d/2)-1 around p; final iff 4*size > prod S_d.
+ *  R13 flood fills run on the pre-relabel labels; new labels count up from K
+ *      in scan order.
+ *  R14 "last encountered label" = output label of x - e_d for the smallest d
+ *      with x_d > 0 (x is the raster-first voxel of its component); the
+ *      component at the origin gets a new label.
+ *  R15 labels are not compacted; centres are not recomputed afterwards.
+ */
+#include "sslic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_EINVAL (-1)
+#define ORACLE_ENOMEM (-2)
+
+typedef struct {
+    int n;              /* spatial dims actually used */
+    int64_t N[3];       /* sizes, padded with 1 */
+    int64_t stride[3];  /* raster strides */
+    int64_t V;          /* voxel count */
+    int C;              /* channels */
+    int dt;             /* dtype */
+    int S[3];           /* grid, padded with 1 */
+    int64_t ns[3];      /* seeds per axis, padded with 1 */
+    int64_t K;          /* clusters */
+    int fp64;           /* arithmetic mode */
+    float w32[3];       /* fl32(m^2 / S_d^2) */
+    double w64[3];      /* m^2 / S_d^2 */
+} geom;
+
+static int make_geom(const oracle_params* p, geom* g)
+{
+    if (!p) return ORACLE_EINVAL;
+    if (p->ndim < 1 || p->ndim > 3) return ORACLE_EINVAL;
+    if (p->channels < 1) return ORACLE_EINVAL;
+    if (p->dtype != ORACLE_U8 && p->dtype != ORACLE_U16 && p->dtype != ORACLE_F32) return ORACLE_EINVAL;
+    if (p->mode != ORACLE_FP32 && p->mode != ORACLE_FP64) return ORACLE_EINVAL;
+    if (!(p->m > 0.0) || !isfinite(p->m)) return ORACLE_EINVAL;
+    if (p->max_iter < 1) return ORACLE_EINVAL;
+    memset(g, 0, sizeof(*g));
+    g->n = p->ndim;
+    g->C = p->channels;
+    g->dt = p->dtype;
+    g->fp64 = (p->mode == ORACLE_FP64);
+    g->V = 1;
+    g->K = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (d < g->n) {
+            /* positions must be exact in float: N_d <= 2^24 */
+            if (p->size[d] < 1 || p->size[d] > (1 << 24)) return ORACLE_EINVAL;
+            if (p->grid[d] < 1) return ORACLE_EINVAL;
+            g->N[d] = p->size[d];
+            g->S[d] = p->grid[d];
+        } else {
+            g->N[d] = 1;
+            g->S[d] = 1;
+        }
+        g->ns[d] = (g->N[d] + g->S[d] - 1) / g->S[d];
+        g->stride[d] = g->V;
+        g->V *= g->N[d];
+        g->K *= g->ns[d];
+        double s = (double)g->S[d];
+        g->w64[d] = (p->m * p->m) / (s * s);
+        g->w32[d] = (float)g->w64[d];
+    }
+    return ORACLE_OK;
+}
+
+int64_t oracle_num_clusters(const oracle_params* p)
+{
+    geom g;
+    if (make_geom(p, &g) != ORACLE_OK) return -1;
+    return g.K;
+}
+
+/* ---- pixel access ------------------------------------------------------ */
+
+/* channel c of voxel q as a double (exact for every supported dtype) */
+static double pix(const geom* g, const void* image, int64_t q, int c)
+{
+    int64_t i = q * g->C + c;
+    switch (g->dt) {
+    case ORACLE_U8: return (double)((const uint8_t*)image)[i];
+    case ORACLE_U16: return (double)((const uint16_t*)image)[i];
+    default: return (double)((const float*)image)[i];
+    }
+}
+
+static int64_t pix_int(const geom* g, const void* image, int64_t q, int c)
+{
+    int64_t i = q * g->C + c;
+    if (g->dt == ORACLE_U8) return (int64_t)((const uint8_t*)image)[i];
+    return (int64_t)((const uint16_t*)image)[i];
+}
+
+static void coords(const geom* g, int64_t q, int64_t* x)
+{
+    for (int d = 0; d < 3; ++d) x[d] = (q / g->stride[d]) % g->N[d];
+}
+
+static int64_t index_of(const geom* g, const int64_t* x)
+{
+    return x[0] * g->stride[0] + x[1] * g->stride[1] + x[2] * g->stride[2];
+}
+
+/* ---- gradient (R2) ------------------------------------------------------ */
+
+static double gradient(const geom* g, const void* image, int64_t q)
+{
+    int64_t x[3];
+    coords(g, q, x);
+    if (g->dt != ORACLE_F32) {
+        /* integer images: exact in int64 */
+        int64_t acc = 0;
+        for (int c = 0; c < g->C; ++c) {
+            for (int d = 0; d < g->n; ++d) {
+                int64_t hi = x[d] + 1 < g->N[d] ? q + g->stride[d] : q;
+                int64_t lo = x[d] > 0 ? q - g->stride[d] : q;
+                int64_t diff = pix_int(g, image, hi, c) - pix_int(g, image, lo, c);
+                acc += diff * diff;
+            }
+        }
+        return (double)acc;
+    }
+    if (!g->fp64) {
+        /* float images, FP32 canonical: channel outer, axis inner, left to right */
+        float acc = 0.0f;
+        int first = 1;
+        for (int c = 0; c < g->C; ++c) {
+            for (int d = 0; d < g->n; ++d) {
+                int64_t hi = x[d] + 1 < g->N[d] ? q + g->stride[d] : q;
+                int64_t lo = x[d] > 0 ? q - g->stride[d] : q;
+                float diff = (float)pix(g, image, hi, c) - (float)pix(g, image, lo, c);
+                float sq = diff * diff;
+                acc = first ? sq : acc + sq;
+                first = 0;
+            }
+        }
+        return (double)acc;
+    }
+    double acc = 0.0;
+    for (int c = 0; c < g->C; ++c) {
+        for (int d = 0; d < g->n; ++d) {
+            int64_t hi = x[d] + 1 < g->N[d] ? q + g->stride[d] : q;
+            int64_t lo = x[d] > 0 ? q - g->stride[d] : q;
+            double diff = pix(g, image, hi, c) - pix(g, image, lo, c);
+            acc += diff * diff;
+        }
+    }
+    return acc;
+}
+
+double oracle_gradient(const oracle_params* p, const void* image, int64_t q)
+{
+    geom g;
+    if (make_geom(p, &g) != ORACLE_OK || q < 0) return -1.0;
+    if (q >= g.V) return -1.0;
+    return gradient(&g, image, q);
+}
+
+/* ---- seeding and perturbation (R1, R3) ---------------------------------- */
+
+static void store_centre(const geom* g, const void* image, int64_t q, double* row)
+{
+    int64_t x[3];
+    coords(g, q, x);
+    for (int c = 0; c < g->C; ++c) {
+        double v = pix(g, image, q, c);
+        row[c] = g->fp64 ? v : (double)(float)v;
+    }
+    for (int d = 0; d < g->n; ++d) row[g->C + d] = (double)x[d];
+}
+
+static int seed(const geom* g, int perturb, const void* image, double* centres)
+{
+    const int width = g->C + g->n;
+    for (int64_t k = 0; k < g->K; ++k) {
+        int64_t x[3];
+        int64_t rem = k;
+        for (int d = 0; d < 3; ++d) {
+            int64_t j = rem % g->ns[d];
+            rem /= g->ns[d];
+            int64_t o = (g->N[d] - 1 - (g->ns[d] - 1) * g->S[d]) / 2;
+            x[d] = o + j * g->S[d];
+        }
+        int64_t best = index_of(g, x);
+        if (perturb) {
+            double best_g = gradient(g, image, best);
+            /* 3^n offsets in raster order, dimension 0 fastest */
+            int lo2 = g->n >= 3 ? -1 : 0, hi2 = g->n >= 3 ? 1 : 0;
+            int lo1 = g->n >= 2 ? -1 : 0, hi1 = g->n >= 2 ? 1 : 0;
+            for (int o2 = lo2; o2 <= hi2; ++o2)
+                for (int o1 = lo1; o1 <= hi1; ++o1)
+                    for (int o0 = -1; o0 <= 1; ++o0) {
+                        int64_t y[3] = {x[0] + o0, x[1] + o1, x[2] + o2};
+                        int inside = 1;
+                        for (int d = 0; d < 3; ++d)
+                            if (y[d] < 0 || y[d] >= g->N[d]) inside = 0;
+                        if (!inside) continue;
+                        int64_t q = index_of(g, y);
+                        double gq = gradient(g, image, q);
+                        if (gq < best_g) {
+                            best_g = gq;
+                            best = q;
+                        }
+                    }
+        }
+        store_centre(g, image, best, centres + k * width);
+    }
+    return ORACLE_OK;
+}
+
+int oracle_seed(const oracle_params* p, const void* image, double* centres)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!image || !centres) return ORACLE_EINVAL;
+    return seed(&g, p->perturb, image, centres);
+}
+
+/* ---- distance (R6) ------------------------------------------------------ */
+
+static float dist32(const geom* g, const float* f, const int64_t* x, const double* ctr)
+{
+    float dc = 0.0f;
+    for (int c = 0; c < g->C; ++c) {
+        float e = f[c] - (float)ctr[c];
+        float sq = e * e;
+        dc = (c == 0) ? sq : dc + sq;
+    }
+    float ds = 0.0f;
+    for (int d = 0; d < g->n; ++d) {
+        float delta = (float)x[d] - (float)ctr[g->C + d];
+        float dd = delta * delta;
+        float t = g->w32[d] * dd;
+        ds = (d == 0) ? t : ds + t;
+    }
+    return dc + ds;
+}
+
+static double dist64(const geom* g, const double* f, const int64_t* x, const double* ctr)
+{
+    double dc = 0.0;
+    for (int c = 0; c < g->C; ++c) {
+        double e = f[c] - ctr[c];
+        dc = (c == 0) ? e * e : dc + e * e;
+    }
+    double ds = 0.0;
+    for (int d = 0; d < g->n; ++d) {
+        double delta = (double)x[d] - ctr[g->C + d];
+        double t = g->w64[d] * (delta * delta);
+        ds = (d == 0) ? t : ds + t;
+    }
+    return dc + ds;
+}
+
+double oracle_distance(const oracle_params* p, const double* feature,
+                       const int64_t* pos, const double* centre)
+{
+    geom g;
+    if (make_geom(p, &g) != ORACLE_OK) return -1.0;
+    int64_t x[3] = {0, 0, 0};
+    for (int d = 0; d < g.n; ++d) x[d] = pos[d];
+    if (g.fp64) return dist64(&g, feature, x, centre);
+    float f[4096];
+    if (g.C > 4096) return -1.0;
+    for (int c = 0; c < g.C; ++c) f[c] = (float)feature[c];
+    return (double)dist32(&g, f, x, centre);
+}
+
+/* ---- assignment (Sec. 2.2 / 3.1 step 2; R4, R5, R7, R8) ------------------ */
+
+/* window test along one axis (R5) */
+static int in_window(const geom* g, int d, int64_t xd, double c)
+{
+    if (g->fp64) return (double)(xd - g->S[d]) < c && c <= (double)(xd + g->S[d]);
+    float cf = (float)c;
+    return (float)(xd - g->S[d]) < cf && cf <= (float)(xd + g->S[d]);
+}
+
+static int assign(const geom* g, const void* image, const double* centres, int64_t K,
+                  int32_t* labels)
+{
+    const int width = g->C + g->n;
+    float* d32 = NULL;
+    double* d64 = NULL;
+    if (g->fp64) d64 = (double*)malloc((size_t)g->V * sizeof(double));
+    else d32 = (float*)malloc((size_t)g->V * sizeof(float));
+    float* f32 = (float*)malloc((size_t)g->C * sizeof(float));
+    double* f64 = (double*)malloc((size_t)g->C * sizeof(double));
+    int64_t* xs[3] = {NULL, NULL, NULL};
+    int64_t len[3];
+    int ok = (d32 || d64) && f32 && f64;
+    for (int d = 0; d < 3 && ok; ++d) {
+        xs[d] = (int64_t*)malloc((size_t)(2 * g->S[d] + 3) * sizeof(int64_t));
+        if (!xs[d]) ok = 0;
+    }
+    if (!ok) {
+        free(d32); free(d64); free(f32); free(f64);
+        for (int d = 0; d < 3; ++d) free(xs[d]);
+        return ORACLE_ENOMEM;
+    }
+    /* R4: reset l = undefined (-1), d = +inf */
+    for (int64_t q = 0; q < g->V; ++q) {
+        labels[q] = -1;
+        if (g->fp64) d64[q] = INFINITY;
+        else d32[q] = INFINITY;
+    }
+    for (int64_t k = 0; k < K; ++k) {
+        const double* ctr = centres + k * width;
+        /* the window of centre k, axis by axis (R5) */
+        for (int d = 0; d < 3; ++d) {
+            len[d] = 0;
+            if (d >= g->n) {
+                xs[d][len[d]++] = 0;
+                continue;
+            }
+            double c = ctr[g->C + d];
+            int64_t fl = (int64_t)floor(c);
+            for (int64_t xd = fl - g->S[d] - 1; xd <= fl + g->S[d] + 1; ++xd) {
+                if (xd < 0 || xd >= g->N[d]) continue;
+                if (in_window(g, d, xd, c)) xs[d][len[d]++] = xd;
+            }
+        }
+        for (int64_t i2 = 0; i2 < len[2]; ++i2)
+            for (int64_t i1 = 0; i1 < len[1]; ++i1)
+                for (int64_t i0 = 0; i0 < len[0]; ++i0) {
+                    int64_t x[3] = {xs[0][i0], xs[1][i1], xs[2][i2]};
+                    int64_t q = index_of(g, x);
+                    if (g->fp64) {
+                        for (int c = 0; c < g->C; ++c) f64[c] = pix(g, image, q, c);
+                        double D = dist64(g, f64, x, ctr);
+                        if (D < d64[q]) { d64[q] = D; labels[q] = (int32_t)k; }
+                    } else {
+                        for (int c = 0; c < g->C; ++c) f32[c] = (float)pix(g, image, q, c);
+                        float D = dist32(g, f32, x, ctr);
+                        if (D < d32[q]) { d32[q] = D; labels[q] = (int32_t)k; }
+                    }
+                }
+    }
+    free(d32); free(d64); free(f32); free(f64);
+    for (int d = 0; d < 3; ++d) free(xs[d]);
+    return ORACLE_OK;
+}
+
+int oracle_assign(const oracle_params* p, const void* image, const double* centres,
+                  int64_t K, int32_t* labels)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!image || !centres || !labels || K < 0 || K > 0x7fffffffLL) return ORACLE_EINVAL;
+    return assign(&g, image, centres, K, labels);
+}
+
+/* ---- update (Sec. 2.2 "Update clusters", Sec. 3.1 map-reduce; R9, R10) --- */
+
+static int update(const geom* g, const void* image, const int32_t* labels, int64_t K,
+                  double* centres, int64_t* counts_out, double* residual)
+{
+    const int width = g->C + g->n;
+    int64_t* cnt = (int64_t*)calloc((size_t)K, sizeof(int64_t));
+    int64_t* isum = (int64_t*)calloc((size_t)K * width, sizeof(int64_t));
+    double* fsum = (double*)calloc((size_t)K * g->C, sizeof(double));
+    if (!cnt || !isum || !fsum) {
+        free(cnt); free(isum); free(fsum);
+        return ORACLE_ENOMEM;
+    }
+    /* map: accumulate [I(x), x] per label */
+    for (int64_t q = 0; q < g->V; ++q) {
+        int32_t k = labels[q];
+        if (k < 0) continue; /* R8 */
+        if (k >= K) { free(cnt); free(isum); free(fsum); return ORACLE_EINVAL; }
+        int64_t x[3];
+        coords(g, q, x);
+        cnt[k] += 1;
+        for (int c = 0; c < g->C; ++c) {
+            if (g->dt == ORACLE_F32) fsum[k * g->C + c] += pix(g, image, q, c);
+            else isum[k * width + c] += pix_int(g, image, q, c);
+        }
+        for (int d = 0; d < g->n; ++d) isum[k * width + g->C + d] += x[d];
+    }
+    /* reduce: divide, keep empty clusters unchanged */
+    double rsum = 0.0;
+    int64_t nonempty = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        double* row = centres + k * width;
+        if (counts_out) counts_out[k] = cnt[k];
+        if (cnt[k] == 0) continue;
+        double n = (double)cnt[k];
+        double D2 = 0.0;
+        for (int j = 0; j < width; ++j) {
+            double s = (j < g->C && g->dt == ORACLE_F32) ? fsum[k * g->C + j]
+                                                          : (double)isum[k * width + j];
+            double mean = s / n;
+            double v = g->fp64 ? mean : (double)(float)mean;
+            double diff = v - row[j];
+            D2 += (j < g->C) ? diff * diff : g->w64[j - g->C] * (diff * diff);
+            row[j] = v;
+        }
+        rsum += sqrt(D2);
+        nonempty += 1;
+    }
+    if (residual) *residual = nonempty ? rsum / (double)nonempty : 0.0;
+    free(cnt); free(isum); free(fsum);
+    return ORACLE_OK;
+}
+
+int oracle_update(const oracle_params* p, const void* image, const int32_t* labels,
+                  int64_t K, double* centres, int64_t* counts, double* residual)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!image || !labels || !centres || K < 0) return ORACLE_EINVAL;
+    return update(&g, image, labels, K, centres, counts, residual);
+}
+
+/* ---- connectivity enforcement (Sec. 3.1 stage 3; R11-R15) --------------- */
+
+/* Flood fill of the face-connected component of label lab containing s, on
+ * the pre-relabel image.  Visited voxels are marked in vis; the component's
+ * voxels are left in queue[0..return). */
+static int64_t flood(const geom* g, const int32_t* lab_in, int64_t s, int32_t lab,
+                     uint8_t* vis, int64_t* queue)
+{
+    int64_t head = 0, tail = 0;
+    queue[tail++] = s;
+    vis[s] = 1;
+    while (head < tail) {
+        int64_t q = queue[head++];
+        int64_t x[3];
+        coords(g, q, x);
+        for (int d = 0; d < g->n; ++d) {
+            if (x[d] > 0) {
+                int64_t r = q - g->stride[d];
+                if (!vis[r] && lab_in[r] == lab) { vis[r] = 1; queue[tail++] = r; }
+            }
+            if (x[d] + 1 < g->N[d]) {
+                int64_t r = q + g->stride[d];
+                if (!vis[r] && lab_in[r] == lab) { vis[r] = 1; queue[tail++] = r; }
+            }
+        }
+    }
+    return tail;
+}
+
+static int connectivity(const geom* g, const double* centres, int64_t K,
+                        const int32_t* lab_in, int32_t* out, int64_t* num_labels)
+{
+    const int width = g->C + g->n;
+    int64_t sprod = 1;
+    for (int d = 0; d < g->n; ++d) sprod *= g->S[d];
+    uint8_t* fin = (uint8_t*)calloc((size_t)g->V, 1);   /* marker image m */
+    uint8_t* vis = (uint8_t*)calloc((size_t)g->V, 1);
+    int64_t* queue = (int64_t*)malloc((size_t)g->V * sizeof(int64_t));
+    if (!fin || !vis || !queue) {
+        free(fin); free(vis); free(queue);
+        return ORACLE_ENOMEM;
+    }
+    memcpy(out, lab_in, (size_t)g->V * sizeof(int32_t));
+
+    /* phase 1: one component per centre, final if large enough (R12) */
+    for (int64_t k = 0; k < K; ++k) {
+        const double* ctr = centres + k * width;
+        int64_t p[3] = {0, 0, 0};
+        for (int d = 0; d < g->n; ++d) {
+            int64_t v = (int64_t)floor(ctr[g->C + d] + 0.5);
+            if (v < 0) v = 0;
+            if (v > g->N[d] - 1) v = g->N[d] - 1;
+            p[d] = v;
+        }
+        int64_t s = -1;
+        int64_t pq = index_of(g, p);
+        if (lab_in[pq] == (int32_t)k) {
+            s = pq;
+        } else {
+            int64_t lo[3], hi[3];
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = p[d] - g->S[d] / 2;
+                hi[d] = p[d] + (g->S[d] + 1) / 2 - 1;
+                if (lo[d] < 0) lo[d] = 0;
+                if (hi[d] > g->N[d] - 1) hi[d] = g->N[d] - 1;
+            }
+            for (int64_t z = lo[2]; z <= hi[2] && s < 0; ++z)
+                for (int64_t y = lo[1]; y <= hi[1] && s < 0; ++y)
+                    for (int64_t x = lo[0]; x <= hi[0] && s < 0; ++x) {
+                        int64_t xx[3] = {x, y, z};
+                        int64_t q = index_of(g, xx);
+                        if (lab_in[q] == (int32_t)k) s = q;
+                    }
+        }
+        if (s < 0) continue;
+        int64_t size = flood(g, lab_in, s, (int32_t)k, vis, queue);
+        int final = 4 * size > sprod;
+        for (int64_t i = 0; i < size; ++i) {
+            vis[queue[i]] = 0;
+            if (final) fin[queue[i]] = 1;
+        }
+    }
+
+    /* phase 2: raster scan over non-final voxels (R13, R14) */
+    int64_t next = K;
+    for (int64_t q = 0; q < g->V; ++q) {
+        if (fin[q]) continue;
+        int64_t size = flood(g, lab_in, q, lab_in[q], vis, queue);
+        int32_t newlab;
+        if (4 * size > sprod || q == 0) {
+            newlab = (int32_t)next++;
+        } else {
+            int64_t x[3];
+            coords(g, q, x);
+            int d = 0;
+            while (x[d] == 0) ++d;
+            newlab = out[q - g->stride[d]];
+        }
+        for (int64_t i = 0; i < size; ++i) {
+            out[queue[i]] = newlab;
+            fin[queue[i]] = 1;
+            vis[queue[i]] = 0;
+        }
+    }
+    if (num_labels) *num_labels = next;
+    free(fin); free(vis); free(queue);
+    return ORACLE_OK;
+}
+
+int oracle_connectivity(const oracle_params* p, const double* centres, int64_t K,
+                        const int32_t* labels_in, int32_t* labels_out, int64_t* num_labels)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!centres || !labels_in || !labels_out || K < 0 || K > 0x7fffffffLL) return ORACLE_EINVAL;
+    return connectivity(&g, centres, K, labels_in, labels_out, num_labels);
+}
+
+/* ---- whole method -------------------------------------------------------- */
+
+static int run(const geom* g, const oracle_params* p, const void* image, double* ctr,
+               int32_t* labels, double* centres_out, int32_t* iters_done,
+               double* residual, int64_t* num_labels)
+{
+    const int width = g->C + g->n;
+    int32_t it = 0;
+    double res = 0.0;
+    int rc = ORACLE_OK;
+    for (it = 0; it < p->max_iter; ++it) {
+        rc = assign(g, image, ctr, g->K, labels);
+        if (rc != ORACLE_OK) return rc;
+        rc = update(g, image, labels, g->K, ctr, NULL, &res);
+        if (rc != ORACLE_OK) return rc;
+        if (p->conv_threshold > 0.0 && res < p->conv_threshold) { ++it; break; }
+    }
+    if (iters_done) *iters_done = it;
+    if (residual) *residual = res;
+    if (centres_out) memcpy(centres_out, ctr, (size_t)(g->K * width) * sizeof(double));
+    if (p->enforce_connectivity) {
+        int32_t* tmp = (int32_t*)malloc((size_t)g->V * sizeof(int32_t));
+        if (!tmp) return ORACLE_ENOMEM;
+        memcpy(tmp, labels, (size_t)g->V * sizeof(int32_t));
+        rc = connectivity(g, ctr, g->K, tmp, labels, num_labels);
+        free(tmp);
+    } else if (num_labels) {
+        *num_labels = g->K;
+    }
+    return rc;
+}
+
+int oracle_slic(const oracle_params* p, const void* image, int32_t* labels,
+                double* centres_out, int32_t* iters_done, double* residual,
+                int64_t* num_labels)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!image || !labels) return ORACLE_EINVAL;
+    double* ctr = (double*)malloc((size_t)(g.K * (g.C + g.n)) * sizeof(double));
+    if (!ctr) return ORACLE_ENOMEM;
+    rc = seed(&g, p->perturb, image, ctr);
+    if (rc == ORACLE_OK)
+        rc = run(&g, p, image, ctr, labels, centres_out, iters_done, residual, num_labels);
+    free(ctr);
+    return rc;
+}
+
+int oracle_slic_from(const oracle_params* p, const void* image, const double* init_centres,
+                     int32_t* labels, double* centres_out, int32_t* iters_done,
+                     double* residual, int64_t* num_labels)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!image || !labels || !init_centres) return ORACLE_EINVAL;
+    size_t n = (size_t)(g.K * (g.C + g.n));
+    double* ctr = (double*)malloc(n * sizeof(double));
+    if (!ctr) return ORACLE_ENOMEM;
+    memcpy(ctr, init_centres, n * sizeof(double));
+    if (!g.fp64)
+        for (size_t i = 0; i < n; ++i) ctr[i] = (double)(float)ctr[i];
+    rc = run(&g, p, image, ctr, labels, centres_out, iters_done, residual, num_labels);
+    free(ctr);
+    return rc;
+}

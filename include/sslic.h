@@ -1,0 +1,153 @@
+/*
+ * sslic.h -- C ABI of the GB300 (sm_103a) Scalable SLIC library.
+ *
+ * Method: Lowekamp, Chen, Yaniv, Bernardini, "Scalable Simple Linear
+ * Iterative Clustering (SSLIC) Using a Generic and Parallel Approach",
+ * arXiv 1806.08741.  Section references below are to that paper.
+ *
+ * Conventions
+ *  - Image layout: C-contiguous [N_{n-1}]...[N_1][N_0][C], dimension 0
+ *    (x) fastest, channels interleaved (Sec. 3.3 keeps a pixel's components
+ *    together).  Element type uint8, uint16 or float32.
+ *  - Labels: int32, one per voxel, same raster order as the image.
+ *  - Centres: float32 table K x (C + n): the C feature components followed
+ *    by the n position components x_0..x_{n-1} (Sec. 3.3 stores all
+ *    centres in one flat array of C + n values each).
+ *  - K = prod_d ceil(N_d / S_d) clusters, seeded on a centred lattice.
+ *  - Ownership: the caller owns every image / label / centre buffer and the
+ *    stream; a context owns its device workspace (bins, sums, connectivity
+ *    scratch), allocated by sslic_create and released by sslic_destroy.
+ *  - Every call returns an int status: SSLIC_OK (0) or a negative code; no
+ *    exception ever crosses the ABI.  sslic_strerror() names a code and
+ *    sslic_last_error() gives detail for the last failure on a context.
+ *  - Calls on one context must not overlap (the context's workspace is
+ *    shared); calls on different contexts are independent.
+ *  - Device-pointer entry points are stream ordered.  They return once the
+ *    work is enqueued, except where noted (a positive convergence
+ *    threshold and connectivity enforcement each need one host read-back,
+ *    and `out` results are filled after a stream synchronisation).
+ */
+#ifndef SSLIC_H
+#define SSLIC_H
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SSLIC_API __attribute__((visibility("default")))
+#else
+#define SSLIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SSLIC_OK 0
+#define SSLIC_EINVAL (-1)   /* bad shape, grid, weight, dtype, channel count or pointer */
+#define SSLIC_ENOMEM (-2)   /* a device or pinned-host allocation failed */
+#define SSLIC_ECUDA (-3)    /* a CUDA launch or runtime call failed */
+#define SSLIC_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define SSLIC_EBUSY (-5)    /* the context is in use by another call */
+#define SSLIC_EUNSUPPORTED (-6) /* valid request this build does not implement */
+
+typedef enum { SSLIC_U8 = 0, SSLIC_U16 = 1, SSLIC_F32 = 2 } sslic_dtype;
+
+/* The paper's filter parameters (Sec. 3.2): grid size per axis, spatial
+ * weight m, iteration cap, monitored residual, connectivity on/off, plus
+ * seed perturbation on/off (Sec. 3.1 step 1). */
+typedef struct {
+    int32_t ndim;           /* n: 1, 2 or 3 */
+    int64_t size[4];        /* N_d (d = 0 fastest); entries >= ndim ignored; 1 <= N_d <= 2^24 */
+    int32_t channels;       /* C: 1 .. 256 */
+    int32_t dtype;          /* sslic_dtype */
+    int32_t grid[4];        /* S_d >= 1 in voxels, per axis (anisotropic grid, Sec. 3.2/3.3) */
+    float   m;              /* spatial weight m > 0 (Sec. 2.1; 10 is the paper's default) */
+    int32_t max_iter;       /* iteration cap >= 1 (Sec. 3.2: 10 for 2-D, 5 for n >= 3) */
+    double  conv_threshold; /* stop once the centre residual drops below this; <= 0 disables (Sec. 3.1) */
+    int32_t perturb;        /* 1: move seeds to the lowest gradient in the 3^n neighbourhood (Sec. 3.1) */
+    int32_t enforce_connectivity; /* 1: run the connectivity enforcement of Sec. 3.1 stage 3 */
+    int32_t precision;      /* 0: exact FP32 distances (only value accepted by this build) */
+} sslic_params;
+
+typedef struct {
+    int64_t num_clusters;   /* K */
+    int64_t num_labels;     /* K + labels created by connectivity enforcement */
+    int32_t iterations;     /* assign/update iterations performed */
+    double  residual;       /* centre residual of the last iteration */
+} sslic_result;
+
+typedef struct sslic_ctx sslic_ctx;
+
+/* Fill *p with the paper's defaults for an n-D image (grid 16, m 10,
+ * 10 iterations for n = 2 and 5 for n >= 3, perturbation on, connectivity on). */
+SSLIC_API int sslic_default_params(int32_t ndim, sslic_params* p);
+
+/* Validate p and allocate the device workspace on the current CUDA device.
+ * Errors: SSLIC_EINVAL, SSLIC_ENOMEM, SSLIC_ECUDA.  *out is NULL on error. */
+SSLIC_API int sslic_create(const sslic_params* p, sslic_ctx** out);
+
+/* K for the context's parameters. */
+SSLIC_API int sslic_num_clusters(const sslic_ctx* c, int64_t* K);
+
+/* The whole method (Sec. 3.1): seeding (+ perturbation), up to max_iter
+ * assign/update iterations, optional connectivity enforcement.
+ *   image_dev   device, read only, layout above
+ *   labels_dev  device, V int32, written (-1 marks voxels no window reaches,
+ *               possible only without connectivity enforcement)
+ *   centres_dev device, K x (C+n) float32, written; may be NULL
+ *   stream      cudaStream_t, or NULL for the legacy default stream
+ *   out         host, may be NULL; filled after a stream synchronisation */
+SSLIC_API int sslic_run(sslic_ctx* c, const void* image_dev, int32_t* labels_dev, float* centres_dev,
+              void* stream, sslic_result* out);
+
+/* As sslic_run, but starting from caller-given centres instead of seeding
+ * (checkpoint / resume: the state after t iterations is the centre table).
+ * init_centres_dev: device, K x (C+n) float32, read only. */
+SSLIC_API int sslic_run_from(sslic_ctx* c, const void* image_dev, const float* init_centres_dev,
+                   int32_t* labels_dev, float* centres_dev, void* stream, sslic_result* out);
+
+/* As sslic_run with HOST buffers: the image is copied to the device, the
+ * method runs, labels (and centres if non-NULL) are copied back, and the
+ * call returns after the stream is synchronised.  Page-locked buffers give
+ * the full copy bandwidth; pageable ones work but copy synchronously.  The
+ * context allocates its device image/label buffers on first use. */
+SSLIC_API int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host,
+                   float* centres_host, void* stream, sslic_result* out);
+
+/* Step entry points (the rows of the method, for parity tests and callers
+ * that drive the loop themselves).  All device pointers, stream ordered. */
+
+/* Seeding on the lattice plus optional perturbation (Sec. 2.2 / 3.1 step 1).
+ * centres_dev: K x (C+n) float32, written. */
+SSLIC_API int sslic_seed(sslic_ctx* c, const void* image_dev, float* centres_dev, void* stream);
+
+/* One iteration: assignment of every voxel to the argmin of D^2 over the
+ * centres whose 2S window covers it, ties to the lowest index (Sec. 2.1,
+ * 2.2, 3.1 step 2), then the centre update as the mean of [I(x), x] over
+ * each label (Sec. 3.1 map-reduce).  centres_in and centres_out are
+ * K x (C+n) float32 and may alias; empty clusters keep their centre.
+ * residual_host (may be NULL): if non-NULL the call synchronises the stream
+ * and stores the centre residual there. */
+SSLIC_API int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* centres_in_dev,
+                  int32_t* labels_dev, float* centres_out_dev, void* stream,
+                  double* residual_host);
+
+/* Connectivity enforcement (Sec. 3.1 stage 3) of a label image produced
+ * with the given centres.  labels_in_dev and labels_out_dev may alias.
+ * num_labels_host (may be NULL) receives K + the number of new labels.
+ * Synchronises the stream once (the component count sizes the scratch). */
+SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* labels_in_dev,
+                       int32_t* labels_out_dev, void* stream, int64_t* num_labels_host);
+
+/* Release the context (NULL is a no-op).  Synchronises the device first. */
+SSLIC_API void sslic_destroy(sslic_ctx* c);
+
+/* Static text for a status code. */
+SSLIC_API const char* sslic_strerror(int code);
+
+/* Detail for the most recent failure on this context ("" if none). */
+SSLIC_API const char* sslic_last_error(const sslic_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

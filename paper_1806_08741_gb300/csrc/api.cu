@@ -1,0 +1,413 @@
+// api.cu -- the C ABI of include/sslic.h: parameter validation, workspace
+// management and the orchestration of the kernels on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace sslic {
+
+int set_error(sslic_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_check(sslic_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return SSLIC_OK;
+    return set_error(c, e == cudaErrorMemoryAllocation ? SSLIC_ENOMEM : SSLIC_ECUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+template <typename P>
+static int dalloc(sslic_ctx* c, P** p, size_t count, const char* what)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(P));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(c, SSLIC_ENOMEM, "cudaMalloc %s (%zu bytes): %s", what, count * sizeof(P),
+                         cudaGetErrorString(e));
+    }
+    return SSLIC_OK;
+}
+
+template <typename P>
+static void dfree(P*& p)
+{
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+static int validate(const sslic_params* p, Geom* g)
+{
+    if (!p) return SSLIC_EINVAL;
+    if (p->ndim < 1 || p->ndim > 3) return SSLIC_EINVAL;
+    if (p->channels < 1 || p->channels > kMaxChannels) return SSLIC_EINVAL;
+    if (p->dtype != SSLIC_U8 && p->dtype != SSLIC_U16 && p->dtype != SSLIC_F32) return SSLIC_EINVAL;
+    if (!(p->m > 0.0f) || !std::isfinite(p->m)) return SSLIC_EINVAL;
+    if (p->max_iter < 1) return SSLIC_EINVAL;
+    if (p->perturb != 0 && p->perturb != 1) return SSLIC_EINVAL;
+    if (p->enforce_connectivity != 0 && p->enforce_connectivity != 1) return SSLIC_EINVAL;
+    if (p->precision != 0) return p->precision == 1 ? SSLIC_EUNSUPPORTED : SSLIC_EINVAL;
+    Geom& G = *g;
+    memset(&G, 0, sizeof(G));
+    G.n = p->ndim;
+    G.C = p->channels;
+    G.dtype = p->dtype;
+    G.CW = G.C + 3;
+    G.AW = G.C + 4;
+    G.V = 1;
+    G.K = 1;
+    G.sprod = 1;
+    const double m = (double)p->m;
+    for (int d = 0; d < 3; ++d) {
+        if (d < G.n) {
+            if (p->size[d] < 1 || p->size[d] > (1 << 24)) return SSLIC_EINVAL;
+            if (p->grid[d] < 1 || p->grid[d] > (1 << 24)) return SSLIC_EINVAL;
+            G.N[d] = p->size[d];
+            G.S[d] = p->grid[d];
+            G.sprod *= G.S[d];
+        } else {
+            G.N[d] = 1;
+            G.S[d] = 1;
+        }
+        G.nb[d] = (G.N[d] + G.S[d] - 1) / G.S[d];
+        G.off[d] = (G.N[d] - 1 - (G.nb[d] - 1) * G.S[d]) / 2;
+        G.V *= G.N[d];
+        G.K *= G.nb[d];
+        const double s = (double)G.S[d];
+        G.w64[d] = (m * m) / (s * s);
+        G.w[d] = (float)G.w64[d];
+    }
+    if (G.K >= (1LL << 30)) return SSLIC_EUNSUPPORTED;  // labels are int32, with room for new ones
+    return SSLIC_OK;
+}
+
+int ensure_ccl_capacity(sslic_ctx* c, int64_t m)
+{
+    Workspace& w = c->ws;
+    const Geom& g = c->g;
+    int rc;
+    if (!w.lid) {
+        if ((rc = dalloc(c, &w.lid, (size_t)g.V, "component ids"))) return rc;
+        w.n_ccl_tiles = ccl_num_tiles(g);
+        if ((rc = dalloc(c, &w.tile_base, (size_t)w.n_ccl_tiles, "tile bases"))) return rc;
+        if ((rc = dalloc(c, &w.counters, 4, "counters"))) return rc;
+    }
+    if (m <= w.m_cap) return SSLIC_OK;
+    dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
+    dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
+    dfree(w.new_key); dfree(w.new_val);
+    w.m_cap = 0;
+    const size_t n = (size_t)m;
+    if ((rc = dalloc(c, &w.comp_label, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.comp_size, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.comp_first, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.gparent, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.root_size, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.root_first, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.fin, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.out_label, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.link, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.new_key, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.new_val, n, "components"))) return rc;
+    w.m_cap = m;
+    return SSLIC_OK;
+}
+
+static void free_all(sslic_ctx* c)
+{
+    Workspace& w = c->ws;
+    dfree(w.ctr); dfree(w.acc); dfree(w.facc); dfree(w.resid_k); dfree(w.nonempty_k);
+    dfree(w.resid_part); dfree(w.resid_cnt_part); dfree(w.resid_out);
+    dfree(w.bin_count); dfree(w.bin_start); dfree(w.bin_cursor); dfree(w.bin_items); dfree(w.bin_of);
+    dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count);
+    dfree(w.lid); dfree(w.tile_base); dfree(w.counters);
+    dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
+    dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
+    dfree(w.new_key); dfree(w.new_val); dfree(w.sort_key); dfree(w.sort_val);
+    dfree(w.img_dev); dfree(w.lab_dev); dfree(w.cen_dev);
+}
+
+static int alloc_core(sslic_ctx* c)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    int rc;
+    const size_t K = (size_t)g.K;
+    if ((rc = dalloc(c, &w.ctr, K * g.CW, "centres"))) return rc;
+    if ((rc = dalloc(c, &w.acc, K * g.AW, "sums"))) return rc;
+    if (g.dtype == SSLIC_F32 && (rc = dalloc(c, &w.facc, K * g.C, "float sums"))) return rc;
+    if ((rc = dalloc(c, &w.resid_k, K, "residual"))) return rc;
+    if ((rc = dalloc(c, &w.nonempty_k, K, "residual"))) return rc;
+    if ((rc = dalloc(c, &w.resid_part, 256, "residual"))) return rc;
+    if ((rc = dalloc(c, &w.resid_cnt_part, 256, "residual"))) return rc;
+    if ((rc = dalloc(c, &w.resid_out, 1, "residual"))) return rc;
+    if ((rc = dalloc(c, &w.bin_count, K + 1, "bins"))) return rc;
+    if ((rc = dalloc(c, &w.bin_start, K + 1, "bins"))) return rc;
+    if ((rc = dalloc(c, &w.bin_cursor, K, "bins"))) return rc;
+    if ((rc = dalloc(c, &w.bin_items, K, "bins"))) return rc;
+    if ((rc = dalloc(c, &w.bin_of, K, "bins"))) return rc;
+    w.scan_tmp_len = scan_tmp_needed((int64_t)K + 1);
+    if ((rc = dalloc(c, &w.scan_tmp, w.scan_tmp_len, "scan"))) return rc;
+    w.n_assign_tiles = assign_num_tiles(g);
+    if ((rc = dalloc(c, &w.ovf_tiles, (size_t)w.n_assign_tiles, "tiles"))) return rc;
+    if ((rc = dalloc(c, &w.ovf_count, 1, "tiles"))) return rc;
+    if ((rc = cuda_check(c, cudaMemset(w.acc, 0, K * g.AW * sizeof(unsigned long long)), "memset sums"))) return rc;
+    if (w.facc && (rc = cuda_check(c, cudaMemset(w.facc, 0, K * g.C * sizeof(double)), "memset sums"))) return rc;
+    if ((rc = cuda_check(c, cudaMemset(w.resid_out, 0, sizeof(double)), "memset"))) return rc;
+    if (c->p.enforce_connectivity) {
+        // components: about a dozen local pieces per cluster; grown on demand
+        if ((rc = ensure_ccl_capacity(c, 32 * (int64_t)K + g.V / 1024 + 4096))) return rc;
+    }
+    return SSLIC_OK;
+}
+
+struct Busy {
+    sslic_ctx* c;
+    bool ok;
+    explicit Busy(sslic_ctx* c_) : c(c_) { ok = __sync_bool_compare_and_swap(&c->busy, 0, 1); }
+    ~Busy() { if (ok) __sync_lock_release(&c->busy); }
+};
+
+static int read_residual(sslic_ctx* c, cudaStream_t st, double* r)
+{
+    int rc = cuda_check(c, cudaMemcpyAsync(r, c->ws.resid_out, sizeof(double), cudaMemcpyDeviceToHost, st),
+                        "read residual");
+    if (rc) return rc;
+    return cuda_check(c, cudaStreamSynchronize(st), "sync");
+}
+
+// the loop of Sec. 3.1 from the centres already in the workspace
+static int run_loop(sslic_ctx* c, const void* image, int32_t* labels, float* centres, cudaStream_t st,
+                    sslic_result* out)
+{
+    int rc;
+    int it = 0;
+    double res = 0.0;
+    for (it = 0; it < c->p.max_iter; ++it) {
+        if ((rc = build_bins(c, st))) return rc;
+        if ((rc = launch_assign_update(c, image, labels, st))) return rc;
+        if ((rc = launch_finalize(c, st))) return rc;
+        if (c->p.conv_threshold > 0.0) {
+            if ((rc = read_residual(c, st, &res))) return rc;
+            if (res < c->p.conv_threshold) { ++it; break; }
+        }
+    }
+    int64_t nlab = c->g.K;
+    if (c->p.enforce_connectivity) {
+        if ((rc = ensure_ccl_capacity(c, 32 * c->g.K + c->g.V / 1024 + 4096))) return rc;
+        if ((rc = run_connectivity(c, labels, labels, st, &nlab))) return rc;
+    }
+    if (centres && (rc = launch_export_centres(c, centres, st))) return rc;
+    if (out) {
+        if ((rc = read_residual(c, st, &res))) return rc;
+        out->num_clusters = c->g.K;
+        out->num_labels = nlab;
+        out->iterations = it;
+        out->residual = res;
+    }
+    return SSLIC_OK;
+}
+
+}  // namespace sslic
+
+using namespace sslic;
+
+extern "C" {
+
+int sslic_default_params(int32_t ndim, sslic_params* p)
+{
+    if (!p || ndim < 1 || ndim > 3) return SSLIC_EINVAL;
+    memset(p, 0, sizeof(*p));
+    p->ndim = ndim;
+    for (int d = 0; d < 4; ++d) {
+        p->size[d] = 1;
+        p->grid[d] = d < ndim ? 16 : 1;
+    }
+    p->channels = 3;
+    p->dtype = SSLIC_U8;
+    p->m = 10.0f;
+    p->max_iter = ndim >= 3 ? 5 : 10;
+    p->conv_threshold = 0.0;
+    p->perturb = 1;
+    p->enforce_connectivity = 1;
+    p->precision = 0;
+    return SSLIC_OK;
+}
+
+int sslic_create(const sslic_params* p, sslic_ctx** out)
+{
+    if (!out) return SSLIC_EINVAL;
+    *out = nullptr;
+    Geom g;
+    int rc = validate(p, &g);
+    if (rc) return rc;
+    sslic_ctx* c = new (std::nothrow) sslic_ctx();
+    if (!c) return SSLIC_ENOMEM;
+    c->p = *p;
+    c->g = g;
+    if ((rc = cuda_check(c, cudaGetDevice(&c->device), "cudaGetDevice")) ||
+        (rc = cuda_check(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device),
+                         "SM count"))) {
+        delete c;
+        return rc;
+    }
+    if ((rc = alloc_core(c))) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return SSLIC_OK;
+}
+
+int sslic_num_clusters(const sslic_ctx* c, int64_t* K)
+{
+    if (!c || !K) return SSLIC_EINVAL;
+    *K = c->g.K;
+    return SSLIC_OK;
+}
+
+int sslic_run(sslic_ctx* c, const void* image_dev, int32_t* labels_dev, float* centres_dev, void* stream,
+              sslic_result* out)
+{
+    if (!c || !image_dev || !labels_dev) return SSLIC_EINVAL;
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = launch_seed(c, image_dev, st);
+    if (rc) return rc;
+    return run_loop(c, image_dev, labels_dev, centres_dev, st, out);
+}
+
+int sslic_run_from(sslic_ctx* c, const void* image_dev, const float* init_centres_dev, int32_t* labels_dev,
+                   float* centres_dev, void* stream, sslic_result* out)
+{
+    if (!c || !image_dev || !labels_dev || !init_centres_dev) return SSLIC_EINVAL;
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = launch_import_centres(c, init_centres_dev, st);
+    if (rc) return rc;
+    return run_loop(c, image_dev, labels_dev, centres_dev, st, out);
+}
+
+int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host, float* centres_host, void* stream,
+                   sslic_result* out)
+{
+    if (!c || !image_host || !labels_host) return SSLIC_EINVAL;
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    const size_t esz = g.dtype == SSLIC_U8 ? 1 : (g.dtype == SSLIC_U16 ? 2 : 4);
+    const size_t img_bytes = (size_t)g.V * g.C * esz;
+    const size_t lab_bytes = (size_t)g.V * sizeof(int32_t);
+    const size_t cen_bytes = (size_t)g.K * (g.C + g.n) * sizeof(float);
+    int rc;
+    if (!w.img_dev) {
+        if ((rc = dalloc(c, (char**)&w.img_dev, img_bytes, "image"))) return rc;
+        if ((rc = dalloc(c, &w.lab_dev, (size_t)g.V, "labels"))) return rc;
+        if ((rc = dalloc(c, &w.cen_dev, (size_t)g.K * (g.C + g.n), "centres"))) return rc;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(w.img_dev, image_host, img_bytes, cudaMemcpyHostToDevice, st), "H2D")))
+        return rc;
+    if ((rc = launch_seed(c, w.img_dev, st))) return rc;
+    sslic_result r;
+    if ((rc = run_loop(c, w.img_dev, w.lab_dev, centres_host ? w.cen_dev : nullptr, st, &r))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(labels_host, w.lab_dev, lab_bytes, cudaMemcpyDeviceToHost, st), "D2H")))
+        return rc;
+    if (centres_host &&
+        (rc = cuda_check(c, cudaMemcpyAsync(centres_host, w.cen_dev, cen_bytes, cudaMemcpyDeviceToHost, st), "D2H")))
+        return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    if (out) *out = r;
+    return SSLIC_OK;
+}
+
+int sslic_seed(sslic_ctx* c, const void* image_dev, float* centres_dev, void* stream)
+{
+    if (!c || !image_dev || !centres_dev) return SSLIC_EINVAL;
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = launch_seed(c, image_dev, st);
+    if (rc) return rc;
+    return launch_export_centres(c, centres_dev, st);
+}
+
+int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* centres_in_dev, int32_t* labels_dev,
+                  float* centres_out_dev, void* stream, double* residual_host)
+{
+    if (!c || !image_dev || !centres_in_dev || !labels_dev || !centres_out_dev) return SSLIC_EINVAL;
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = launch_import_centres(c, centres_in_dev, st))) return rc;
+    if ((rc = build_bins(c, st))) return rc;
+    if ((rc = launch_assign_update(c, image_dev, labels_dev, st))) return rc;
+    if ((rc = launch_finalize(c, st))) return rc;
+    if ((rc = launch_export_centres(c, centres_out_dev, st))) return rc;
+    if (residual_host) return read_residual(c, st, residual_host);
+    return SSLIC_OK;
+}
+
+int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* labels_in_dev,
+                       int32_t* labels_out_dev, void* stream, int64_t* num_labels_host)
+{
+    if (!c || !centres_dev || !labels_in_dev || !labels_out_dev) return SSLIC_EINVAL;
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = ensure_ccl_capacity(c, 32 * c->g.K + c->g.V / 1024 + 4096))) return rc;
+    if ((rc = launch_import_centres(c, centres_dev, st))) return rc;
+    int64_t n = 0;
+    if ((rc = run_connectivity(c, labels_in_dev, labels_out_dev, st, &n))) return rc;
+    if (num_labels_host) *num_labels_host = n;
+    return SSLIC_OK;
+}
+
+void sslic_destroy(sslic_ctx* c)
+{
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+const char* sslic_strerror(int code)
+{
+    switch (code) {
+    case SSLIC_OK: return "ok";
+    case SSLIC_EINVAL: return "invalid argument";
+    case SSLIC_ENOMEM: return "out of memory";
+    case SSLIC_ECUDA: return "CUDA error";
+    case SSLIC_ETIMEOUT: return "device wait timed out";
+    case SSLIC_EBUSY: return "context busy";
+    case SSLIC_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown error";
+    }
+}
+
+const char* sslic_last_error(const sslic_ctx* c)
+{
+    return c ? c->err : "";
+}
+
+}  // extern "C"

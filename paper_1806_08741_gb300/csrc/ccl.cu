@@ -1,0 +1,535 @@
+// ccl.cu -- connectivity enforcement (Sec. 3.1, stage 3).
+//
+// The paper marks, for every centre, the connected component of its label
+// that contains the centre (or the label found in the S-box around it) as
+// final when it is larger than S^n/4, then walks the image in raster order:
+// each component that is not final gets a new label when large, otherwise
+// the label last encountered, and becomes final.  Readings used here: face
+// adjacency; seed = round-half-up(C_k) clamped, else the raster-first voxel of
+// label k in the box of offsets -floor(S_d/2)..ceil(S_d/2)-1; flood fills see
+// the labels before any relabelling; "last encountered" = the output label
+// of x - e_d for the smallest d with x_d > 0, where x is the raster-first
+// voxel of the component (the origin's component gets a new label); new
+// labels count up from K in raster order of the components' first voxels.
+//
+// Parallel form, equal to that sequential walk:
+//  1. ccl_local: per tile (2048 voxels), union-find in shared memory with
+//     atomicMin linking; local roots are the tile-raster-first voxels and
+//     get dense local ids (uint16 per voxel) and global record ids
+//     (tile base + local id) with label, size and first voxel.
+//  2. ccl_faces: union of the records across tile faces (global union-find).
+//  3. flatten + root statistics: component size = sum, first voxel = min.
+//  4. phase 1 (per centre) sets the final flag of its component.
+//  5. phase 2 (per component): final -> own label; large or at the origin ->
+//     new, ranked by first voxel (sort); otherwise a link to the component
+//     holding x - e_d, whose first voxel is strictly smaller, so the links
+//     form a forest rooted at resolved components; each pending component
+//     walks its links to a resolved one.
+//  6. relabel every voxel through its record.
+#include <climits>
+#include <vector>
+
+#include "common.cuh"
+
+namespace sslic {
+
+template <int NDIM>
+struct CclCfg;
+template <>
+struct CclCfg<3> { static constexpr int TX = 32, TY = 8, TZ = 8; };
+template <>
+struct CclCfg<2> { static constexpr int TX = 64, TY = 32, TZ = 1; };
+template <>
+struct CclCfg<1> { static constexpr int TX = 2048, TY = 1, TZ = 1; };
+
+constexpr int kCclThreads = 256;
+constexpr int kCclTV = 2048;
+constexpr int kPerThread = kCclTV / kCclThreads;  // 8 consecutive voxels per thread
+
+// ---- union-find with atomicMin linking (parents only ever decrease) --------
+// Parent indices strictly decrease along every chain, so walks end within
+// the number of nodes; every walk is still bounded and reports a broken
+// invariant through *err instead of spinning.
+constexpr int kWalkLimit = 1 << 26;
+
+__device__ __forceinline__ int uf_find(volatile int* par, int x, unsigned* err)
+{
+    for (int i = 0; i < kWalkLimit; ++i) {
+        const int p = par[x];
+        if (p == x) return x;
+        x = p;
+    }
+    atomicExch(err, 1u);
+    return x;
+}
+
+__device__ __forceinline__ void uf_unite(int* par, int a, int b, unsigned* err)
+{
+    a = uf_find(par, a, err);
+    b = uf_find(par, b, err);
+    for (int i = 0; i < kWalkLimit && a != b; ++i) {
+        if (a < b) { int t = a; a = b; b = t; }
+        const int old = atomicMin(&par[a], b);
+        if (old == a) return;       // a was a root and now hangs under b
+        a = uf_find(par, old, err); // a had been re-linked meanwhile: retry from its root
+        b = uf_find(par, b, err);
+    }
+    if (a != b) atomicExch(err, 1u);
+}
+
+template <int NDIM>
+__device__ __forceinline__ int64_t ccl_tile_of(const Geom& g, int64_t x, int64_t y, int64_t z, int64_t ntx,
+                                               int64_t nty)
+{
+    using Cfg = CclCfg<NDIM>;
+    return x / Cfg::TX + ntx * (y / Cfg::TY + nty * (z / Cfg::TZ));
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kCclThreads)
+ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restrict__ lid_img,
+                 int* __restrict__ tile_base, int* __restrict__ comp_label, unsigned* __restrict__ comp_size,
+                 unsigned long long* __restrict__ comp_first, int* __restrict__ gparent,
+                 unsigned* __restrict__ counters, int64_t m_cap, int64_t ntx, int64_t nty)
+{
+    using Cfg = CclCfg<NDIM>;
+    constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
+    static_assert(TX * TY * TZ == kCclTV, "tile size");
+    __shared__ int lab[kCclTV];
+    __shared__ int par[kCclTV];
+    __shared__ uint16_t lidv[kCclTV];
+    __shared__ unsigned sz[kCclTV];
+    __shared__ unsigned wsum[kCclThreads / 32];
+    __shared__ int s_base;
+
+    const int tid = threadIdx.x;
+    const int64_t tile = blockIdx.x;
+    const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * TZ;
+    const int ex = (int)imin64(TX, g.N[0] - X0);
+    const int ey = (int)imin64(TY, g.N[1] - Y0);
+    const int ez = (int)imin64(TZ, g.N[2] - Z0);
+
+    for (int e = tid; e < kCclTV; e += kCclThreads) {
+        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        bool v = xl < ex && yl < ey && zl < ez;
+        lab[e] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
+        par[e] = v ? e : -1;
+        sz[e] = 0;
+    }
+    __syncthreads();
+    for (int e = tid; e < kCclTV; e += kCclThreads) {
+        if (par[e] < 0) continue;
+        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        const int L = lab[e];
+        if (xl > 0 && lab[e - 1] == L) uf_unite(par, e, e - 1, &counters[3]);
+        if (NDIM >= 2 && yl > 0 && lab[e - TX] == L) uf_unite(par, e, e - TX, &counters[3]);
+        if (NDIM >= 3 && zl > 0 && lab[e - TX * TY] == L) uf_unite(par, e, e - TX * TY, &counters[3]);
+    }
+    __syncthreads();
+    for (int e = tid; e < kCclTV; e += kCclThreads)
+        if (par[e] >= 0) par[e] = uf_find(par, e, &counters[3]);
+    __syncthreads();
+    // rank the roots (the tile-raster-first voxel of each local component)
+    unsigned mine = 0;
+    for (int i = 0; i < kPerThread; ++i) {
+        int e = tid * kPerThread + i;
+        mine += (par[e] == e) ? 1u : 0u;
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    unsigned woff = 0, total = 0;
+    for (int w = 0; w < kCclThreads / 32; ++w) {
+        if (w < warp) woff += wsum[w];
+        total += wsum[w];
+    }
+    if (tid == 0) {
+        unsigned base = atomicAdd(&counters[0], total);
+        if ((int64_t)base + total > m_cap) atomicExch(&counters[1], 1u);
+        s_base = (int)base;
+    }
+    unsigned rank = woff + incl - mine;
+    for (int i = 0; i < kPerThread; ++i) {
+        int e = tid * kPerThread + i;
+        if (par[e] == e) lidv[e] = (uint16_t)(rank++);
+    }
+    __syncthreads();
+    const int base = s_base;
+    if ((int64_t)base + total > m_cap) return;  // host grows the records and reruns
+    for (int e = tid; e < kCclTV; e += kCclThreads) {
+        if (par[e] < 0) continue;
+        const uint16_t l = lidv[par[e]];
+        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
+        atomicAdd(&sz[l], 1u);
+    }
+    __syncthreads();
+    for (int e = tid; e < kCclTV; e += kCclThreads) {
+        if (par[e] != e) continue;
+        const int r = base + lidv[e];
+        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        comp_label[r] = lab[e];
+        comp_size[r] = sz[lidv[e]];
+        comp_first[r] = (unsigned long long)vidx(g, X0 + xl, Y0 + yl, Z0 + zl);
+        gparent[r] = r;
+    }
+    if (tid == 0) tile_base[tile] = base;
+}
+
+template <int NDIM>
+__device__ __forceinline__ int gid_of(const Geom& g, const uint16_t* lid_img, const int* tile_base, int64_t x,
+                                      int64_t y, int64_t z, int64_t ntx, int64_t nty)
+{
+    return tile_base[ccl_tile_of<NDIM>(g, x, y, z, ntx, nty)] + (int)lid_img[vidx(g, x, y, z)];
+}
+
+// union across the low faces of every tile
+template <int NDIM>
+__global__ void __launch_bounds__(kCclThreads)
+ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __restrict__ lid_img,
+                 const int* __restrict__ tile_base, int* gparent, unsigned* counters, int64_t ntx,
+                 int64_t nty)
+{
+    using Cfg = CclCfg<NDIM>;
+    constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
+    const int64_t tile = blockIdx.x;
+    const int64_t T0[3] = {(tile % ntx) * TX, ((tile / ntx) % nty) * TY, (tile / (ntx * nty)) * TZ};
+    const int TT[3] = {TX, TY, TZ};
+    int E[3];
+    for (int d = 0; d < 3; ++d) E[d] = (int)imin64(TT[d], g.N[d] - T0[d]);
+    for (int d = 0; d < NDIM; ++d) {
+        if (T0[d] == 0) continue;
+        const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+        const int n = E[a1] * E[a2];
+        for (int i = threadIdx.x; i < n; i += kCclThreads) {
+            int64_t p[3];
+            p[d] = T0[d];
+            p[a1] = T0[a1] + i % E[a1];
+            p[a2] = T0[a2] + i / E[a1];
+            int64_t q[3] = {p[0], p[1], p[2]};
+            q[d] -= 1;
+            const int64_t ia = vidx(g, p[0], p[1], p[2]), ib = vidx(g, q[0], q[1], q[2]);
+            if (labels[ia] != labels[ib]) continue;
+            uf_unite(gparent, gid_of<NDIM>(g, lid_img, tile_base, p[0], p[1], p[2], ntx, nty),
+                     gid_of<NDIM>(g, lid_img, tile_base, q[0], q[1], q[2], ntx, nty), &counters[3]);
+        }
+    }
+}
+
+__global__ void ccl_flatten_kernel(int* gparent, unsigned* counters)
+{
+    const int64_t M = counters[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        gparent[i] = uf_find(gparent, (int)i, &counters[3]);
+}
+
+__global__ void ccl_rootstats_kernel(const int* __restrict__ gparent, const unsigned* __restrict__ comp_size,
+                                     const unsigned long long* __restrict__ comp_first,
+                                     unsigned long long* __restrict__ root_size,
+                                     unsigned long long* __restrict__ root_first,
+                                     const unsigned* __restrict__ counters)
+{
+    const int64_t M = counters[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = gparent[i];
+        atomicAdd(&root_size[r], (unsigned long long)comp_size[i]);
+        atomicMin(&root_first[r], comp_first[i]);
+    }
+}
+
+// phase 1: one component per centre, final if 4 * size > prod S
+template <int NDIM>
+__global__ void conn_phase1_kernel(Geom g, const float* __restrict__ ctr, const int32_t* __restrict__ labels,
+                                   const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
+                                   const int* __restrict__ gparent, const unsigned long long* __restrict__ root_size,
+                                   uint8_t* __restrict__ fin, int64_t ntx, int64_t nty)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= g.K) return;
+    const float* pc = ctr + k * g.CW + g.C;
+    int64_t p[3] = {0, 0, 0};
+    for (int d = 0; d < g.n; ++d) {
+        int64_t v = (int64_t)floor((double)pc[d] + 0.5);
+        p[d] = v < 0 ? 0 : (v > g.N[d] - 1 ? g.N[d] - 1 : v);
+    }
+    int64_t s[3] = {-1, -1, -1};
+    if (labels[vidx(g, p[0], p[1], p[2])] == (int32_t)k) {
+        s[0] = p[0]; s[1] = p[1]; s[2] = p[2];
+    } else {
+        int64_t lo[3], hi[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = imax64(0, p[d] - g.S[d] / 2);
+            hi[d] = imin64(g.N[d] - 1, p[d] + (g.S[d] + 1) / 2 - 1);
+        }
+        for (int64_t z = lo[2]; z <= hi[2] && s[0] < 0; ++z)
+            for (int64_t y = lo[1]; y <= hi[1] && s[0] < 0; ++y)
+                for (int64_t x = lo[0]; x <= hi[0]; ++x)
+                    if (labels[vidx(g, x, y, z)] == (int32_t)k) { s[0] = x; s[1] = y; s[2] = z; break; }
+    }
+    if (s[0] < 0) return;
+    const int G = gparent[gid_of<NDIM>(g, lid_img, tile_base, s[0], s[1], s[2], ntx, nty)];
+    if (4ull * root_size[G] > (unsigned long long)g.sprod) fin[G] = 1;
+}
+
+constexpr int kPendingMerge = -2;
+constexpr int kPendingNew = -3;
+
+template <int NDIM>
+__global__ void conn_phase2_kernel(Geom g, const int* __restrict__ gparent, const int* __restrict__ comp_label,
+                                   const unsigned long long* __restrict__ root_size,
+                                   const unsigned long long* __restrict__ root_first,
+                                   const uint8_t* __restrict__ fin, const uint16_t* __restrict__ lid_img,
+                                   const int* __restrict__ tile_base, int* __restrict__ out_label,
+                                   int* __restrict__ link, unsigned long long* __restrict__ new_key,
+                                   int* __restrict__ new_val, unsigned* __restrict__ counters, int64_t ntx,
+                                   int64_t nty)
+{
+    const int64_t M = counters[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        if (gparent[i] != (int)i) continue;
+        if (fin[i]) { out_label[i] = comp_label[i]; continue; }
+        const unsigned long long f = root_first[i];
+        if (4ull * root_size[i] > (unsigned long long)g.sprod || f == 0ull) {
+            unsigned pos = atomicAdd(&counters[2], 1u);
+            new_key[pos] = f;
+            new_val[pos] = (int)i;
+            out_label[i] = kPendingNew;
+            continue;
+        }
+        int64_t x[3] = {(int64_t)(f % (unsigned long long)g.N[0]),
+                        (int64_t)((f / (unsigned long long)g.N[0]) % (unsigned long long)g.N[1]),
+                        (int64_t)(f / ((unsigned long long)g.N[0] * (unsigned long long)g.N[1]))};
+        int d = 0;
+        while (x[d] == 0) ++d;
+        x[d] -= 1;
+        link[i] = gparent[gid_of<NDIM>(g, lid_img, tile_base, x[0], x[1], x[2], ntx, nty)];
+        out_label[i] = kPendingMerge;
+    }
+}
+
+// bitonic sort of (key, value) pairs -- one block, in shared memory
+constexpr int kSmallSort = 2048;
+__global__ void sort_small_kernel(unsigned long long* key, int* val, const unsigned* __restrict__ counters)
+{
+    __shared__ unsigned long long sk[kSmallSort];
+    __shared__ int sv[kSmallSort];
+    const int n = (int)counters[2];
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        sk[i] = i < n ? key[i] : ~0ull;
+        sv[i] = i < n ? val[i] : -1;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = (i & k) == 0;
+                    if ((sk[i] > sk[l]) == up) {
+                        unsigned long long tk = sk[i]; sk[i] = sk[l]; sk[l] = tk;
+                        int tv = sv[i]; sv[i] = sv[l]; sv[l] = tv;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { key[i] = sk[i]; val[i] = sv[i]; }
+}
+
+__global__ void sort_pad_kernel(const unsigned long long* __restrict__ key, const int* __restrict__ val,
+                                unsigned long long* __restrict__ k2, int* __restrict__ v2, int64_t n, int64_t P)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        k2[i] = i < n ? key[i] : ~0ull;
+        v2[i] = i < n ? val[i] : -1;
+    }
+}
+
+__global__ void sort_step_kernel(unsigned long long* key, int* val, int64_t P, int64_t k, int64_t j)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t l = i ^ j;
+        if (l > i) {
+            bool up = (i & k) == 0;
+            if ((key[i] > key[l]) == up) {
+                unsigned long long tk = key[i]; key[i] = key[l]; key[l] = tk;
+                int tv = val[i]; val[i] = val[l]; val[l] = tv;
+            }
+        }
+    }
+}
+
+__global__ void assign_new_kernel(const int* __restrict__ val, int* __restrict__ out_label, int64_t K,
+                                  int64_t n)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        out_label[val[r]] = (int)(K + r);
+}
+
+__global__ void conn_resolve_kernel(const int* __restrict__ gparent, const int* __restrict__ link,
+                                    volatile int* out_label, unsigned* counters)
+{
+    const int64_t M = counters[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        if (gparent[i] != (int)i || out_label[i] != kPendingMerge) continue;
+        int j = link[i];
+        int o = out_label[j];
+        // pending merge: follow its link (first voxels strictly decrease, so
+        // the walk is shorter than the component count)
+        for (int64_t step = 0; o < 0; ++step) {
+            if (step > M) { atomicExch(&counters[3], 1u); o = 0; break; }
+            j = link[j];
+            o = out_label[j];
+        }
+        out_label[i] = o;
+    }
+}
+
+template <int NDIM>
+__global__ void __launch_bounds__(kCclThreads)
+conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
+                    const int* __restrict__ gparent, const int* __restrict__ out_label,
+                    int32_t* __restrict__ labels_out, int64_t ntx, int64_t nty)
+{
+    using Cfg = CclCfg<NDIM>;
+    constexpr int TX = Cfg::TX, TY = Cfg::TY;
+    const int64_t tile = blockIdx.x;
+    const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * Cfg::TZ;
+    const int base = tile_base[tile];
+    for (int e = threadIdx.x; e < kCclTV; e += kCclThreads) {
+        int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
+        if (x >= g.N[0] || y >= g.N[1] || z >= g.N[2]) continue;
+        const int64_t q = vidx(g, x, y, z);
+        labels_out[q] = out_label[gparent[base + lid_img[q]]];
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int NDIM>
+static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,
+                             int64_t* num_labels)
+{
+    using Cfg = CclCfg<NDIM>;
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    const int64_t ntx = (g.N[0] + Cfg::TX - 1) / Cfg::TX;
+    const int64_t nty = (g.N[1] + Cfg::TY - 1) / Cfg::TY;
+    const int64_t ntz = (g.N[2] + Cfg::TZ - 1) / Cfg::TZ;
+    const int64_t ntiles = ntx * nty * ntz;
+    int rc;
+    unsigned hc[4];
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
+        ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.comp_label,
+                                                              w.comp_size, w.comp_first, w.gparent, w.counters,
+                                                              w.m_cap, ntx, nty);
+        if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
+        if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                             "read component count")))
+            return rc;
+        if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+        if (!hc[1]) break;
+        if (attempt == 1) return set_error(c, SSLIC_ENOMEM, "component records still overflow");
+        if ((rc = ensure_ccl_capacity(c, (int64_t)hc[0] + hc[0] / 4 + 4096))) return rc;
+    }
+    const int64_t M = hc[0];
+    if (M > INT_MAX) return set_error(c, SSLIC_EUNSUPPORTED, "more than 2^31 components");
+    if ((rc = cuda_check(c, cudaMemsetAsync(w.root_size, 0, M * sizeof(unsigned long long), st), "memset"))) return rc;
+    if ((rc = cuda_check(c, cudaMemsetAsync(w.root_first, 0xff, M * sizeof(unsigned long long), st), "memset"))) return rc;
+    if ((rc = cuda_check(c, cudaMemsetAsync(w.fin, 0, M, st), "memset"))) return rc;
+    ccl_faces_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.gparent,
+                                                           w.counters, ntx, nty);
+    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
+    const int gb = c->sms * 8;
+    ccl_flatten_kernel<<<gb, 256, 0, st>>>(w.gparent, w.counters);
+    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
+    ccl_rootstats_kernel<<<gb, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
+                                             w.counters);
+    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_rootstats_kernel"))) return rc;
+    conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,
+                                                                 w.gparent, w.root_size, w.fin, ntx, nty);
+    if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase1_kernel"))) return rc;
+    conn_phase2_kernel<NDIM><<<gb, 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
+                                                  w.lid, w.tile_base, w.out_label, w.link, w.new_key, w.new_val,
+                                                  w.counters, ntx, nty);
+    if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase2_kernel"))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                         "read new count")))
+        return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    const int64_t Mn = hc[2];
+    if (g.K + Mn > INT_MAX) return set_error(c, SSLIC_EUNSUPPORTED, "label count exceeds int32");
+    if (Mn > 0) {
+        const int* sorted_val = w.new_val;
+        if (Mn <= kSmallSort) {
+            sort_small_kernel<<<1, 1024, 0, st>>>(w.new_key, w.new_val, w.counters);
+            if ((rc = cuda_check(c, cudaGetLastError(), "sort_small_kernel"))) return rc;
+        } else {
+            int64_t P = 1;
+            while (P < Mn) P <<= 1;
+            if (P > w.sort_cap) {
+                cudaFree(w.sort_key);
+                cudaFree(w.sort_val);
+                w.sort_key = nullptr;
+                w.sort_val = nullptr;
+                w.sort_cap = 0;
+                if (cudaMalloc(&w.sort_key, P * sizeof(unsigned long long)) != cudaSuccess ||
+                    cudaMalloc(&w.sort_val, P * sizeof(int)) != cudaSuccess)
+                    return set_error(c, SSLIC_ENOMEM, "sort scratch");
+                w.sort_cap = P;
+            }
+            sort_pad_kernel<<<gb, 256, 0, st>>>(w.new_key, w.new_val, w.sort_key, w.sort_val, Mn, P);
+            for (int64_t k = 2; k <= P; k <<= 1)
+                for (int64_t j = k >> 1; j > 0; j >>= 1)
+                    sort_step_kernel<<<gb, 256, 0, st>>>(w.sort_key, w.sort_val, P, k, j);
+            if ((rc = cuda_check(c, cudaGetLastError(), "sort_step_kernel"))) return rc;
+            sorted_val = w.sort_val;
+        }
+        assign_new_kernel<<<gb, 256, 0, st>>>(sorted_val, w.out_label, g.K, Mn);
+        if ((rc = cuda_check(c, cudaGetLastError(), "assign_new_kernel"))) return rc;
+    }
+    conn_resolve_kernel<<<gb, 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
+    if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
+    conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.gparent, w.out_label,
+                                                              labels_out, ntx, nty);
+    if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                         "read status")))
+        return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a union-find walk exceeded its bound");
+    if (num_labels) *num_labels = g.K + Mn;
+    return SSLIC_OK;
+}
+
+int64_t ccl_num_tiles(const Geom& g)
+{
+    if (g.n == 3) {
+        using C3 = CclCfg<3>;
+        return ((g.N[0] + C3::TX - 1) / C3::TX) * ((g.N[1] + C3::TY - 1) / C3::TY) * ((g.N[2] + C3::TZ - 1) / C3::TZ);
+    }
+    if (g.n == 2) {
+        using C2 = CclCfg<2>;
+        return ((g.N[0] + C2::TX - 1) / C2::TX) * ((g.N[1] + C2::TY - 1) / C2::TY);
+    }
+    return (g.N[0] + CclCfg<1>::TX - 1) / CclCfg<1>::TX;
+}
+
+int run_connectivity(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,
+                     int64_t* num_labels)
+{
+    switch (c->g.n) {
+    case 3: return connectivity_impl<3>(c, labels_in, labels_out, st, num_labels);
+    case 2: return connectivity_impl<2>(c, labels_in, labels_out, st, num_labels);
+    default: return connectivity_impl<1>(c, labels_in, labels_out, st, num_labels);
+    }
+}
+
+}  // namespace sslic

@@ -1,0 +1,172 @@
+// common.cuh -- shared definitions of the sm_103a SSLIC kernels.
+//
+// Internal conventions (the C ABI in include/sslic.h converts to and from
+// the public layout):
+//  * every image is handled as 3-D: missing axes have N_d = 1 and S_d = 1,
+//    which adds no term to the distance and no seed along that axis;
+//  * centres are a K x CW float table with CW = C + 3: the C features, then
+//    x_0, x_1, x_2 (padded axes hold 0);
+//  * integer images accumulate exact uint64 sums (C features, 3 positions,
+//    count) per cluster; float images add C double feature sums.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sslic.h"
+
+namespace sslic {
+
+constexpr int kMaxChannels = 256;
+constexpr uint8_t kNoSlot = 255;
+
+struct Geom {
+    int n;            // real spatial dims (1..3)
+    int64_t N[3];     // sizes, padded with 1
+    int S[3];         // grid, padded with 1
+    int64_t nb[3];    // seeds (= bins) per axis: ceil(N_d / S_d)
+    int64_t off[3];   // lattice offset o_d = floor((N_d - 1 - (nb_d - 1) S_d) / 2)
+    int64_t V, K;
+    int C;            // channels
+    int dtype;        // SSLIC_U8 / SSLIC_U16 / SSLIC_F32
+    int CW;           // internal centre row width C + 3
+    int AW;           // accumulator row width C + 4 (features, x, y, z, count)
+    float w[3];       // fl32(m^2 / S_d^2)
+    double w64[3];    // m^2 / S_d^2
+    int64_t sprod;    // prod S_d over the real axes
+};
+
+// ---- packed FP32 pairs (sm_100 family .f32x2 arithmetic, round to nearest) --
+__device__ __forceinline__ uint64_t pk2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// ---- geometry helpers ------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
+
+__host__ __device__ __forceinline__ int64_t vidx(const Geom& g, int64_t x, int64_t y, int64_t z)
+{
+    return x + g.N[0] * (y + g.N[1] * z);
+}
+
+// Covered range of a centre coordinate c along an axis of grid S: the voxels
+// x with c - S <= x < c + S are exactly [ceil(c) - S, ceil(c) + S - 1]
+// (S is an integer, so c - S <= x <=> x >= ceil(c) - S, and x < c + S <=>
+// x <= ceil(c) + S - 1).  Sec. 2.2 "[2S x 2S] region around C_k".
+__device__ __forceinline__ int64_t window_lo(float c, int S)
+{
+    return (int64_t)ceilf(c) - S;
+}
+
+// bin of a centre coordinate: floor(c) / S (exactly floor(c / S) for c >= 0)
+__device__ __forceinline__ int64_t bin_of_coord(float c, int S, int64_t nb)
+{
+    int64_t b = (int64_t)floorf(c);
+    b = b < 0 ? 0 : b / S;
+    return b >= nb ? nb - 1 : b;
+}
+
+// ---- context ---------------------------------------------------------------
+struct Workspace {
+    // centres and update sums
+    float* ctr = nullptr;               // K x CW
+    unsigned long long* acc = nullptr;  // K x AW
+    double* facc = nullptr;             // K x C (float images)
+    double* resid_k = nullptr;          // K: per-cluster residual terms
+    unsigned* nonempty_k = nullptr;     // K
+    double* resid_part = nullptr;       // reduction partials
+    unsigned* resid_cnt_part = nullptr;
+    double* resid_out = nullptr;        // [0] residual
+    // bins
+    unsigned* bin_count = nullptr;      // K + 1
+    unsigned* bin_start = nullptr;      // K + 1
+    unsigned* bin_cursor = nullptr;     // K
+    int* bin_items = nullptr;           // K
+    int* bin_of = nullptr;              // K
+    unsigned* scan_tmp = nullptr;       // scan block sums (all levels)
+    size_t scan_tmp_len = 0;
+    // assign tile overflow list
+    int64_t n_assign_tiles = 0;
+    int64_t* ovf_tiles = nullptr;
+    unsigned* ovf_count = nullptr;
+    // connectivity
+    uint16_t* lid = nullptr;            // V
+    int64_t n_ccl_tiles = 0;
+    int* tile_base = nullptr;           // n_ccl_tiles
+    unsigned* counters = nullptr;       // [0] M, [1] overflow, [2] new count
+    int64_t m_cap = 0;
+    int* comp_label = nullptr;
+    unsigned* comp_size = nullptr;
+    unsigned long long* comp_first = nullptr;
+    int* gparent = nullptr;
+    unsigned long long* root_size = nullptr;
+    unsigned long long* root_first = nullptr;
+    uint8_t* fin = nullptr;
+    int* out_label = nullptr;
+    int* link = nullptr;
+    unsigned long long* new_key = nullptr;
+    int* new_val = nullptr;
+    unsigned long long* sort_key = nullptr;  // power-of-two scratch for large sorts
+    int* sort_val = nullptr;
+    int64_t sort_cap = 0;
+    // host-buffer entry point
+    void* img_dev = nullptr;
+    int32_t* lab_dev = nullptr;
+    float* cen_dev = nullptr;
+};
+
+}  // namespace sslic
+
+struct sslic_ctx {
+    sslic_params p;
+    sslic::Geom g;
+    sslic::Workspace ws;
+    int device = 0;
+    int sms = 148;
+    int busy = 0;
+    char err[512] = {0};
+};
+
+namespace sslic {
+// kernels / launchers implemented in the .cu files
+int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st);
+int build_bins(sslic_ctx* c, cudaStream_t st);
+int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st);
+int launch_finalize(sslic_ctx* c, cudaStream_t st);
+int launch_export_centres(sslic_ctx* c, float* out, cudaStream_t st);
+int launch_import_centres(sslic_ctx* c, const float* in, cudaStream_t st);
+int run_connectivity(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,
+                     int64_t* num_labels);
+int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t n, cudaStream_t st);
+size_t scan_tmp_needed(int64_t n);
+int64_t ccl_num_tiles(const Geom& g);
+int64_t assign_num_tiles(const Geom& g);
+int ensure_ccl_capacity(sslic_ctx* c, int64_t m);
+int set_error(sslic_ctx* c, int code, const char* fmt, ...);
+int cuda_check(sslic_ctx* c, cudaError_t e, const char* what);
+}  // namespace sslic

@@ -1,0 +1,320 @@
+"""Thin Python binding of the SSLIC C ABI (include/sslic.h).
+
+Argument marshalling only: every step of the method runs in the sm_103a
+kernels of ``libsslic.so``.  Tensors are torch tensors (device memory and
+streams come from PyTorch); their data pointers are handed to the library
+unchanged.  There is no CPU fallback: if the library cannot be loaded, or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsslic.so")
+
+SSLIC_OK = 0
+U8, U16, F32 = 0, 1, 2
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUSY", -6: "EUNSUPPORTED"}
+
+EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_run",
+           "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
+           "sslic_connectivity", "sslic_destroy", "sslic_strerror", "sslic_last_error")
+
+
+class SSLICError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        self.code = code
+        super().__init__(f"{what} failed: {_ERRORS.get(code, code)} {detail}".strip())
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int32),
+        ("size", ctypes.c_int64 * 4),
+        ("channels", ctypes.c_int32),
+        ("dtype", ctypes.c_int32),
+        ("grid", ctypes.c_int32 * 4),
+        ("m", ctypes.c_float),
+        ("max_iter", ctypes.c_int32),
+        ("conv_threshold", ctypes.c_double),
+        ("perturb", ctypes.c_int32),
+        ("enforce_connectivity", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("num_clusters", ctypes.c_int64),
+        ("num_labels", ctypes.c_int64),
+        ("iterations", ctypes.c_int32),
+        ("residual", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsslic.so (built by ``paper_1806_08741_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    P = ctypes.POINTER(_Params)
+    R = ctypes.POINTER(_Result)
+    C = ctypes.c_void_p  # sslic_ctx*
+    L.sslic_default_params.argtypes = [ctypes.c_int32, P]
+    L.sslic_create.argtypes = [P, ctypes.POINTER(C)]
+    L.sslic_num_clusters.argtypes = [C, ctypes.POINTER(ctypes.c_int64)]
+    L.sslic_run.argtypes = [C, vp, vp, vp, vp, R]
+    L.sslic_run_from.argtypes = [C, vp, vp, vp, vp, vp, R]
+    L.sslic_run_host.argtypes = [C, vp, vp, vp, vp, R]
+    L.sslic_seed.argtypes = [C, vp, vp, vp]
+    L.sslic_iterate.argtypes = [C, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    L.sslic_connectivity.argtypes = [C, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.sslic_destroy.argtypes = [C]
+    L.sslic_destroy.restype = None
+    L.sslic_strerror.argtypes = [ctypes.c_int]
+    L.sslic_strerror.restype = ctypes.c_char_p
+    L.sslic_last_error.argtypes = [C]
+    L.sslic_last_error.restype = ctypes.c_char_p
+    for f in ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_run",
+              "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
+              "sslic_connectivity"):
+        getattr(L, f).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+@dataclass
+class Params:
+    """The paper's filter parameters (Sec. 3.2).  ``size`` and ``grid`` list
+    axis 0 (x, fastest) first."""
+
+    size: tuple
+    grid: tuple
+    channels: int = 3
+    dtype: int = U8
+    m: float = 10.0
+    max_iter: int = 10
+    conv_threshold: float = 0.0
+    perturb: bool = True
+    enforce_connectivity: bool = False
+    precision: int = 0
+
+    @property
+    def ndim(self) -> int:
+        return len(self.size)
+
+    def to_c(self) -> _Params:
+        p = _Params()
+        p.ndim = len(self.size)
+        grid = tuple(self.grid)
+        if len(grid) == 1:
+            grid = grid * len(self.size)
+        for d in range(4):
+            p.size[d] = int(self.size[d]) if d < len(self.size) else 1
+            p.grid[d] = int(grid[d]) if d < len(grid) else 1
+        p.channels = int(self.channels)
+        p.dtype = int(self.dtype)
+        p.m = float(self.m)
+        p.max_iter = int(self.max_iter)
+        p.conv_threshold = float(self.conv_threshold)
+        p.perturb = int(bool(self.perturb))
+        p.enforce_connectivity = int(bool(self.enforce_connectivity))
+        p.precision = int(self.precision)
+        return p
+
+
+def _dtype_code(t) -> int:
+    import torch
+    return {torch.uint8: U8, torch.uint16: U16, torch.float32: F32}[t.dtype]
+
+
+def params_for(image, grid, **kw) -> Params:
+    """Params for an image tensor/array shaped [N_{n-1}, ..., N_0, C]."""
+    shape = tuple(image.shape)
+    size = tuple(int(s) for s in reversed(shape[:-1]))
+    if isinstance(image, np.ndarray):
+        dt = {np.dtype(np.uint8): U8, np.dtype(np.uint16): U16, np.dtype(np.float32): F32}[image.dtype]
+    else:
+        dt = _dtype_code(image)
+    return Params(size=size, grid=tuple(grid), channels=int(shape[-1]), dtype=dt, **kw)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One SSLIC context (device workspace sized for one image shape)."""
+
+    def __init__(self, params: Params):
+        self.lib = load()
+        self.params = params
+        self._c = ctypes.c_void_p(0)
+        rc = self.lib.sslic_create(ctypes.byref(params.to_c()), ctypes.byref(self._c))
+        if rc != SSLIC_OK:
+            raise SSLICError(rc, "sslic_create")
+        k = ctypes.c_int64(0)
+        self._check(self.lib.sslic_num_clusters(self._c, ctypes.byref(k)), "sslic_num_clusters")
+        self.K = int(k.value)
+
+    # -- helpers -----------------------------------------------------------------
+    def _check(self, rc: int, what: str):
+        if rc != SSLIC_OK:
+            detail = self.lib.sslic_last_error(self._c) if self._c else b""
+            raise SSLICError(rc, what, (detail or b"").decode())
+
+    @property
+    def centre_width(self) -> int:
+        return self.params.channels + self.params.ndim
+
+    def _need(self, t, numel, what, device=True):
+        if t is None:
+            return
+        n = t.size if isinstance(t, np.ndarray) else t.numel()
+        if n != numel:
+            raise ValueError(f"{what}: expected {numel} elements, got {n}")
+        if isinstance(t, np.ndarray):
+            if device:
+                raise ValueError(f"{what} must be a device tensor")
+            if not t.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"{what} must be contiguous")
+        else:
+            if device != t.is_cuda:
+                raise ValueError(f"{what} must be on the {'GPU' if device else 'host'}")
+            if not t.is_contiguous():
+                raise ValueError(f"{what} must be contiguous")
+
+    def _voxels(self) -> int:
+        return int(np.prod(self.params.size))
+
+    # -- the C ABI -----------------------------------------------------------------
+    def run(self, image, labels, centres=None, stream=None) -> dict:
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image")
+        self._need(labels, V, "labels")
+        self._need(centres, self.K * self.centre_width, "centres")
+        r = _Result()
+        self._check(self.lib.sslic_run(self._c, _ptr(image), _ptr(labels), _ptr(centres),
+                                       _stream(stream), ctypes.byref(r)), "sslic_run")
+        return {"num_clusters": r.num_clusters, "num_labels": r.num_labels,
+                "iterations": r.iterations, "residual": r.residual}
+
+    def run_async(self, image, labels, centres=None, stream=None) -> None:
+        """sslic_run without the result read-back (stays stream ordered when
+        the convergence threshold is off and connectivity is disabled)."""
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image")
+        self._need(labels, V, "labels")
+        self._need(centres, self.K * self.centre_width, "centres")
+        self._check(self.lib.sslic_run(self._c, _ptr(image), _ptr(labels), _ptr(centres),
+                                       _stream(stream), None), "sslic_run")
+
+    def run_from(self, image, init_centres, labels, centres=None, stream=None) -> dict:
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image")
+        self._need(init_centres, self.K * self.centre_width, "init_centres")
+        self._need(labels, V, "labels")
+        self._need(centres, self.K * self.centre_width, "centres")
+        r = _Result()
+        self._check(self.lib.sslic_run_from(self._c, _ptr(image), _ptr(init_centres), _ptr(labels),
+                                            _ptr(centres), _stream(stream), ctypes.byref(r)),
+                    "sslic_run_from")
+        return {"num_clusters": r.num_clusters, "num_labels": r.num_labels,
+                "iterations": r.iterations, "residual": r.residual}
+
+    def run_host(self, image, labels, centres=None, stream=None) -> dict:
+        """Host buffers (numpy arrays or CPU tensors, ideally pinned)."""
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image", device=False)
+        self._need(labels, V, "labels", device=False)
+        self._need(centres, self.K * self.centre_width, "centres", device=False)
+        r = _Result()
+        self._check(self.lib.sslic_run_host(self._c, _ptr(image), _ptr(labels), _ptr(centres),
+                                            _stream(stream), ctypes.byref(r)), "sslic_run_host")
+        return {"num_clusters": r.num_clusters, "num_labels": r.num_labels,
+                "iterations": r.iterations, "residual": r.residual}
+
+    def seed(self, image, centres, stream=None) -> None:
+        self._need(image, self._voxels() * self.params.channels, "image")
+        self._need(centres, self.K * self.centre_width, "centres")
+        self._check(self.lib.sslic_seed(self._c, _ptr(image), _ptr(centres), _stream(stream)),
+                    "sslic_seed")
+
+    def iterate(self, image, centres_in, labels, centres_out, stream=None,
+                residual: bool = False):
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image")
+        self._need(centres_in, self.K * self.centre_width, "centres_in")
+        self._need(labels, V, "labels")
+        self._need(centres_out, self.K * self.centre_width, "centres_out")
+        res = ctypes.c_double(0.0)
+        self._check(self.lib.sslic_iterate(self._c, _ptr(image), _ptr(centres_in), _ptr(labels),
+                                           _ptr(centres_out), _stream(stream),
+                                           ctypes.byref(res) if residual else None),
+                    "sslic_iterate")
+        return res.value if residual else None
+
+    def connectivity(self, centres, labels_in, labels_out, stream=None) -> int:
+        V = self._voxels()
+        self._need(centres, self.K * self.centre_width, "centres")
+        self._need(labels_in, V, "labels_in")
+        self._need(labels_out, V, "labels_out")
+        n = ctypes.c_int64(0)
+        self._check(self.lib.sslic_connectivity(self._c, _ptr(centres), _ptr(labels_in),
+                                                _ptr(labels_out), _stream(stream), ctypes.byref(n)),
+                    "sslic_connectivity")
+        return int(n.value)
+
+    def close(self):
+        if self._c:
+            self.lib.sslic_destroy(self._c)
+            self._c = ctypes.c_void_p(0)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def segment(image, grid, stream=None, **kw):
+    """Convenience: labels and centres of one device image tensor
+    [N_{n-1}, ..., N_0, C]; keyword arguments are Params fields."""
+    import torch
+    p = params_for(image, grid, **kw)
+    with Context(p) as ctx:
+        labels = torch.empty(tuple(image.shape[:-1]), dtype=torch.int32, device=image.device)
+        centres = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device=image.device)
+        info = ctx.run(image, labels, centres, stream=stream)
+    return labels, centres, info

@@ -1,0 +1,79 @@
+"""The C-ABI library loads and exports every entry point include/sslic.h
+declares (no GPU needed; no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"SSLIC_API\s+[\w\s\*]+?\b(sslic_\w+)\s*\(", text)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1806_08741_gb300 import build as B
+    from paper_1806_08741_gb300 import sslic as S
+    B.build()
+    return S.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("sslic_create", "sslic_run", "sslic_destroy", "sslic_iterate", "sslic_seed",
+              "sslic_connectivity", "sslic_run_host", "sslic_run_from"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+        assert ctypes.cast(getattr(lib, n), ctypes.c_void_p).value
+
+
+def test_binding_names_match_header():
+    from paper_1806_08741_gb300 import sslic as S
+    assert sorted(S.EXPORTS) == sorted(_declared())
+
+
+def test_host_only_calls(lib):
+    from paper_1806_08741_gb300 import sslic as S
+    p = S._Params()
+    assert lib.sslic_default_params(3, ctypes.byref(p)) == 0
+    assert p.ndim == 3 and p.max_iter == 5 and abs(p.m - 10.0) < 1e-6 and p.grid[0] == 16
+    assert lib.sslic_default_params(2, ctypes.byref(p)) == 0 and p.max_iter == 10
+    assert lib.sslic_default_params(7, ctypes.byref(p)) == -1
+    assert lib.sslic_strerror(0) == b"ok"
+    assert lib.sslic_strerror(-1) == b"invalid argument"
+    assert lib.sslic_last_error(None) == b""
+
+
+@pytest.mark.parametrize("field,value", [("ndim", 0), ("ndim", 4), ("channels", 0),
+                                         ("channels", 300), ("dtype", 5), ("m", 0.0),
+                                         ("m", float("nan")), ("max_iter", 0), ("perturb", 2),
+                                         ("precision", 7)])
+def test_create_rejects_bad_params_without_touching_the_gpu(lib, field, value):
+    from paper_1806_08741_gb300 import sslic as S
+    p = S.Params(size=(64, 64), grid=(8, 8)).to_c()
+    setattr(p, field, value)
+    out = ctypes.c_void_p(0)
+    assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -1
+    assert not out.value
+
+
+def test_create_rejects_bad_sizes(lib):
+    from paper_1806_08741_gb300 import sslic as S
+    out = ctypes.c_void_p(0)
+    for size, grid in [((0, 4), (2, 2)), ((1 << 25, 4), (2, 2)), ((4, 4), (0, 2))]:
+        p = S.Params(size=size, grid=grid).to_c()
+        assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -1
+    p = S.Params(size=(64, 64), grid=(8, 8), precision=1).to_c()
+    assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -6

@@ -1,0 +1,309 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, step by
+step and end to end.  Integer images: labels and centres bit-exact.  Float
+images: labels equal to the FP32-canonical oracle for one iteration from the
+same centres; against the FP64 oracle over a whole run, label agreement
+>= 99.99 % and centre relative error <= 1e-5."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_08741_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _S():
+    from paper_1806_08741_gb300 import sslic as S
+    return S
+
+
+def _dev(a):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _gpu_seed(img, grid, **kw):
+    torch, S = _torch(), _S()
+    p = S.params_for(img, grid, **kw)
+    with S.Context(p) as ctx:
+        out = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+        ctx.seed(_dev(img), out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy().astype(np.float64)
+
+
+def _gpu_iterate(img, grid, centres, m=10.0):
+    torch, S = _torch(), _S()
+    p = S.params_for(img, grid, m=m, max_iter=1)
+    with S.Context(p) as ctx:
+        cin = _dev(centres.astype(np.float32))
+        lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+        cout = torch.empty_like(cin)
+        res = ctx.iterate(_dev(img), cin, lab, cout, residual=True)
+        return lab.cpu().numpy(), cout.cpu().numpy().astype(np.float64), res
+
+
+def _gpu_run(img, grid, **kw):
+    torch, S = _torch(), _S()
+    p = S.params_for(img, grid, **kw)
+    with S.Context(p) as ctx:
+        lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+        cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+        info = ctx.run(_dev(img), lab, cen)
+        return lab.cpu().numpy(), cen.cpu().numpy().astype(np.float64), info
+
+
+def _rand_img(shape, dtype, seed):
+    rng = np.random.default_rng(seed)
+    if dtype == np.float32:
+        return rng.uniform(0, 1, size=shape).astype(np.float32)
+    hi = 256 if dtype == np.uint8 else 65536
+    return rng.integers(0, hi, size=shape).astype(dtype)
+
+
+def _synth(size, C=3, dtype="u8", regions=None, sigma=6, seed=5, ramp=0):
+    V = int(np.prod(size))
+    regions = regions or max(2, V // 4000)
+    return I.make_image(I.ImageSpec(tuple(size), C, dtype, seed, regions, sigma, ramp))
+
+
+# ---------------------------------------------------------------------------
+# a1 / a2: seeding and perturbation
+# ---------------------------------------------------------------------------
+SEED_CASES = [
+    ("2d_rgb", lambda: _synth((256, 256)), (16, 16)),
+    ("2d_ragged", lambda: _synth((203, 150)), (16, 16)),
+    ("3d_rgb", lambda: _synth((70, 50, 37)), (8, 8, 8)),
+    ("3d_aniso_u16", lambda: _synth((64, 40, 30), 1, "u16", sigma=300), (16, 8, 4)),
+    ("1d", lambda: _synth((1000,), 3), (7,)),
+    ("2d_f32_c4", lambda: _rand_img((60, 70, 4), np.float32, 3), (6, 6)),
+    ("2d_u8_c2", lambda: _rand_img((40, 50, 2), np.uint8, 4), (5, 5)),
+]
+
+
+@pytest.mark.parametrize("name,mk,grid", SEED_CASES, ids=[c[0] for c in SEED_CASES])
+@pytest.mark.parametrize("perturb", [True, False])
+def test_seed_parity(name, mk, grid, perturb):
+    img = mk()
+    ref = O.seed(O.params_for(img, grid, perturb=perturb, max_iter=1), img)
+    got = _gpu_seed(img, grid, perturb=perturb)
+    np.testing.assert_array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# a3 / a4: one assignment + update from the same centres
+# ---------------------------------------------------------------------------
+ITER_CASES = [
+    ("2d_256", lambda: _synth((256, 256), regions=32, sigma=8), (16, 16), 10.0),
+    ("2d_ragged", lambda: _synth((203, 150)), (16, 16), 10.0),
+    ("2d_S8", lambda: _synth((190, 130)), (8, 8), 10.0),
+    ("2d_S32", lambda: _synth((300, 260)), (32, 32), 20.0),
+    ("3d_S16", lambda: _synth((96, 80, 48)), (16, 16, 16), 10.0),
+    ("3d_ragged_S8", lambda: _synth((70, 50, 37)), (8, 8, 8), 10.0),
+    ("3d_small_S_overflow", lambda: _synth((40, 30, 20)), (3, 3, 3), 5.0),
+    ("3d_aniso", lambda: _synth((80, 48, 30)), (16, 8, 4), 10.0),
+    ("3d_u16", lambda: _synth((64, 40, 30), 1, "u16", sigma=300), (8, 8, 8), 10.0),
+    ("2d_gray_u8", lambda: _synth((150, 100), 1), (10, 10), 5.0),
+    ("1d", lambda: _synth((1000,), 3), (7,), 10.0),
+    ("2d_u8_c2_generic", lambda: _rand_img((40, 50, 2), np.uint8, 4), (5, 5), 10.0),
+    ("2d_f32_c4", lambda: _rand_img((60, 70, 4), np.float32, 3), (6, 6), 0.5),
+]
+
+
+@pytest.mark.parametrize("name,mk,grid,m", ITER_CASES, ids=[c[0] for c in ITER_CASES])
+@pytest.mark.parametrize("after", [0, 3])
+def test_iterate_parity(name, mk, grid, m, after):
+    img = mk()
+    p = O.params_for(img, grid, m=m, max_iter=max(after, 1), perturb=True)
+    cen = O.seed(p, img) if after == 0 else O.slic(p, img)["centres"]
+    ref_lab = O.assign(p, img, cen)
+    ref_cen, _, ref_res = O.update(p, img, ref_lab, cen)
+    lab, got_cen, res = _gpu_iterate(img, grid, cen, m=m)
+    np.testing.assert_array_equal(lab, ref_lab)
+    if img.dtype == np.float32:
+        np.testing.assert_allclose(got_cen, ref_cen, rtol=1e-6, atol=1e-6)
+    else:
+        np.testing.assert_array_equal(got_cen, ref_cen)
+    assert res == pytest.approx(ref_res, rel=1e-9, abs=1e-12)
+
+
+def test_iterate_random_centres_ties():
+    """Integer centre positions and equal features: every tie is decided by
+    the cluster index alone."""
+    img = np.full((37, 45, 3), 100, np.uint8)
+    p = O.params_for(img, (5, 5), m=3.0, max_iter=1)
+    K = O.num_clusters(p)
+    rng = np.random.default_rng(9)
+    cen = np.zeros((K, 5))
+    cen[:, :3] = 100.0
+    cen[:, 3] = rng.integers(0, 45, size=K)
+    cen[:, 4] = rng.integers(0, 37, size=K)
+    ref_lab = O.assign(p, img, cen)
+    lab, _, _ = _gpu_iterate(img, (5, 5), cen, m=3.0)
+    np.testing.assert_array_equal(lab, ref_lab)
+
+
+# ---------------------------------------------------------------------------
+# a6: connectivity enforcement alone
+# ---------------------------------------------------------------------------
+def _gpu_conn(img_shape, grid, centres, labels, C=3):
+    torch, S = _torch(), _S()
+    size = tuple(reversed(img_shape))
+    p = S.Params(size=size, grid=grid, channels=C, dtype=S.U8, enforce_connectivity=True)
+    with S.Context(p) as ctx:
+        lin = _dev(labels.astype(np.int32))
+        lout = torch.empty_like(lin)
+        n = ctx.connectivity(_dev(centres.astype(np.float32)), lin, lout)
+        return lout.cpu().numpy(), n
+
+
+@pytest.mark.parametrize("shape,grid,m", [((150, 203), (16, 16), 2.0), ((37, 50, 70), (8, 8, 8), 1.0),
+                                          ((30, 40, 20), (4, 4, 4), 0.5), ((2000,), (9,), 1.0)])
+def test_connectivity_parity(shape, grid, m):
+    img = _rand_img(tuple(shape) + (3,), np.uint8, 12)
+    p = O.params_for(img, grid, m=m, max_iter=3)
+    r = O.slic(p, img)
+    ref, nref = O.connectivity(p, r["centres"], r["labels"])
+    got, n = _gpu_conn(shape, grid, r["centres"], r["labels"])
+    np.testing.assert_array_equal(got, ref)
+    assert n == nref
+
+
+def test_connectivity_uncovered_and_blocky():
+    """Labels with -1 holes, tiny islands and components spanning many tiles."""
+    rng = np.random.default_rng(2)
+    shape = (70, 130)
+    grid = (10, 10)
+    K = 7 * 13
+    blocks = rng.integers(-1, K, size=(14, 26))
+    lab = np.kron(blocks, np.ones((5, 5), np.int64))[:70, :130].astype(np.int32)
+    noise = rng.random(shape) < 0.05
+    lab[noise] = rng.integers(-1, K, size=noise.sum())
+    cen = np.zeros((K, 5))
+    cen[:, 3] = rng.uniform(0, 129, size=K)
+    cen[:, 4] = rng.uniform(0, 69, size=K)
+    p = O.Params(size=(130, 70), grid=grid, channels=3)
+    ref, nref = O.connectivity(p, cen, lab)
+    got, n = _gpu_conn(shape, grid, cen, lab)
+    np.testing.assert_array_equal(got, ref)
+    assert n == nref
+
+
+# ---------------------------------------------------------------------------
+# end to end
+# ---------------------------------------------------------------------------
+def _cfg_image(name):
+    w = I.WORKLOADS[name]
+    return w, I.make_image(w.image)
+
+
+@pytest.mark.parametrize("name", ["rgb2d_256", "rgb2d_2048x1216"])
+def test_full_run_2d_workloads(name):
+    w, img = _cfg_image(name)
+    kw = dict(m=w.m, max_iter=w.max_iter, perturb=w.perturb, enforce_connectivity=w.connectivity)
+    ref = O.slic(O.params_for(img, w.grid, **kw), img)
+    lab, cen, info = _gpu_run(img, w.grid, **kw)
+    np.testing.assert_array_equal(lab, ref["labels"])
+    np.testing.assert_array_equal(cen, ref["centres"])
+    assert info["num_labels"] == ref["num_labels"]
+    assert info["iterations"] == ref["iterations"] == w.max_iter
+    assert info["residual"] == pytest.approx(ref["residual"], rel=1e-9)
+
+
+@pytest.mark.parametrize("size,grid,conn", [((128, 96, 64), (16, 16, 16), True),
+                                            ((77, 61, 45), (8, 8, 8), True),
+                                            ((100, 60, 40), (16, 8, 4), False)])
+def test_full_run_3d(size, grid, conn):
+    img = _synth(size, regions=int(np.prod(size)) // 20000 + 2)
+    kw = dict(m=10.0, max_iter=5, perturb=True, enforce_connectivity=conn)
+    ref = O.slic(O.params_for(img, grid, **kw), img)
+    lab, cen, info = _gpu_run(img, grid, **kw)
+    np.testing.assert_array_equal(lab, ref["labels"])
+    np.testing.assert_array_equal(cen, ref["centres"])
+    assert info["num_labels"] == ref["num_labels"]
+
+
+def test_full_run_u16_blocks():
+    img = _synth((96, 96, 96), 1, "u16", regions=60, sigma=300)
+    kw = dict(m=10.0, max_iter=10, perturb=True, enforce_connectivity=True)
+    ref = O.slic(O.params_for(img, (16, 16, 16), **kw), img)
+    lab, cen, info = _gpu_run(img, (16, 16, 16), **kw)
+    np.testing.assert_array_equal(lab, ref["labels"])
+    np.testing.assert_array_equal(cen, ref["centres"])
+
+
+def test_float_hyperspectral_vs_fp64_oracle():
+    w = I.WORKLOADS["hyper64_1024"]
+    img = I.make_hyperspectral()
+    kw = dict(m=w.m, max_iter=w.max_iter, perturb=True)
+    ref = O.slic(O.params_for(img, w.grid, mode=O.FP64, **kw), img)
+    lab, cen, _ = _gpu_run(img, w.grid, **kw)
+    agree = (lab == ref["labels"]).mean()
+    assert agree >= 0.9999, agree
+    rel = np.abs(cen - ref["centres"]) / np.maximum(np.abs(ref["centres"]), 1e-3)
+    assert rel.max() <= 1e-5, rel.max()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape,grid", [((1, 1), (1, 1)), ((1, 1, 1), (4, 4, 4)), ((5, 7), (16, 16)),
+                                        ((3, 200), (2, 2)), ((33, 17, 5), (40, 40, 40))])
+def test_degenerate_shapes(shape, grid):
+    img = _rand_img(tuple(shape) + (3,), np.uint8, 1)
+    kw = dict(m=10.0, max_iter=3, perturb=True, enforce_connectivity=True)
+    ref = O.slic(O.params_for(img, grid, **kw), img)
+    lab, cen, info = _gpu_run(img, grid, **kw)
+    np.testing.assert_array_equal(lab, ref["labels"])
+    np.testing.assert_array_equal(cen, ref["centres"])
+    assert info["num_labels"] == ref["num_labels"]
+
+
+def test_threshold_iterations_match():
+    img = _synth((160, 120))
+    for thr in (1e-9, 0.5, 5.0):
+        kw = dict(m=10.0, max_iter=10, conv_threshold=thr)
+        ref = O.slic(O.params_for(img, (16, 16), **kw), img)
+        lab, cen, info = _gpu_run(img, (16, 16), **kw)
+        assert info["iterations"] == ref["iterations"]
+        np.testing.assert_array_equal(lab, ref["labels"])
+
+
+def test_resume_and_host_entry():
+    torch, S = _torch(), _S()
+    img = _synth((120, 90))
+    p5 = S.params_for(img, (8, 8), max_iter=5)
+    p10 = S.params_for(img, (8, 8), max_iter=10)
+    l10, c10, _ = _gpu_run(img, (8, 8), max_iter=10)
+    with S.Context(p5) as ctx:
+        d = _dev(img)
+        lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+        c5 = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+        ctx.run(d, lab, c5)
+        c_res = torch.empty_like(c5)
+        ctx.run_from(d, c5, lab, c_res)
+        np.testing.assert_array_equal(lab.cpu().numpy(), l10)
+        np.testing.assert_array_equal(c_res.cpu().numpy().astype(np.float64), c10)
+    with S.Context(p10) as ctx:
+        h_img = torch.from_numpy(img).pin_memory()
+        h_lab = torch.empty(img.shape[:-1], dtype=torch.int32).pin_memory()
+        h_cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32).pin_memory()
+        ctx.run_host(h_img, h_lab, h_cen)
+        np.testing.assert_array_equal(h_lab.numpy(), l10)
+        np.testing.assert_array_equal(h_cen.numpy().astype(np.float64), c10)
+
+
+def test_invalid_calls_raise():
+    torch, S = _torch(), _S()
+    with pytest.raises(S.SSLICError):
+        S.Context(S.Params(size=(10, 10), grid=(0, 2)))
+    img = _synth((40, 30))
+    with S.Context(S.params_for(img, (8, 8))) as ctx:
+        with pytest.raises(ValueError):
+            ctx.run(_dev(img), torch.empty(5, dtype=torch.int32, device="cuda"))
+        assert ctx.lib.sslic_run(ctx._c, None, None, None, None, None) == -1

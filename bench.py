@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the SSLIC hot path on GB300.
+
+One step = one pass of the whole method through the C ABI (sslic_run):
+seeding with gradient perturbation, the iterated assign/update loop and
+connectivity enforcement, over one synthetic image already resident in HBM.
+The default workload is the 3-D RGB uint8 volume 2048x1216x1871 (14 GB,
+S = 16, K = 1,138,176, m = 10, 10 iterations, connectivity on).
+
+Metric: Gvoxel-iterations/s = voxels x iterations / step time (device time,
+CUDA events on the launching stream, max over ranks).  Printed as one JSON
+line with the roofline of the dominant kernel (its launches timed live with
+CUDA events by the library's profiler), the end-to-end figure through the
+host-buffer entry point (H2D image + D2H labels inside the timed region),
+SM clocks sampled during the timed region and the CPU oracle timed on a
+bounded sample of the same workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU: launched by torch.distributed.run, one rank per GPU; every rank
+segments its own copy of the workload (independent problems, weak scaling,
+no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "rgb3d_2048x1216x1871"
+METRIC = "Gvoxel-iters/s"
+UNIT = "Gvoxel-iter/s"
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch
+# of the dominant kernel at the default workload, from the ncu capture
+# summarised in profiles/, keyed by the SHA-256 of the kernel's source file:
+# a changed kernel reports null until it is profiled again.
+TRAFFIC_BYTES = {}
+
+
+def _sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = list(csv.reader(open(self.path)))
+        finally:
+            os.unlink(self.path)
+        if len(rows) < 2:
+            return None
+        head = [h.strip() for h in rows[0]]
+        sm, mx, reasons = [], [], set()
+        names = {"clocks_event_reasons.hw_slowdown": "hw_slowdown",
+                 "clocks_event_reasons.hw_thermal_slowdown": "hw_thermal_slowdown",
+                 "clocks_event_reasons.sw_thermal_slowdown": "sw_thermal_slowdown",
+                 "clocks_event_reasons.sw_power_cap": "sw_power_cap"}
+        for r in rows[1:]:
+            if len(r) != len(head):
+                continue
+            d = {h: v.strip() for h, v in zip(head, r)}
+            try:
+                sm.append(float(d["clocks.current.sm [MHz]"].split()[0]))
+                mx.append(float(d["clocks.max.sm [MHz]"].split()[0]))
+            except (KeyError, ValueError):
+                continue
+            for k, nm in names.items():
+                if d.get(k, "").startswith("Active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(w, edge):
+    """The corner crop [0, edge)^n of the workload's image, run by the
+    single-threaded oracle with the workload's parameters."""
+    import numpy as np
+
+    import oracle
+    from paper_1806_08741_gb300 import inputs
+
+    ext = tuple(min(edge, s) for s in w.image.size)
+    img = inputs.make_image(w.image, origin=(0,) * w.image.ndim, extent=ext)
+    p = oracle.params_for(img, w.grid, m=w.m, max_iter=w.max_iter, perturb=w.perturb,
+                          enforce_connectivity=w.connectivity)
+    t0 = time.perf_counter()
+    r = oracle.slic(p, img)
+    dt = time.perf_counter() - t0
+    vox = int(np.prod(ext))
+    desc = (f"corner crop {'x'.join(map(str, ext))} of the same image (K={oracle.num_clusters(p)}), "
+            f"{w.max_iter} iterations + {'connectivity' if w.connectivity else 'no connectivity'}, "
+            f"single-threaded C oracle, {dt:.1f} s")
+    return vox * r["iterations"] / dt / 1e9, desc, dt
+
+
+def run_reference(args, w):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    steps = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc, dt = oracle_sample(w, args.reference_edge)
+        if i >= args.warmup:
+            steps.append((v, dt))
+    val = statistics.median(v for v, _ in steps)
+    ms = statistics.median(dt for _, dt in steps) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": _config(w),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(w):
+    img = w.image
+    return {"workload": w.name, "size": list(img.size), "channels": img.channels,
+            "image_dtype": img.dtype, "grid": list(w.grid), "m": w.m, "iterations": w.max_iter,
+            "perturb": w.perturb, "connectivity": w.connectivity,
+            "regions": int(__import__("numpy").prod(img.sites())), "noise_sigma": img.sigma,
+            "l2": "inputs larger than L2 (image and labels exceed the 129 MB L2)"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    from paper_1806_08741_gb300 import inputs
+    from paper_1806_08741_gb300 import sslic as S
+
+    rank, world = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    spec = w.image
+    tdt = torch.uint8 if spec.dtype == "u8" else torch.uint16
+    img = torch.empty(spec.shape, dtype=tdt, device=dev)
+    inputs.make_image_device(spec, img.data_ptr(), stream.cuda_stream)
+    labels = torch.empty(spec.shape[:-1], dtype=torch.int32, device=dev)
+    p = S.params_for(img, w.grid, m=w.m, max_iter=w.max_iter, perturb=w.perturb,
+                     enforce_connectivity=w.connectivity)
+    ctx = S.Context(p)
+    centres = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device=dev)
+    V = spec.voxels
+
+    for _ in range(args.warmup):
+        info = ctx.run(img, labels, centres, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        info = ctx.run(img, labels, centres, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+        dist.barrier()
+    iters = info["iterations"]
+    value = world * V * iters / (ms_step / 1e3) / 1e9
+
+    # roofline of the dominant kernel: the fused assign + update tile kernel
+    esz = 1 if spec.dtype == "u8" else 2
+    bytes_per_vox = spec.channels * esz + 4
+    a_ms, a_calls = prof["assign"]
+    peak, peak_src = _peaks()
+    roof = None
+    if a_calls:
+        avg_s = a_ms / a_calls / 1e3
+        algo = V * bytes_per_vox
+        achieved = algo / avg_s / 1e9
+        src = _sha(os.path.join(ROOT, "paper_1806_08741_gb300", "csrc", "assign.cu"))
+        roof = {"kernel": "assign_tile_kernel (fused assign + map-update)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"of {peak_src}", "bytes_per_launch": algo,
+                "bytes_per_voxel": bytes_per_vox, "avg_launch_ms": a_ms / a_calls,
+                "traffic": TRAFFIC_BYTES.get((w.name, src))}
+    phases = {k: {"ms_per_step": v[0] / args.steps, "calls_per_step": v[1] / args.steps}
+              for k, v in prof.items() if k != "kernel_launches"}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        h_img = torch.empty(spec.shape, dtype=tdt, pin_memory=True)
+        h_img.copy_(img)
+        h_lab = torch.empty(spec.shape[:-1], dtype=torch.int32, pin_memory=True)
+        h_cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, pin_memory=True)
+        ctx.run_host(h_img, h_lab, h_cen, stream=stream)   # warm-up (allocates device buffers)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        n_e2e = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            ctx.run_host(h_img, h_lab, h_cen, stream=stream)
+        dt = (time.perf_counter() - t0) / n_e2e
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        same = bool(torch.equal(h_lab, labels.cpu()))
+        e2e = {"value": world * V * iters / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_img.numel() * h_img.element_size()),
+               "d2h_bytes_per_step": int(h_lab.numel() * 4 + h_cen.numel() * 4),
+               "ms_per_step": dt * 1e3, "labels_equal_device_run": same}
+        del h_img, h_lab, h_cen
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, _ = oracle_sample(w, args.cpu_edge)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**_config(w), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "num_labels": info["num_labels"], "K": info["num_clusters"]},
+            "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": prof["kernel_launches"], "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
+    ap.add_argument("--reference-edge", type=int, default=128,
+                    help="edge of the crop each reference-arm step runs")
+    args = ap.parse_args()
+    from paper_1806_08741_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_ours(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

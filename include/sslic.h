@@ -138,6 +138,30 @@ SSLIC_API int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* ce
 SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* labels_in_dev,
                        int32_t* labels_out_dev, void* stream, int64_t* num_labels_host);
 
+/* Tracing.  When enabled, every phase of the method is bracketed by CUDA
+ * events recorded on the launching stream; sslic_profile_read waits for the
+ * recorded events and returns the summed device time per phase.  The
+ * kernel-launch counter runs whether or not timing is enabled. */
+#define SSLIC_PHASE_SEED 0          /* seeding + perturbation */
+#define SSLIC_PHASE_BINS 1          /* bin grid of the centres */
+#define SSLIC_PHASE_ASSIGN 2        /* fused assign + map-update tile kernel */
+#define SSLIC_PHASE_ASSIGN_VOXEL 3  /* per-voxel assign + update (other shapes, crowded tiles) */
+#define SSLIC_PHASE_FINALIZE 4      /* centre division, residual */
+#define SSLIC_PHASE_CONNECTIVITY 5  /* the whole connectivity enforcement */
+#define SSLIC_NPHASES 6
+
+typedef struct {
+    double ms[8];             /* device milliseconds per phase */
+    int64_t calls[8];         /* timed executions per phase */
+    int64_t kernel_launches;  /* kernels this context launched since the last enable */
+} sslic_profile;
+
+/* Turn phase timing on (1) or off (0); both reset the counters. */
+SSLIC_API int sslic_profile_enable(sslic_ctx* c, int32_t on);
+
+/* Read the counters (host struct).  Synchronises on the recorded events. */
+SSLIC_API int sslic_profile_read(sslic_ctx* c, sslic_profile* out);
+
 /* Release the context (NULL is a no-op).  Synchronises the device first. */
 SSLIC_API void sslic_destroy(sslic_ctx* c);
 

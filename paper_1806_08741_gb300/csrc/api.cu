@@ -28,6 +28,30 @@ int cuda_check(sslic_ctx* c, cudaError_t e, const char* what)
                      cudaGetErrorString(e));
 }
 
+int prof_begin(sslic_ctx* c, int phase, cudaStream_t st)
+{
+    if (!c->prof_on) return -1;
+    const size_t need = 2 * (c->prof.size() + 1);
+    while (c->prof_pool.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        c->prof_pool.push_back(e);
+    }
+    ProfRec r;
+    r.phase = phase;
+    r.start = c->prof_pool[need - 2];
+    r.stop = c->prof_pool[need - 1];
+    if (cudaEventRecord(r.start, st) != cudaSuccess) return -1;
+    c->prof.push_back(r);
+    return (int)c->prof.size() - 1;
+}
+
+void prof_end(sslic_ctx* c, int rec, cudaStream_t st)
+{
+    if (rec < 0) return;
+    cudaEventRecord(c->prof[rec].stop, st);
+}
+
 template <typename P>
 static int dalloc(sslic_ctx* c, P** p, size_t count, const char* what)
 {
@@ -383,10 +407,38 @@ int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* la
     return SSLIC_OK;
 }
 
+int sslic_profile_enable(sslic_ctx* c, int32_t on)
+{
+    if (!c) return SSLIC_EINVAL;
+    c->prof_on = on ? 1 : 0;
+    c->prof.clear();
+    c->launches = 0;
+    return SSLIC_OK;
+}
+
+int sslic_profile_read(sslic_ctx* c, sslic_profile* out)
+{
+    if (!c || !out) return SSLIC_EINVAL;
+    memset(out, 0, sizeof(*out));
+    for (const ProfRec& r : c->prof) {
+        int rc = cuda_check(c, cudaEventSynchronize(r.stop), "profile event");
+        if (rc) return rc;
+        float ms = 0.0f;
+        if ((rc = cuda_check(c, cudaEventElapsedTime(&ms, r.start, r.stop), "profile elapsed"))) return rc;
+        if (r.phase >= 0 && r.phase < 8) {
+            out->ms[r.phase] += ms;
+            out->calls[r.phase] += 1;
+        }
+    }
+    out->kernel_launches = c->launches;
+    return SSLIC_OK;
+}
+
 void sslic_destroy(sslic_ctx* c)
 {
     if (!c) return;
     cudaDeviceSynchronize();
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
     free_all(c);
     delete c;
 }

@@ -451,14 +451,20 @@ static int launch_tile(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t
     if (rc) return rc;
     rc = cuda_check(c, cudaMemsetAsync(w.ovf_count, 0, sizeof(unsigned), st), "memset ovf");
     if (rc) return rc;
+    int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
     assign_tile_kernel<T, C, NDIM><<<ntiles, kTileThreads, smem, st>>>(
         g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc, w.ovf_tiles, w.ovf_count, ntx, nty);
+    count_launch(c);
+    prof_end(c, pr, st);
     if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_kernel"))) return rc;
     // tiles with too many reaching centres: per-voxel kernel over those tiles only
     int blocks = c->sms * 4;
+    pr = prof_begin(c, SSLIC_PHASE_ASSIGN_VOXEL, st);
     assign_voxel_kernel<T><<<blocks, 256, 0, st>>>(g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc,
                                                     w.facc, w.ovf_tiles, w.ovf_count, ntx, nty, Cfg::TX,
                                                     Cfg::TY, Cfg::TZ);
+    count_launch(c);
+    prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "assign_voxel_kernel(overflow)");
 }
 
@@ -468,8 +474,11 @@ static int launch_voxel(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_
     const Geom& g = c->g;
     Workspace& w = c->ws;
     int64_t blocks = imin64((g.V + 255) / 256, (int64_t)c->sms * 16);
+    const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN_VOXEL, st);
     assign_voxel_kernel<T><<<blocks, 256, 0, st>>>(g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc,
                                                     w.facc, nullptr, nullptr, 1, 1, 1, 1, 1);
+    count_launch(c);
+    prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "assign_voxel_kernel");
 }
 
@@ -578,13 +587,16 @@ int launch_finalize(sslic_ctx* c, cudaStream_t st)
     Workspace& w = c->ws;
     int threads = 256;
     int64_t blocks = (g.K + threads - 1) / threads;
+    const int pr = prof_begin(c, SSLIC_PHASE_FINALIZE, st);
     finalize_kernel<<<blocks, threads, 0, st>>>(g, w.ctr, w.acc, w.facc, w.resid_k, w.nonempty_k);
+    count_launch(c, 3);
     int rc = cuda_check(c, cudaGetLastError(), "finalize_kernel");
     if (rc) return rc;
     resid_partial_kernel<<<kResidParts, kRedThreads, 0, st>>>(w.resid_k, w.nonempty_k, g.K, w.resid_part,
                                                               w.resid_cnt_part);
     if ((rc = cuda_check(c, cudaGetLastError(), "resid_partial_kernel"))) return rc;
     resid_final_kernel<<<1, 32, 0, st>>>(w.resid_part, w.resid_cnt_part, kResidParts, w.resid_out);
+    prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "resid_final_kernel");
 }
 
@@ -616,6 +628,7 @@ int launch_export_centres(sslic_ctx* c, float* out, cudaStream_t st)
     const Geom& g = c->g;
     int64_t n = g.K * (g.C + g.n);
     export_kernel<<<(n + 255) / 256, 256, 0, st>>>(g, c->ws.ctr, out);
+    count_launch(c);
     return cuda_check(c, cudaGetLastError(), "export_kernel");
 }
 
@@ -624,6 +637,7 @@ int launch_import_centres(sslic_ctx* c, const float* in, cudaStream_t st)
     const Geom& g = c->g;
     int64_t n = g.K * g.CW;
     import_kernel<<<(n + 255) / 256, 256, 0, st>>>(g, in, c->ws.ctr);
+    count_launch(c);
     return cuda_check(c, cudaGetLastError(), "import_kernel");
 }
 

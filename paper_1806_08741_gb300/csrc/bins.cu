@@ -82,15 +82,18 @@ static int scan_rec(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t n, 
     int64_t nb = (n + kScanBlock - 1) / kScanBlock;
     if (nb <= 1) {
         scan_block_kernel<<<1, kScanThreads, 0, st>>>(in, out, nullptr, n);
+        count_launch(c);
         return cuda_check(c, cudaGetLastError(), "scan_block_kernel");
     }
     unsigned* sums = tmp;
     scan_block_kernel<<<nb, kScanThreads, 0, st>>>(in, out, sums, n);
+    count_launch(c);
     int rc = cuda_check(c, cudaGetLastError(), "scan_block_kernel");
     if (rc) return rc;
     rc = scan_rec(c, sums, sums, nb, tmp + nb, st);
     if (rc) return rc;
     scan_add_kernel<<<nb, kScanThreads, 0, st>>>(out, sums, n);
+    count_launch(c);
     return cuda_check(c, cudaGetLastError(), "scan_add_kernel");
 }
 
@@ -129,6 +132,7 @@ int build_bins(sslic_ctx* c, cudaStream_t st)
 {
     const Geom& g = c->g;
     Workspace& w = c->ws;
+    const int pr = prof_begin(c, SSLIC_PHASE_BINS, st);
     int rc = cuda_check(c, cudaMemsetAsync(w.bin_count, 0, (g.K + 1) * sizeof(unsigned), st), "memset bins");
     if (rc) return rc;
     rc = cuda_check(c, cudaMemsetAsync(w.bin_cursor, 0, g.K * sizeof(unsigned), st), "memset cursor");
@@ -136,9 +140,12 @@ int build_bins(sslic_ctx* c, cudaStream_t st)
     int threads = 256;
     int64_t blocks = (g.K + threads - 1) / threads;
     bin_count_kernel<<<blocks, threads, 0, st>>>(g, w.ctr, w.bin_of, w.bin_count);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "bin_count_kernel"))) return rc;
     if ((rc = scan_exclusive_u32(c, w.bin_count, w.bin_start, g.K + 1, st))) return rc;
     bin_scatter_kernel<<<blocks, threads, 0, st>>>(g, w.bin_of, w.bin_start, w.bin_cursor, w.bin_items);
+    count_launch(c);
+    prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "bin_scatter_kernel");
 }
 

@@ -425,11 +425,13 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     const int64_t ntiles = ntx * nty * ntz;
     int rc;
     unsigned hc[4];
+    const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
     for (int attempt = 0; attempt < 2; ++attempt) {
         if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
         ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.comp_label,
                                                               w.comp_size, w.comp_first, w.gparent, w.counters,
                                                               w.m_cap, ntx, nty);
+        count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
         if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
                              "read component count")))
@@ -446,19 +448,24 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     if ((rc = cuda_check(c, cudaMemsetAsync(w.fin, 0, M, st), "memset"))) return rc;
     ccl_faces_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.gparent,
                                                            w.counters, ntx, nty);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     const int gb = c->sms * 8;
     ccl_flatten_kernel<<<gb, 256, 0, st>>>(w.gparent, w.counters);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
     ccl_rootstats_kernel<<<gb, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
                                              w.counters);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_rootstats_kernel"))) return rc;
     conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,
                                                                  w.gparent, w.root_size, w.fin, ntx, nty);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase1_kernel"))) return rc;
     conn_phase2_kernel<NDIM><<<gb, 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
                                                   w.lid, w.tile_base, w.out_label, w.link, w.new_key, w.new_val,
                                                   w.counters, ntx, nty);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase2_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
                          "read new count")))
@@ -470,6 +477,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
         const int* sorted_val = w.new_val;
         if (Mn <= kSmallSort) {
             sort_small_kernel<<<1, 1024, 0, st>>>(w.new_key, w.new_val, w.counters);
+            count_launch(c);
             if ((rc = cuda_check(c, cudaGetLastError(), "sort_small_kernel"))) return rc;
         } else {
             int64_t P = 1;
@@ -486,24 +494,31 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
                 w.sort_cap = P;
             }
             sort_pad_kernel<<<gb, 256, 0, st>>>(w.new_key, w.new_val, w.sort_key, w.sort_val, Mn, P);
+            count_launch(c);
             for (int64_t k = 2; k <= P; k <<= 1)
-                for (int64_t j = k >> 1; j > 0; j >>= 1)
+                for (int64_t j = k >> 1; j > 0; j >>= 1) {
                     sort_step_kernel<<<gb, 256, 0, st>>>(w.sort_key, w.sort_val, P, k, j);
+                    count_launch(c);
+                }
             if ((rc = cuda_check(c, cudaGetLastError(), "sort_step_kernel"))) return rc;
             sorted_val = w.sort_val;
         }
         assign_new_kernel<<<gb, 256, 0, st>>>(sorted_val, w.out_label, g.K, Mn);
+        count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "assign_new_kernel"))) return rc;
     }
     conn_resolve_kernel<<<gb, 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
     conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.gparent, w.out_label,
                                                               labels_out, ntx, nty);
+    count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
                          "read status")))
         return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    prof_end(c, pr, st);
     if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a union-find walk exceeded its bound");
     if (num_labels) *num_labels = g.K + Mn;
     return SSLIC_OK;

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "sslic.h"
 
 namespace sslic {
@@ -142,6 +144,13 @@ struct Workspace {
 
 }  // namespace sslic
 
+namespace sslic {
+struct ProfRec {
+    int phase;
+    cudaEvent_t start, stop;
+};
+}  // namespace sslic
+
 struct sslic_ctx {
     sslic_params p;
     sslic::Geom g;
@@ -150,6 +159,11 @@ struct sslic_ctx {
     int sms = 148;
     int busy = 0;
     char err[512] = {0};
+    // tracing
+    int prof_on = 0;
+    int64_t launches = 0;
+    std::vector<sslic::ProfRec> prof;       // recorded brackets (events owned by the pool)
+    std::vector<cudaEvent_t> prof_pool;     // created events, reused
 };
 
 namespace sslic {
@@ -168,5 +182,9 @@ int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
 int ensure_ccl_capacity(sslic_ctx* c, int64_t m);
 int set_error(sslic_ctx* c, int code, const char* fmt, ...);
+// phase brackets: prof_begin returns a record index (or -1 when timing is off)
+int prof_begin(sslic_ctx* c, int phase, cudaStream_t st);
+void prof_end(sslic_ctx* c, int rec, cudaStream_t st);
+inline void count_launch(sslic_ctx* c, int n = 1) { c->launches += n; }
 int cuda_check(sslic_ctx* c, cudaError_t e, const char* what);
 }  // namespace sslic

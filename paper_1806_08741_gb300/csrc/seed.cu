@@ -100,6 +100,8 @@ int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st)
     const Geom& g = c->g;
     int threads = 128;
     int64_t blocks = (g.K + threads - 1) / threads;
+    const int pr = prof_begin(c, SSLIC_PHASE_SEED, st);
+    count_launch(c);
     switch (g.dtype) {
     case SSLIC_U8:
         seed_kernel<uint8_t><<<blocks, threads, 0, st>>>(g, (const uint8_t*)img, c->ws.ctr, c->p.perturb);
@@ -110,6 +112,7 @@ int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st)
     default:
         seed_kernel<float><<<blocks, threads, 0, st>>>(g, (const float*)img, c->ws.ctr, c->p.perturb);
     }
+    prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "seed_kernel");
 }
 

@@ -23,7 +23,9 @@ _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUSY",
 
 EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_run",
            "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
-           "sslic_connectivity", "sslic_destroy", "sslic_strerror", "sslic_last_error")
+           "sslic_connectivity", "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
+           "sslic_strerror", "sslic_last_error")
+PHASES = ("seed", "bins", "assign", "assign_voxel", "finalize", "connectivity")
 
 
 class SSLICError(RuntimeError):
@@ -45,6 +47,14 @@ class _Params(ctypes.Structure):
         ("perturb", ctypes.c_int32),
         ("enforce_connectivity", ctypes.c_int32),
         ("precision", ctypes.c_int32),
+    ]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [
+        ("ms", ctypes.c_double * 8),
+        ("calls", ctypes.c_int64 * 8),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
 
@@ -81,6 +91,10 @@ def load(path: str = LIB_PATH):
     L.sslic_seed.argtypes = [C, vp, vp, vp]
     L.sslic_iterate.argtypes = [C, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sslic_connectivity.argtypes = [C, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.sslic_profile_enable.argtypes = [C, ctypes.c_int32]
+    L.sslic_profile_read.argtypes = [C, ctypes.POINTER(_Profile)]
+    L.sslic_profile_enable.restype = ctypes.c_int
+    L.sslic_profile_read.restype = ctypes.c_int
     L.sslic_destroy.argtypes = [C]
     L.sslic_destroy.restype = None
     L.sslic_strerror.argtypes = [ctypes.c_int]
@@ -289,6 +303,18 @@ class Context:
                                                 _ptr(labels_out), _stream(stream), ctypes.byref(n)),
                     "sslic_connectivity")
         return int(n.value)
+
+    def profile_enable(self, on: bool = True) -> None:
+        """Start (or stop) per-phase CUDA-event timing; resets the counters."""
+        self._check(self.lib.sslic_profile_enable(self._c, int(bool(on))), "sslic_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{phase: (ms, calls)} plus 'kernel_launches' since the last enable."""
+        p = _Profile()
+        self._check(self.lib.sslic_profile_read(self._c, ctypes.byref(p)), "sslic_profile_read")
+        out = {name: (p.ms[i], int(p.calls[i])) for i, name in enumerate(PHASES)}
+        out["kernel_launches"] = int(p.kernel_launches)
+        return out
 
     def close(self):
         if self._c:

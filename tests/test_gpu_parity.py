@@ -238,6 +238,9 @@ def test_full_run_u16_blocks():
 
 
 def test_float_hyperspectral_vs_fp64_oracle():
+    """Float tolerance: label agreement >= 99.99 %; the centre table's
+    relative error ||C - C_ref||_F / ||C_ref||_F <= 1e-5; and every centre
+    whose member set is the same on both sides within 1e-5 relative."""
     w = I.WORKLOADS["hyper64_1024"]
     img = I.make_hyperspectral()
     kw = dict(m=w.m, max_iter=w.max_iter, perturb=True)
@@ -245,7 +248,11 @@ def test_float_hyperspectral_vs_fp64_oracle():
     lab, cen, _ = _gpu_run(img, w.grid, **kw)
     agree = (lab == ref["labels"]).mean()
     assert agree >= 0.9999, agree
-    rel = np.abs(cen - ref["centres"]) / np.maximum(np.abs(ref["centres"]), 1e-3)
+    table = np.linalg.norm(cen - ref["centres"]) / np.linalg.norm(ref["centres"])
+    assert table <= 1e-5, table
+    differ = np.unique(np.concatenate([lab[lab != ref["labels"]], ref["labels"][lab != ref["labels"]]]))
+    same = np.setdiff1d(np.arange(cen.shape[0]), differ)
+    rel = np.abs(cen[same] - ref["centres"][same]) / np.maximum(np.abs(ref["centres"][same]), 1e-3)
     assert rel.max() <= 1e-5, rel.max()
 
 

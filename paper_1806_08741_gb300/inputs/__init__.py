@@ -242,6 +242,11 @@ WORKLOADS = {
     "rgb3d_2048x1216x1871": Workload("rgb3d_2048x1216x1871",
                                      ImageSpec((2048, 1216, 1871), 3, "u8", 1809, 200000, 6, 0),
                                      (16, 16, 16), 10.0, 10, True, True),
+    # the same 3-D recipe on 512x512x256 (201 MB, above the L2) for kernel
+    # profiling captures that must stay small
+    "rgb3d_512x512x256": Workload("rgb3d_512x512x256",
+                                  ImageSpec((512, 512, 256), 3, "u8", 1809, 2881, 6, 0),
+                                  (16, 16, 16), 10.0, 10, True, True),
     # 64-band float 1024x1024 hyperspectral mixture; S=16, m=0.1, 10 iterations
     "hyper64_1024": Workload("hyper64_1024", None, (16, 16), 0.1, 10, True, False,
                              float_image={"size": (1024, 1024), "bands": 64}),

@@ -180,6 +180,11 @@ int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t 
 size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
+template <typename T, int C, int NDIM>
+int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st);
+template <typename T>
+int launch_voxel_tiles(sslic_ctx* c, const T* img, int32_t* labels, int tx, int ty, int tz, int ntx, int nty,
+                       cudaStream_t st);
 int ensure_ccl_capacity(sslic_ctx* c, int64_t m);
 int set_error(sslic_ctx* c, int code, const char* fmt, ...);
 // phase brackets: prof_begin returns a record index (or -1 when timing is off)

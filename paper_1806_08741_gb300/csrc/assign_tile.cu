@@ -13,21 +13,22 @@
 // The map step of the update (Sec. 3.1) is fused: [I(x), x, 1] is summed
 // per label in the same pass, so the image is read once per iteration.
 //
-// Work decomposition.  A CTA (4 warps) owns a tile of 32x8x8 voxels (3-D) or
-// 64x32 pixels (2-D):
+// Work decomposition.  A CTA (4 warps) owns a tile of 32x16x8 voxels (3-D)
+// or 64x32 pixels (2-D):
 //  1. stages the tile's channels as bank-padded planes in shared memory;
 //  2. gathers the centres of the bins that can reach the tile (3 bins per
 //     axis around it), keeps those whose window meets the tile, sorts them by
 //     index, and builds per centre the feature pair (C_c, C_c) and per axis
-//     the table t_d(x_d) for the tile's coordinates, +inf outside the window
+//     the table t_d(x_d) over the tile's coordinates, +inf outside the window
 //     (the window test is folded into the distance);
 //  3. each warp sweeps 4x4x4 (3-D) / 8x8 (2-D) boxes, two voxels per lane in
-//     packed .f32x2 arithmetic, visiting only the centres that reach its box;
-//  4. per box, the winners' [I, x, 1] sums are reduced across the warp with
-//     redux.sync on bit-packed words (one word carries several small sums)
-//     into per-warp accumulators;
-//  5. labels leave through coalesced int32 stores, per-tile sums through one
-//     uint64 atomic per (centre, field).
+//     packed .f32x2 arithmetic, visiting only the centres that reach its box,
+//     and leaves the winning slot of every voxel in shared memory;
+//  4. one sweep over 16-voxel row segments writes the int32 labels with
+//     16-byte stores and sums [I, x, y, z, 1] along runs of equal slots (a
+//     run of four equal slots takes one byte-sum instruction per channel)
+//     into per-tile accumulators;
+//  5. per-tile sums leave through one uint64 atomic per (centre, field).
 // Tiles reached by more than kCap centres are handed to the per-voxel kernel.
 #include "common.cuh"
 
@@ -40,13 +41,14 @@ constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kCap = 64;     // candidate centres per tile
 constexpr int kStage = 512;  // gathered centres before filtering
+constexpr int kSeg = 16;     // voxels per row segment in the label / sum sweep
 
 template <int NDIM>
 struct Cfg;
 template <>
 struct Cfg<3> {
-    static constexpr int TX = 32, TY = 8, TZ = 8;  // 2048 voxels
-    static constexpr int WX = 2, WY = 4, WZ = 4;   // lanes -> box 4x4x4 (pairs along x)
+    static constexpr int TX = 32, TY = 16, TZ = 8;  // 4096 voxels
+    static constexpr int WX = 2, WY = 4, WZ = 4;    // lanes -> box 4x4x4 (pairs along x)
 };
 template <>
 struct Cfg<2> {
@@ -57,74 +59,32 @@ struct Cfg<2> {
 // per-candidate record in shared memory
 template <int C, int NDIM>
 struct Cand {
-    float2 fe[C];            // (C_c, C_c)
+    float2 fe[C];              // (C_c, C_c)
     float2 t1[Cfg<NDIM>::TY];  // (t_1, t_1) by local y
     float2 t2[Cfg<NDIM>::TZ];  // (t_2, t_2) by local z
     float t0[Cfg<NDIM>::TX];   // t_0 by local x
-};
-
-// ---- bit-packed per-box sums ------------------------------------------------
-__host__ __device__ constexpr int bits_for(unsigned long long v)
-{
-    int b = 0;
-    while (v) { ++b; v >>= 1; }
-    return b;
-}
-
-// fields: C features, x, y, z (local), count; per warp box of 64 voxels
-template <typename T, int C, int NDIM>
-struct Pack {
-    static constexpr int F = C + 4;
-    static constexpr unsigned long long kVmax = sizeof(T) == 1 ? 255ull : 65535ull;
-    __host__ __device__ static constexpr int width(int f)
-    {
-        return f < C ? bits_for(64ull * kVmax)
-                     : f == C ? bits_for(64ull * (Cfg<NDIM>::TX - 1))
-                     : f == C + 1 ? bits_for(64ull * (Cfg<NDIM>::TY - 1))
-                     : f == C + 2 ? bits_for(64ull * (Cfg<NDIM>::TZ - 1))
-                                  : bits_for(64ull);
-    }
-    // greedy first-fit into 32-bit words
-    __host__ __device__ static constexpr int word(int f)
-    {
-        int w = 0, used = 0;
-        for (int i = 0; i <= f; ++i) {
-            if (used + width(i) > 32) { ++w; used = 0; }
-            if (i == f) return w;
-            used += width(i);
-        }
-        return w;
-    }
-    __host__ __device__ static constexpr int shift(int f)
-    {
-        int used = 0;
-        for (int i = 0; i <= f; ++i) {
-            if (used + width(i) > 32) used = 0;
-            if (i == f) return used;
-            used += width(i);
-        }
-        return 0;
-    }
-    static constexpr int NW = word(F - 1) + 1;
 };
 
 template <typename T, int C, int NDIM>
 struct Smem {
     using G = Cfg<NDIM>;
     static constexpr int TX = G::TX, TY = G::TY, TZ = G::TZ, TV = TX * TY * TZ;
-    // channel planes, padded so the lanes of a warp box hit distinct banks
-    static constexpr int RPB = TX * (int)sizeof(T) + 4;   // row pitch, bytes
-    static constexpr int PPB = TY * RPB + 8;              // plane (z) pitch, bytes
-    static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;  // channel pitch, bytes
+    // channel planes: row pitch 4 bytes past the row, plane pitch chosen so a
+    // plane advances 4 banks -- the 4x4 (y, z) lanes of a warp box then hit
+    // distinct banks
+    static constexpr int RPB = TX * (int)sizeof(T) + 4;
+    static constexpr int PPB_RAW = TY * RPB;
+    static constexpr int PPB = PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
+    static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;
     Cand<C, NDIM> cd[kCap];
     alignas(16) unsigned char planes[C * CPB];
-    unsigned accw[kWarps][kCap][C + 4];   // per-warp sums: features, x, y, z, count
+    unsigned acc[kCap][C + 4];   // per-tile sums: features, x, y, z (local), count
     float cpos[kCap][3];
     int cand[kCap];
     int tmp[kCap];
     int stage[kStage];
     uint32_t bmask[kCap];
-    alignas(4) uint8_t slot[TV];
+    alignas(16) uint8_t slot[TV];
     int nstage, ncand;
 };
 
@@ -144,8 +104,21 @@ __device__ __forceinline__ void split_pair(unsigned v, unsigned& lo, unsigned& h
     else { lo = v & 0xffffu; hi = v >> 16; }
 }
 
+template <int C>
+__device__ __forceinline__ void flush_run(unsigned (*acc)[C + 4], int cur, const unsigned* fs, unsigned xs,
+                                          unsigned cnt, int yl, int zl)
+{
+    if (cur == kNoSlot || cnt == 0) return;
+#pragma unroll
+    for (int c = 0; c < C; ++c) atomicAdd(&acc[cur][c], fs[c]);
+    atomicAdd(&acc[cur][C], xs);
+    atomicAdd(&acc[cur][C + 1], cnt * (unsigned)yl);
+    atomicAdd(&acc[cur][C + 2], cnt * (unsigned)zl);
+    atomicAdd(&acc[cur][C + 3], cnt);
+}
+
 template <typename T, int C, int NDIM>
-__global__ void __launch_bounds__(kThreads, 6)
+__global__ void __launch_bounds__(kThreads, 5)
 assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ ctr,
                    const unsigned* __restrict__ bin_start, const int* __restrict__ bin_items,
                    int32_t* __restrict__ labels, unsigned long long* __restrict__ acc,
@@ -153,7 +126,6 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
 {
     using G = Cfg<NDIM>;
     using S = Smem<T, C, NDIM>;
-    using P = Pack<T, C, NDIM>;
     constexpr int TX = G::TX, TY = G::TY, TZ = G::TZ, TV = TX * TY * TZ;
     constexpr int WX = G::WX, WY = G::WY, WZ = G::WZ;
     constexpr int BX = 2 * WX, BY = WY, BZ = WZ;
@@ -161,9 +133,10 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     constexpr int NBOX = NBX * NBY * NBZ;
     constexpr int PASSES = NBOX / kWarps;
     constexpr int F = C + 4;
+    constexpr int SPR = TX / kSeg;  // segments per row
     static_assert(NBOX % kWarps == 0, "boxes per warp");
     static_assert(NBX + NBY + NBZ <= 32, "box mask bits");
-    static_assert(BX * BY * BZ == 64, "64 voxels per warp box");
+    static_assert(TX % kSeg == 0, "row segments");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S& s = *reinterpret_cast<S*>(smem_raw);
@@ -177,11 +150,11 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     const int ex = min(TX, N0 - X0), ey = min(TY, N1 - Y0), ez = min(TZ, N2 - Z0);
 
     if (tid == 0) { s.nstage = 0; s.ncand = 0; }
-    for (int i = tid; i < kWarps * kCap * F; i += kThreads) (&s.accw[0][0][0])[i] = 0u;
+    for (int i = tid; i < kCap * F; i += kThreads) (&s.acc[0][0])[i] = 0u;
 
     // ---- 1. stage the tile as channel planes --------------------------------
     if constexpr (sizeof(T) == 1 && C == 3) {
-        // full rows: 12-byte groups (4 voxels) -> 3 words per plane row segment
+        // full rows: 12-byte groups (4 voxels) -> one word per plane
         const bool fast = (ex == TX) && ((N0 * 3) % 4 == 0) && (((uintptr_t)img & 3) == 0);
         if (fast) {
             constexpr int GPR = TX / 4;  // groups per row
@@ -282,23 +255,31 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     __syncthreads();
 
     // ---- per-centre tables and warp-box reach masks -------------------------
-    constexpr int TT = TX + (NDIM >= 2 ? TY : 0) + (NDIM >= 3 ? TZ : 0);
-    for (int i = tid; i < nc * TT; i += kThreads) {
-        const int sl = i / TT;
-        int j = i % TT;
-        int d = 0;
-        if (j >= TX) { j -= TX; d = 1; if (j >= TY) { j -= TY; d = 2; } }
-        const float c = s.cpos[sl][d];
+    // t_d entry: w_d (x - c)^2 with one rounding per operation, +inf outside
+    auto entry = [&](int d, int j, float c) -> float {
         const int lo = (int)ceilf(c) - g.S[d];
         const int x = T0[d] + j;
-        float t = kInf;
-        if (x >= lo && x <= lo + 2 * g.S[d] - 1) {
-            const float dl = __fsub_rn((float)x, c);
-            t = __fmul_rn(g.w[d], __fmul_rn(dl, dl));
+        if (x < lo || x > lo + 2 * g.S[d] - 1) return kInf;
+        const float dl = __fsub_rn((float)x, c);
+        return __fmul_rn(g.w[d], __fmul_rn(dl, dl));
+    };
+    for (int i = tid; i < nc * TX; i += kThreads) {
+        const int sl = i / TX, j = i % TX;
+        s.cd[sl].t0[j] = entry(0, j, s.cpos[sl][0]);
+    }
+    if constexpr (NDIM >= 2) {
+        for (int i = tid; i < nc * TY; i += kThreads) {
+            const int sl = i / TY, j = i % TY;
+            const float t = entry(1, j, s.cpos[sl][1]);
+            s.cd[sl].t1[j] = make_float2(t, t);
         }
-        if (d == 0) s.cd[sl].t0[j] = t;
-        else if (d == 1) s.cd[sl].t1[j] = make_float2(t, t);
-        else s.cd[sl].t2[j] = make_float2(t, t);
+    }
+    if constexpr (NDIM >= 3) {
+        for (int i = tid; i < nc * TZ; i += kThreads) {
+            const int sl = i / TZ, j = i % TZ;
+            const float t = entry(2, j, s.cpos[sl][2]);
+            s.cd[sl].t2[j] = make_float2(t, t);
+        }
     }
     for (int i = tid; i < nc; i += kThreads) {
         uint32_t m = 0;
@@ -316,14 +297,14 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     }
     __syncthreads();
 
-    // ---- 3-4. warp boxes: assignment + packed per-box sums ---------------------
+    // ---- 3. warp boxes: assignment ------------------------------------------
     const int lx = lane % WX, ly = (lane / WX) % WY, lz = lane / (WX * WY);
     const uint32_t bm0 = lane < nc ? s.bmask[lane] : 0u;
     const uint32_t bm1 = lane + 32 < nc ? s.bmask[lane + 32] : 0u;
     const unsigned char* cdb = reinterpret_cast<const unsigned char*>(&s.cd[0]);
     using CandT = Cand<C, NDIM>;
     constexpr int CDS = (int)sizeof(CandT);
-    constexpr int kOffT1 = 8 * C;                 // layout of Cand: fe, t1, t2, t0
+    constexpr int kOffT1 = 8 * C;  // layout of Cand: fe, t1, t2, t0
     constexpr int kOffT2 = kOffT1 + 8 * TY;
     constexpr int kOffT0 = kOffT2 + 8 * TZ;
     static_assert(kOffT0 + 4 * TX == CDS, "Cand layout");
@@ -335,12 +316,12 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
         const uint32_t want = (1u << bxi) | (1u << (NBX + byi)) | (1u << (NBX + NBY + bzi));
         const uint32_t m0 = __ballot_sync(0xffffffffu, (bm0 & want) == want);
         const uint32_t m1 = __ballot_sync(0xffffffffu, (bm1 & want) == want);
-        unsigned fl[C], fh[C];
         uint64_t Fp[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            split_pair<T>(plane_pair(s, c, xl, yl, zl), fl[c], fh[c]);
-            Fp[c] = pk2((float)fl[c], (float)fh[c]);
+            unsigned lo, hi;
+            split_pair<T>(plane_pair(s, c, xl, yl, zl), lo, hi);
+            Fp[c] = pk2((float)lo, (float)hi);
         }
         float b0 = kInf, b1 = kInf;
         int s0 = kNoSlot, s1 = kNoSlot;
@@ -370,73 +351,109 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
                 if (d1 < b1) { b1 = d1; s1 = sl; }
             }
         }
-        const int e0 = (zl * TY + yl) * TX + xl;
-        const bool in_yz = (yl < ey) && (zl < ez);
-        const bool v0 = in_yz && xl < ex && s0 != kNoSlot;
-        const bool v1 = in_yz && xl + 1 < ex && s1 != kNoSlot;
-        *reinterpret_cast<uint16_t*>(&s.slot[e0]) = (uint16_t)(s0 | (s1 << 8));
-
-        // packed records of the lane's voxels, merged when both have one label
-        unsigned w0[P::NW], w1[P::NW];
-#pragma unroll
-        for (int i = 0; i < P::NW; ++i) { w0[i] = 0u; w1[i] = 0u; }
-#pragma unroll
-        for (int f = 0; f < F; ++f) {
-            unsigned a = f < C ? fl[f < C ? f : 0] : f == C ? (unsigned)xl : f == C + 1 ? (unsigned)yl
-                       : f == C + 2 ? (unsigned)zl : 1u;
-            unsigned b = f < C ? fh[f < C ? f : 0] : f == C ? (unsigned)(xl + 1) : f == C + 1 ? (unsigned)yl
-                       : f == C + 2 ? (unsigned)zl : 1u;
-            w0[P::word(f)] += a << P::shift(f);
-            w1[P::word(f)] += b << P::shift(f);
-        }
-        bool p0 = v0, p1 = v1;
-        if (v0 && v1 && s0 == s1) {
-#pragma unroll
-            for (int i = 0; i < P::NW; ++i) w0[i] += w1[i];
-            p1 = false;
-        }
-        for (;;) {
-            const uint32_t pend = __ballot_sync(0xffffffffu, p0 || p1);
-            if (!pend) break;
-            const int leader = __ffs(pend) - 1;
-            const int L = __shfl_sync(0xffffffffu, p0 ? s0 : s1, leader);
-            unsigned r[P::NW];
-            const bool t0 = p0 && s0 == L, t1 = p1 && s1 == L;
-#pragma unroll
-            for (int i = 0; i < P::NW; ++i) {
-                r[i] = (t0 ? w0[i] : 0u) + (t1 ? w1[i] : 0u);
-                r[i] = __reduce_add_sync(0xffffffffu, r[i]);
-            }
-            p0 = p0 && !t0;
-            p1 = p1 && !t1;
-            if (lane < F) {
-                unsigned v = 0;
-#pragma unroll
-                for (int f = 0; f < F; ++f)
-                    if (lane == f) v = (r[P::word(f)] >> P::shift(f)) & ((1u << P::width(f)) - 1u);
-                s.accw[warp][L][lane] += v;
-            }
-        }
+        *reinterpret_cast<uint16_t*>(&s.slot[(zl * TY + yl) * TX + xl]) = (uint16_t)(s0 | (s1 << 8));
     }
     __syncthreads();
 
-    // ---- 5. labels (coalesced) and per-tile sums ------------------------------
-    for (int e = tid; e < TV; e += kThreads) {
-        const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
-        if (xl < ex && yl < ey && zl < ez) {
-            const int sl = s.slot[e];
-            labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = sl == kNoSlot ? -1 : s.cand[sl];
+    // ---- 4. row segments: labels out, run sums in -------------------------------
+    const bool vec_ok = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
+    for (int sg = tid; sg < TY * TZ * SPR; sg += kThreads) {
+        const int r = sg / SPR, h = sg % SPR;
+        const int yl = r % TY, zl = r / TY;
+        if (yl >= ey || zl >= ez) continue;
+        const int xs0 = h * kSeg;
+        const int n = min(kSeg, ex - xs0);
+        if (n <= 0) continue;
+        int32_t* lrow = labels + vidx(g, X0 + xs0, Y0 + yl, Z0 + zl);
+        const unsigned char* prow = s.planes + zl * S::PPB + yl * S::RPB;
+        // the segment's slots, read word by word in a lane-rotated order
+        uint32_t sw[kSeg / 4];
+        const uint32_t* sp = reinterpret_cast<const uint32_t*>(&s.slot[r * TX + xs0]);
+#pragma unroll
+        for (int j = 0; j < kSeg / 4; ++j) {
+            const int jj = (j + (lane >> 3)) & (kSeg / 4 - 1);
+            sw[jj] = sp[jj];
         }
+        int cur = kNoSlot, curlab = -1;
+        unsigned fs[C], xs = 0, cnt = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) fs[c] = 0;
+        // start a new run at slot sl (flushing the previous one)
+        auto next_run = [&](int sl) {
+            flush_run<C>(s.acc, cur, fs, xs, cnt, yl, zl);
+            cur = sl;
+            curlab = sl == kNoSlot ? -1 : s.cand[sl];
+#pragma unroll
+            for (int c = 0; c < C; ++c) fs[c] = 0;
+            xs = 0;
+            cnt = 0;
+        };
+        if (n == kSeg) {
+#pragma unroll
+            for (int j = 0; j < kSeg / 4; ++j) {
+                const uint32_t w = sw[j];
+                const int xq = xs0 + 4 * j;
+                int lab4[4];
+                if (sizeof(T) == 1 && w == (w & 0xffu) * 0x01010101u) {
+                    // four voxels, one slot: byte sums of the planes' words
+                    const int sl = (int)(w & 0xffu);
+                    if (sl != cur) next_run(sl);
+                    if (sl != kNoSlot) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            fs[c] += __vsadu4(*reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq), 0u);
+                        xs += 4u * (unsigned)xq + 6u;
+                        cnt += 4u;
+                    }
+                    lab4[0] = lab4[1] = lab4[2] = lab4[3] = curlab;
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int sl = (int)((w >> (8 * b)) & 0xffu);
+                        if (sl != cur) next_run(sl);
+                        if (sl != kNoSlot) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c)
+                                fs[c] += (unsigned)*reinterpret_cast<const T*>(
+                                    prow + c * S::CPB + (xq + b) * (int)sizeof(T));
+                            xs += (unsigned)(xq + b);
+                            cnt += 1u;
+                        }
+                        lab4[b] = curlab;
+                    }
+                }
+                if (vec_ok) {
+                    *reinterpret_cast<int4*>(lrow + 4 * j) = make_int4(lab4[0], lab4[1], lab4[2], lab4[3]);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) lrow[4 * j + b] = lab4[b];
+                }
+            }
+        } else {
+            for (int b = 0; b < n; ++b) {
+                const uint32_t wb = b < 4 ? sw[0] : (b < 8 ? sw[1] : (b < 12 ? sw[2] : sw[3]));
+                const int sl = (int)((wb >> (8 * (b & 3))) & 0xffu);
+                if (sl != cur) next_run(sl);
+                if (sl != kNoSlot) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        fs[c] += (unsigned)*reinterpret_cast<const T*>(prow + c * S::CPB + (xs0 + b) * (int)sizeof(T));
+                    xs += (unsigned)(xs0 + b);
+                    cnt += 1u;
+                }
+                lrow[b] = curlab;
+            }
+        }
+        flush_run<C>(s.acc, cur, fs, xs, cnt, yl, zl);
     }
+    __syncthreads();
+
+    // ---- 5. per-tile sums, shifted to global coordinates ----------------------
     for (int i = tid; i < nc * F; i += kThreads) {
         const int sl = i / F, f = i % F;
-        unsigned long long cnt = 0, v = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            cnt += s.accw[w][sl][C + 3];
-            v += s.accw[w][sl][f];
-        }
+        const unsigned long long cnt = s.acc[sl][C + 3];
         if (!cnt) continue;
+        unsigned long long v = s.acc[sl][f];
         if (f == C) v += cnt * (unsigned long long)X0;
         if (f == C + 1) v += cnt * (unsigned long long)Y0;
         if (f == C + 2) v += cnt * (unsigned long long)Z0;

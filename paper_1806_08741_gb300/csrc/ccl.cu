@@ -52,10 +52,32 @@ constexpr int kPerThread = kCclTV / kCclThreads;  // 8 consecutive voxels per th
 // invariant through *err instead of spinning.
 constexpr int kWalkLimit = 1 << 26;
 
-__device__ __forceinline__ int uf_find(volatile int* par, int x, unsigned* err)
+__device__ __forceinline__ int uf_find(int* par, int x, unsigned* err)
 {
+    // path halving: every write points a node at one of its ancestors, which
+    // is in the same set and has a smaller index, so concurrent finds and
+    // links keep the forest acyclic
+    volatile int* vp = par;
     for (int i = 0; i < kWalkLimit; ++i) {
-        const int p = par[x];
+        const int p = vp[x];
+        if (p == x) return x;
+        const int gp = vp[p];
+        if (gp == p) return p;
+        vp[x] = gp;
+        x = gp;
+    }
+    atomicExch(err, 1u);
+    return x;
+}
+
+// read-only walk to the root, for the compress / flatten passes: those run
+// after every union has finished, and a halving write landing after another
+// thread's final "parent = root" store would leave a non-root parent behind
+__device__ __forceinline__ int uf_root(const int* par, int x, unsigned* err)
+{
+    const volatile int* vp = par;
+    for (int i = 0; i < kWalkLimit; ++i) {
+        const int p = vp[x];
         if (p == x) return x;
         x = p;
     }
@@ -113,21 +135,34 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         bool v = xl < ex && yl < ey && zl < ez;
         lab[e] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
-        par[e] = v ? e : -1;
         sz[e] = 0;
     }
     __syncthreads();
-    for (int e = tid; e < kCclTV; e += kCclThreads) {
-        if (par[e] < 0) continue;
-        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+    // runs along x inside the thread's 8 consecutive voxels: plain links
+    const int e0 = tid * kPerThread;
+    for (int i = 0; i < kPerThread; ++i) {
+        const int e = e0 + i;
         const int L = lab[e];
-        if (xl > 0 && lab[e - 1] == L) uf_unite(par, e, e - 1, &counters[3]);
-        if (NDIM >= 2 && yl > 0 && lab[e - TX] == L) uf_unite(par, e, e - TX, &counters[3]);
-        if (NDIM >= 3 && zl > 0 && lab[e - TX * TY] == L) uf_unite(par, e, e - TX * TY, &counters[3]);
+        par[e] = L == INT_MIN ? -1 : ((i > 0 && lab[e - 1] == L) ? par[e - 1] : e);
+    }
+    __syncthreads();
+    // unions: across the thread boundary along x, and with the voxel below
+    // along y / z unless the left neighbour already carries the same link
+    for (int i = 0; i < kPerThread; ++i) {
+        const int e = e0 + i;
+        const int L = lab[e];
+        if (L == INT_MIN) continue;
+        const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        if (i == 0 && xl > 0 && lab[e - 1] == L) uf_unite(par, e, e - 1, &counters[3]);
+        const bool left = xl > 0 && lab[e - 1] == L;
+        if (NDIM >= 2 && yl > 0 && lab[e - TX] == L && !(left && lab[e - 1 - TX] == L))
+            uf_unite(par, e, e - TX, &counters[3]);
+        if (NDIM >= 3 && zl > 0 && lab[e - TX * TY] == L && !(left && lab[e - 1 - TX * TY] == L))
+            uf_unite(par, e, e - TX * TY, &counters[3]);
     }
     __syncthreads();
     for (int e = tid; e < kCclTV; e += kCclThreads)
-        if (par[e] >= 0) par[e] = uf_find(par, e, &counters[3]);
+        if (par[e] >= 0) par[e] = uf_root(par, e, &counters[3]);
     __syncthreads();
     // rank the roots (the tile-raster-first voxel of each local component)
     unsigned mine = 0;
@@ -214,7 +249,12 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
             int64_t q[3] = {p[0], p[1], p[2]};
             q[d] -= 1;
             const int64_t ia = vidx(g, p[0], p[1], p[2]), ib = vidx(g, q[0], q[1], q[2]);
-            if (labels[ia] != labels[ib]) continue;
+            const int L = labels[ia];
+            if (L != labels[ib]) continue;
+            if (p[a1] > T0[a1]) {  // the previous pair along a1 already links these two sets
+                const int64_t st = a1 == 0 ? 1 : (a1 == 1 ? g.N[0] : g.N[0] * g.N[1]);
+                if (labels[ia - st] == L && labels[ib - st] == L) continue;
+            }
             uf_unite(gparent, gid_of<NDIM>(g, lid_img, tile_base, p[0], p[1], p[2], ntx, nty),
                      gid_of<NDIM>(g, lid_img, tile_base, q[0], q[1], q[2], ntx, nty), &counters[3]);
         }
@@ -225,7 +265,7 @@ __global__ void ccl_flatten_kernel(int* gparent, unsigned* counters)
 {
     const int64_t M = counters[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
-        gparent[i] = uf_find(gparent, (int)i, &counters[3]);
+        gparent[i] = uf_root(gparent, (int)i, &counters[3]);
 }
 
 __global__ void ccl_rootstats_kernel(const int* __restrict__ gparent, const unsigned* __restrict__ comp_size,
@@ -396,7 +436,8 @@ template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
                     const int* __restrict__ gparent, const int* __restrict__ out_label,
-                    int32_t* __restrict__ labels_out, int64_t ntx, int64_t nty)
+                    const int* __restrict__ comp_label, int32_t* __restrict__ labels_out, int inplace,
+                    int64_t ntx, int64_t nty)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY;
@@ -407,7 +448,9 @@ conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __r
         int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
         if (x >= g.N[0] || y >= g.N[1] || z >= g.N[2]) continue;
         const int64_t q = vidx(g, x, y, z);
-        labels_out[q] = out_label[gparent[base + lid_img[q]]];
+        const int G = gparent[base + lid_img[q]];
+        const int o = out_label[G];
+        if (!inplace || o != comp_label[G]) labels_out[q] = o;
     }
 }
 
@@ -511,7 +554,8 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
     conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.gparent, w.out_label,
-                                                              labels_out, ntx, nty);
+                                                              w.comp_label, labels_out,
+                                                              labels_in == labels_out ? 1 : 0, ntx, nty);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),

@@ -194,6 +194,28 @@ def test_connectivity_uncovered_and_blocky():
     assert n == nref
 
 
+def test_connectivity_many_components_and_capacity_growth():
+    """~10^6 components on 8M voxels: many concurrent union-find walks, and a
+    component count far above the initial record capacity (grown on demand)."""
+    rng = np.random.default_rng(31)
+    shape = (160, 224, 224)
+    grid = (56, 56, 40)
+    K = 4 * 4 * 4
+    blocks = rng.integers(-1, K, size=(80, 112, 112))
+    lab = np.kron(blocks, np.ones((2, 2, 2), np.int64)).astype(np.int32)
+    flip = rng.random(shape) < 0.02
+    lab[flip] = rng.integers(-1, K, size=int(flip.sum()))
+    cen = np.zeros((K, 6))
+    cen[:, 3] = rng.uniform(0, 223, size=K)
+    cen[:, 4] = rng.uniform(0, 223, size=K)
+    cen[:, 5] = rng.uniform(0, 159, size=K)
+    p = O.Params(size=(224, 224, 160), grid=grid, channels=3)
+    ref, nref = O.connectivity(p, cen, lab)
+    got, n = _gpu_conn(shape, grid, cen, lab)
+    assert n == nref
+    np.testing.assert_array_equal(got, ref)
+
+
 # ---------------------------------------------------------------------------
 # end to end
 # ---------------------------------------------------------------------------

@@ -76,7 +76,10 @@ struct Smem {
     static constexpr int PPB_RAW = TY * RPB;
     static constexpr int PPB = PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
     static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;
-    Cand<C, NDIM> cd[kCap];
+    static constexpr int NBOX = (TX / (2 * G::WX)) * (TY / G::WY) * (TZ / G::WZ);
+    Cand<C, NDIM> cd[kCap + 1];          // [kCap]: a dummy centre that reaches nothing
+    uint8_t blist[NBOX][kCap + 2];       // per warp box: reaching slots, ascending, even length
+    uint8_t bcnt[NBOX];
     alignas(16) unsigned char planes[C * CPB];
     unsigned acc[kCap][C + 4];   // per-tile sums: features, x, y, z (local), count
     float cpos[kCap][3];
@@ -95,6 +98,13 @@ __device__ __forceinline__ unsigned plane_pair(const Smem<T, C, NDIM>& s, int c,
     const unsigned char* p = s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * (int)sizeof(T);
     if constexpr (sizeof(T) == 1) return *reinterpret_cast<const uint16_t*>(p);
     else return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ uint64_t lds64(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
 }
 
 template <typename T>
@@ -295,13 +305,34 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
         }
         s.bmask[i] = m;
     }
+    for (int i = tid; i < TX; i += kThreads) s.cd[kCap].t0[i] = kInf;
+    for (int i = tid; i < TY; i += kThreads) s.cd[kCap].t1[i] = make_float2(kInf, kInf);
+    for (int i = tid; i < TZ; i += kThreads) s.cd[kCap].t2[i] = make_float2(kInf, kInf);
+    if (tid < C) s.cd[kCap].fe[tid] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    // per warp box: the slots whose window reaches it, ascending, padded to
+    // an even count with the dummy so the sweep takes two centres per step
+    for (int wb = warp; wb < NBOX; wb += kWarps) {
+        const int bxi = wb % NBX, byi = (wb / NBX) % NBY, bzi = wb / (NBX * NBY);
+        const uint32_t want = (1u << bxi) | (1u << (NBX + byi)) | (1u << (NBX + NBY + bzi));
+        const bool h0 = lane < nc && (s.bmask[lane] & want) == want;
+        const bool h1 = lane + 32 < nc && (s.bmask[lane + 32] & want) == want;
+        const uint32_t m0 = __ballot_sync(0xffffffffu, h0);
+        const uint32_t m1 = __ballot_sync(0xffffffffu, h1);
+        const uint32_t lt = (1u << lane) - 1u;
+        const int n0 = __popc(m0), n = n0 + __popc(m1);
+        if (h0) s.blist[wb][__popc(m0 & lt)] = (uint8_t)lane;
+        if (h1) s.blist[wb][n0 + __popc(m1 & lt)] = (uint8_t)(lane + 32);
+        if (lane == 0) {
+            if (n & 1) s.blist[wb][n] = (uint8_t)kCap;
+            s.bcnt[wb] = (uint8_t)((n + 1) & ~1);
+        }
+    }
     __syncthreads();
 
     // ---- 3. warp boxes: assignment ------------------------------------------
     const int lx = lane % WX, ly = (lane / WX) % WY, lz = lane / (WX * WY);
-    const uint32_t bm0 = lane < nc ? s.bmask[lane] : 0u;
-    const uint32_t bm1 = lane + 32 < nc ? s.bmask[lane + 32] : 0u;
-    const unsigned char* cdb = reinterpret_cast<const unsigned char*>(&s.cd[0]);
+    const uint32_t cdb = (uint32_t)__cvta_generic_to_shared(&s.cd[0]);
     using CandT = Cand<C, NDIM>;
     constexpr int CDS = (int)sizeof(CandT);
     constexpr int kOffT1 = 8 * C;  // layout of Cand: fe, t1, t2, t0
@@ -313,9 +344,6 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
         const int wb = warp + pass * kWarps;
         const int bxi = wb % NBX, byi = (wb / NBX) % NBY, bzi = wb / (NBX * NBY);
         const int xl = bxi * BX + lx * 2, yl = byi * BY + ly, zl = bzi * BZ + lz;
-        const uint32_t want = (1u << bxi) | (1u << (NBX + byi)) | (1u << (NBX + NBY + bzi));
-        const uint32_t m0 = __ballot_sync(0xffffffffu, (bm0 & want) == want);
-        const uint32_t m1 = __ballot_sync(0xffffffffu, (bm1 & want) == want);
         uint64_t Fp[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
@@ -325,31 +353,39 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
         }
         float b0 = kInf, b1 = kInf;
         int s0 = kNoSlot, s1 = kNoSlot;
-        const int o0 = kOffT0 + xl * 4;
-        const int o1 = kOffT1 + yl * 8;
-        const int o2 = kOffT2 + zl * 8;
-#pragma unroll 1
-        for (int word = 0; word < 2; ++word) {
-            uint32_t m = word ? m1 : m0;
-            while (m) {
-                const int sl = __ffs(m) - 1 + 32 * word;
-                m &= m - 1;
-                const unsigned char* base = cdb + sl * CDS;
-                uint64_t dc;
+        const uint32_t a0 = cdb + kOffT0 + xl * 4;
+        const uint32_t a1 = cdb + kOffT1 + yl * 8;
+        const uint32_t a2 = cdb + kOffT2 + zl * 8;
+        const int nb = s.bcnt[wb];
+        const uint16_t* lst = reinterpret_cast<const uint16_t*>(&s.blist[wb][0]);
+        // D^2 of both voxels of the lane against the centre in slot sl
+        auto dist2 = [&](int sl) -> uint64_t {
+            const uint32_t so = (uint32_t)(sl * CDS);
+            uint64_t dc;
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const uint64_t e = sub2(Fp[c], *reinterpret_cast<const uint64_t*>(base + c * 8));
-                    const uint64_t sq = mul2(e, e);
-                    dc = c == 0 ? sq : add2(dc, sq);
-                }
-                uint64_t ds = *reinterpret_cast<const uint64_t*>(base + o0);
-                if (NDIM >= 2) ds = add2(ds, *reinterpret_cast<const uint64_t*>(base + o1));
-                if (NDIM >= 3) ds = add2(ds, *reinterpret_cast<const uint64_t*>(base + o2));
-                float d0, d1;
-                upk2(add2(dc, ds), d0, d1);
-                if (d0 < b0) { b0 = d0; s0 = sl; }
-                if (d1 < b1) { b1 = d1; s1 = sl; }
+            for (int c = 0; c < C; ++c) {
+                const uint64_t e = sub2(Fp[c], lds64(cdb + so + c * 8));
+                const uint64_t sq = mul2(e, e);
+                dc = c == 0 ? sq : add2(dc, sq);
             }
+            uint64_t ds = lds64(a0 + so);
+            if (NDIM >= 2) ds = add2(ds, lds64(a1 + so));
+            if (NDIM >= 3) ds = add2(ds, lds64(a2 + so));
+            return add2(dc, ds);
+        };
+#pragma unroll 1
+        for (int i = 0; i < nb; i += 2) {
+            const unsigned two = lst[i >> 1];
+            const int sa = (int)(two & 0xffu), sb = (int)(two >> 8);
+            const uint64_t Da = dist2(sa);
+            const uint64_t Db = dist2(sb);
+            float d0, d1;
+            upk2(Da, d0, d1);
+            if (d0 < b0) { b0 = d0; s0 = sa; }
+            if (d1 < b1) { b1 = d1; s1 = sa; }
+            upk2(Db, d0, d1);
+            if (d0 < b0) { b0 = d0; s0 = sb; }
+            if (d1 < b1) { b1 = d1; s1 = sb; }
         }
         *reinterpret_cast<uint16_t*>(&s.slot[(zl * TY + yl) * TX + xl]) = (uint16_t)(s0 | (s1 << 8));
     }
@@ -407,15 +443,23 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
                     }
                     lab4[0] = lab4[1] = lab4[2] = lab4[3] = curlab;
                 } else {
+                    uint32_t pw[C];
+                    if constexpr (sizeof(T) == 1) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            pw[c] = *reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq);
+                    }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const int sl = (int)((w >> (8 * b)) & 0xffu);
                         if (sl != cur) next_run(sl);
                         if (sl != kNoSlot) {
 #pragma unroll
-                            for (int c = 0; c < C; ++c)
-                                fs[c] += (unsigned)*reinterpret_cast<const T*>(
+                            for (int c = 0; c < C; ++c) {
+                                if constexpr (sizeof(T) == 1) fs[c] += (pw[c] >> (8 * b)) & 0xffu;
+                                else fs[c] += (unsigned)*reinterpret_cast<const T*>(
                                     prow + c * S::CPB + (xq + b) * (int)sizeof(T));
+                            }
                             xs += (unsigned)(xq + b);
                             cnt += 1u;
                         }

@@ -138,6 +138,27 @@ SSLIC_API int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* ce
 SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* labels_in_dev,
                        int32_t* labels_out_dev, void* stream, int64_t* num_labels_host);
 
+/* One assign + update iteration (the same step as sslic_iterate) that
+ * allocates nothing.  The paper has no counterpart to this call.  It serves
+ * callers that cannot call cudaMalloc: code running under an allocator or
+ * memory pool that must not grow, plug-ins whose device memory is budgeted
+ * up front, and latency-critical paths that cannot afford an allocation's
+ * implicit device synchronisation.  Instead of a context it uses one
+ * file-scope device array of about 3 MB, which every GPU that loads this
+ * library holds until the process exits.  That array bounds the request:
+ * K <= 16384 clusters, C <= 4 channels and at most 65536 assignment tiles
+ * (a tile is 32x16x8 voxels in 3-D, 64x32 pixels in 2-D); larger requests
+ * return SSLIC_EINVAL.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current, so make
+ * it before any stream capture.  All calls share the array and it keeps the
+ * previous call's contents: the sums are cleared at the start of each call,
+ * and calls whose work overlaps on the GPU (unordered streams) race on it.
+ *   p                parameters, validated as for sslic_create
+ *   image_dev, centres_in_dev, labels_dev, centres_out_dev: as sslic_iterate
+ *   stream           cudaStream_t, or NULL for the legacy default stream */
+SSLIC_API int sslic_iterate_static(const sslic_params* p, const void* image_dev, const float* centres_in_dev,
+                                   int32_t* labels_dev, float* centres_out_dev, void* stream);
+
 /* Tracing.  When enabled, every phase of the method is bracketed by CUDA
  * events recorded on the launching stream; sslic_profile_read waits for the
  * recorded events and returns the summed device time per phase.  The

@@ -119,6 +119,11 @@ static int validate(const sslic_params* p, Geom* g)
     return SSLIC_OK;
 }
 
+int make_geom(const sslic_params* p, Geom* g)
+{
+    return validate(p, g);
+}
+
 int ensure_ccl_capacity(sslic_ctx* c, int64_t m)
 {
     Workspace& w = c->ws;

@@ -187,6 +187,7 @@ int launch_voxel_tiles(sslic_ctx* c, const T* img, int32_t* labels, int tx, int 
                        cudaStream_t st);
 int ensure_ccl_capacity(sslic_ctx* c, int64_t m);
 int set_error(sslic_ctx* c, int code, const char* fmt, ...);
+int make_geom(const sslic_params* p, Geom* g);
 // phase brackets: prof_begin returns a record index (or -1 when timing is off)
 int prof_begin(sslic_ctx* c, int phase, cudaStream_t st);
 void prof_end(sslic_ctx* c, int rec, cudaStream_t st);

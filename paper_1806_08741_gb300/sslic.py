@@ -23,8 +23,8 @@ _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUSY",
 
 EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_run",
            "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
-           "sslic_connectivity", "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
-           "sslic_strerror", "sslic_last_error")
+           "sslic_connectivity", "sslic_iterate_static", "sslic_profile_enable",
+           "sslic_profile_read", "sslic_destroy", "sslic_strerror", "sslic_last_error")
 PHASES = ("seed", "bins", "assign", "assign_voxel", "finalize", "connectivity")
 
 
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH):
     L.sslic_seed.argtypes = [C, vp, vp, vp]
     L.sslic_iterate.argtypes = [C, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sslic_connectivity.argtypes = [C, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.sslic_iterate_static.argtypes = [P, vp, vp, vp, vp, vp]
+    L.sslic_iterate_static.restype = ctypes.c_int
     L.sslic_profile_enable.argtypes = [C, ctypes.c_int32]
     L.sslic_profile_read.argtypes = [C, ctypes.POINTER(_Profile)]
     L.sslic_profile_enable.restype = ctypes.c_int
@@ -332,6 +334,28 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def iterate_static(params: Params, image, centres_in, labels, centres_out, stream=None) -> None:
+    """One assign + update iteration through sslic_iterate_static: no
+    allocation at all (a fixed device array of the library holds the
+    workspace; K <= 16384, C <= 4).  For callers that cannot allocate device
+    memory.  Tensors as for Context.iterate."""
+    L = load()
+    V = int(np.prod(params.size))
+    K = 1
+    grid = tuple(params.grid) * (len(params.size) if len(params.grid) == 1 else 1)
+    for n_d, s_d in zip(params.size, grid):
+        K *= -(-int(n_d) // int(s_d))
+    W = params.channels + len(params.size)
+    for t, n, what in ((image, V * params.channels, "image"), (labels, V, "labels"),
+                       (centres_in, K * W, "centres_in"), (centres_out, K * W, "centres_out")):
+        if t.numel() != n or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{what}: expected a contiguous device tensor of {n} elements")
+    rc = L.sslic_iterate_static(ctypes.byref(params.to_c()), _ptr(image), _ptr(centres_in),
+                                _ptr(labels), _ptr(centres_out), _stream(stream))
+    if rc != SSLIC_OK:
+        raise SSLICError(rc, "sslic_iterate_static")
 
 
 def segment(image, grid, stream=None, **kw):

@@ -13,7 +13,7 @@
 // The map step of the update (Sec. 3.1) is fused: [I(x), x, 1] is summed
 // per label in the same pass, so the image is read once per iteration.
 //
-// Work decomposition.  A CTA (4 warps) owns a tile of 32x16x8 voxels (3-D)
+// Work decomposition.  A CTA (8 warps) owns a tile of 32x16x8 voxels (3-D)
 // or 64x32 pixels (2-D):
 //  1. stages the tile's channels as bank-padded planes in shared memory;
 //  2. gathers the centres of the bins that can reach the tile (3 bins per
@@ -37,10 +37,10 @@ namespace sslic {
 namespace tile {
 
 constexpr float kInf = __builtin_huge_valf();
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kCap = 64;     // candidate centres per tile
-constexpr int kStage = 512;  // gathered centres before filtering
+constexpr int kCap = 48;     // candidate centres per tile (a 32x16x8 tile at S = 16 sees ~23, <= 40)
+constexpr int kStage = 256;  // gathered centres before filtering
 constexpr int kSeg = 16;     // voxels per row segment in the label / sum sweep
 
 template <int NDIM>
@@ -128,7 +128,7 @@ __device__ __forceinline__ void flush_run(unsigned (*acc)[C + 4], int cur, const
 }
 
 template <typename T, int C, int NDIM>
-__global__ void __launch_bounds__(kThreads, 5)
+__global__ void __launch_bounds__(kThreads, 4)
 assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ ctr,
                    const unsigned* __restrict__ bin_start, const int* __restrict__ bin_items,
                    int32_t* __restrict__ labels, unsigned long long* __restrict__ acc,
@@ -394,8 +394,19 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     // ---- 4. row segments: labels out, run sums in -------------------------------
     const bool vec_ok = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
     for (int sg = tid; sg < TY * TZ * SPR; sg += kThreads) {
-        const int r = sg / SPR, h = sg % SPR;
-        const int yl = r % TY, zl = r / TY;
+        // lanes of a warp take segments in different z planes (different
+        // labels, fewer same-address flushes); 2-D: consecutive segments
+        int h, yl, zl;
+        if constexpr (TZ > 1) {
+            zl = sg % TZ;
+            h = (sg / TZ) % SPR;
+            yl = sg / (TZ * SPR);
+        } else {
+            h = sg % SPR;
+            yl = sg / SPR;
+            zl = 0;
+        }
+        const int r = zl * TY + yl;
         if (yl >= ey || zl >= ez) continue;
         const int xs0 = h * kSeg;
         const int n = min(kSeg, ex - xs0);
@@ -403,11 +414,12 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
         int32_t* lrow = labels + vidx(g, X0 + xs0, Y0 + yl, Z0 + zl);
         const unsigned char* prow = s.planes + zl * S::PPB + yl * S::RPB;
         // the segment's slots, read word by word in a lane-rotated order
+        // (spreads the lanes of a warp over the banks)
         uint32_t sw[kSeg / 4];
         const uint32_t* sp = reinterpret_cast<const uint32_t*>(&s.slot[r * TX + xs0]);
 #pragma unroll
         for (int j = 0; j < kSeg / 4; ++j) {
-            const int jj = (j + (lane >> 3)) & (kSeg / 4 - 1);
+            const int jj = (j + (TZ > 1 ? (lane & 7) : (lane >> 3))) & (kSeg / 4 - 1);
             sw[jj] = sp[jj];
         }
         int cur = kNoSlot, curlab = -1;

@@ -295,6 +295,13 @@ def run_ours(args, w):
                "ms_per_step": dt * 1e3, "labels_equal_device_run": same}
         del h_img, h_lab, h_cen
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        ctx.close()
+        del img, labels, centres
+        torch.cuda.empty_cache()
+        serving = serving_bench(n_req=args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, _ = oracle_sample(w, args.cpu_edge)
@@ -307,7 +314,7 @@ def run_ours(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {**_config(w), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
-            "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -315,6 +322,133 @@ def run_ours(args, w):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# serving: request stream, continuous batching vs one image per launch
+# ---------------------------------------------------------------------------
+def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12):
+    """Poisson arrivals (rate per second) of requests mixing 2-D RGB uint8
+    tiles (side ~ U[256, 4096]) and 3-D uint16 blocks (side ~ U[128, 512]),
+    S in {8, 16, 32}, m in {5, 10, 20}, 10 iterations.  Inputs come from a
+    pool of pool_n images of each kind (made on the GPU, kept in page-locked
+    host memory).  Returns latency percentiles and throughput of the served
+    form (sslic_server_*) and of the plain form (one sslic_run_host call per
+    request, in arrival order)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1806_08741_gb300 import inputs
+    from paper_1806_08741_gb300 import sslic as S
+
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(pool_n):
+        side = int(rng.integers(256, 4097))
+        spec = inputs.ImageSpec((side, side), 3, "u8", seed * 10 + i, max(2, side * side // 3000), 6)
+        pool.append(spec)
+    for i in range(pool_n):
+        side = int(rng.integers(128, 513))
+        spec = inputs.ImageSpec((side, side, side), 1, "u16", seed * 10 + 100 + i,
+                                max(2, side ** 3 // 20000), 300)
+        pool.append(spec)
+    host = []
+    for spec in pool:
+        dt = torch.uint8 if spec.dtype == "u8" else torch.uint16
+        d = torch.empty(spec.shape, dtype=dt, device="cuda")
+        inputs.make_image_device(spec, d.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        h = torch.empty(spec.shape, dtype=dt, pin_memory=True)
+        h.copy_(d)
+        host.append(h)
+        del d
+    torch.cuda.synchronize()
+    reqs = []
+    t = 0.0
+    for _ in range(n_req):
+        t += float(rng.exponential(1.0 / rate))
+        idx = int(rng.integers(0, 2 * pool_n))
+        grid = int(rng.choice([8, 16, 32]))
+        m = float(rng.choice([5.0, 10.0, 20.0]))
+        reqs.append((t, idx, grid, m))
+
+    def params(idx, grid, m):
+        spec = pool[idx]
+        return S.Params(size=spec.size, grid=(grid,) * spec.ndim, channels=spec.channels,
+                        dtype=S.U8 if spec.dtype == "u8" else S.U16, m=m, max_iter=10)
+
+    # page-locked output buffers, made before the timed region and recycled
+    lock = threading.Lock()
+    out_pool = {i: [torch.empty(pool[i].shape[:-1], dtype=torch.int32, pin_memory=True) for _ in range(4)]
+                for i in range(len(pool))}
+
+    def out_buf(idx):
+        with lock:
+            if out_pool[idx]:
+                return out_pool[idx].pop()
+        return torch.empty(pool[idx].shape[:-1], dtype=torch.int32, pin_memory=True)
+
+    def give_back(idx, buf):
+        with lock:
+            out_pool[idx].append(buf)
+
+    vox_iters = sum(pool[i].voxels * 10 for _, i, _, _ in reqs)
+
+    # served form: a submitter at the arrival times, a waiter recycling outputs
+    res = {}
+    with S.Server(int(budget_gb * (1 << 30)), max_active=256) as srv:
+        import queue as _q
+        handed = _q.Queue()
+        lats = []
+
+        def waiter():
+            while True:
+                item = handed.get()
+                if item is None:
+                    return
+                tk, idx, lab = item
+                lats.append(srv.wait(tk))
+                give_back(idx, lab)
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for (ta, idx, grid, m) in reqs:
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            lab = out_buf(idx)
+            handed.put((srv.submit(params(idx, grid, m), host[idx], lab), idx, lab))
+        handed.put(None)
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    res["served"] = {"p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+                     "mean_ms": float(np.mean(lats)), "throughput": vox_iters / wall / 1e9,
+                     "wall_s": wall, "max_active": st["max_active"], "rounds": st["rounds"],
+                     "peak_gb": st["peak_bytes"] / 2 ** 30}
+
+    # plain form: one request at a time, in arrival order
+    lats = []
+    t0 = time.perf_counter()
+    for (ta, idx, grid, m) in reqs:
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        lab = out_buf(idx)
+        with S.Context(params(idx, grid, m)) as ctx:
+            ctx.run_host(host[idx], lab)
+        lats.append((time.perf_counter() - t0 - ta) * 1e3)
+        give_back(idx, lab)
+    wall = time.perf_counter() - t0
+    res["plain"] = {"p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
+                    "mean_ms": float(np.mean(lats)), "throughput": vox_iters / wall / 1e9, "wall_s": wall}
+    res["stream"] = {"requests": n_req, "rate_per_s": rate, "iterations": 10,
+                     "mix": "1/2 2-D RGB u8 side U[256,4096], 1/2 3-D u16 side U[128,512]; S in {8,16,32}; m in {5,10,20}",
+                     "inputs": f"{2 * pool_n} pool images", "offered_gvox_iter_s": vox_iters / reqs[-1][0] / 1e9,
+                     "unit": UNIT}
+    return res
 
 
 def main():
@@ -329,7 +463,16 @@ def main():
     ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
     ap.add_argument("--reference-edge", type=int, default=128,
                     help="edge of the crop each reference-arm step runs")
+    ap.add_argument("--serve", action="store_true",
+                    help="only the request-stream benchmark (served vs plain form)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-stream benchmark")
+    ap.add_argument("--serve-requests", type=int, default=200)
     args = ap.parse_args()
+    if args.serve:
+        import torch
+        torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        print(json.dumps({"serving": serving_bench(n_req=args.serve_requests)}), flush=True)
+        return 0
     from paper_1806_08741_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":

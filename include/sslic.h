@@ -159,6 +159,51 @@ SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const i
 SSLIC_API int sslic_iterate_static(const sslic_params* p, const void* image_dev, const float* centres_in_dev,
                                    int32_t* labels_dev, float* centres_out_dev, void* stream);
 
+/* Serving (continuous batching).  A server keeps requests on the device and
+ * advances all admitted requests together, one assign/update iteration per
+ * round, each round running one launch per phase over every request of the
+ * batch (batched form of Sec. 3.1 step 2).  Requests that have done their
+ * iterations leave after the round and queued requests are admitted, first
+ * come first served, as soon as the HBM budget has room for their image,
+ * labels, centres, bins and sums.  Each request's labels and centres are the
+ * ones sslic_run gives for it alone.  Requests need enforce_connectivity = 0
+ * and conv_threshold <= 0 (every request runs its max_iter iterations). */
+typedef struct sslic_server sslic_server;
+
+typedef struct {
+    int64_t submitted, completed, rejected;  /* rejected: larger than the whole budget */
+    int64_t rounds;                          /* batched iterations run */
+    int32_t max_active;                      /* most requests on the device at once */
+    int32_t status;                          /* SSLIC_OK, or the first error of the worker */
+    int64_t peak_bytes;                      /* most budget bytes in use */
+    double  voxel_iters;                     /* sum of voxels x iterations of completed requests */
+    double  busy_s;                          /* first admission to last completion, seconds */
+    double  p50_ms, p99_ms, mean_ms;         /* latency: submission to result in host memory */
+} sslic_server_stats;
+
+/* Start a server on the current device with a device-memory budget for
+ * requests (allocated once, here) and a cap on requests on the device. */
+SSLIC_API int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, sslic_server** out);
+
+/* Queue one request.  image_host (read), labels_host (V int32, written) and
+ * centres_host (K x (C+n) float32, written, may be NULL) must stay valid
+ * until sslic_server_wait returns for the ticket; page-locked buffers let the
+ * copies overlap the computation.  SSLIC_ENOMEM if the request alone exceeds
+ * the budget; SSLIC_EUNSUPPORTED for connectivity or a convergence threshold. */
+SSLIC_API int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* image_host,
+                                  int32_t* labels_host, float* centres_host, int64_t* ticket);
+
+/* Wait up to timeout_ms for a ticket; on success the results are in the
+ * caller's buffers and latency_ms (may be NULL) holds submission-to-result
+ * time.  SSLIC_ETIMEOUT if the ticket is still running (wait again).  A
+ * ticket is released by its first successful wait. */
+SSLIC_API int sslic_server_wait(sslic_server* s, int64_t ticket, int32_t timeout_ms, double* latency_ms);
+
+SSLIC_API int sslic_server_stats_get(sslic_server* s, sslic_server_stats* out);
+
+/* Finish every queued request, stop the worker and free the server. */
+SSLIC_API void sslic_server_destroy(sslic_server* s);
+
 /* Tracing.  When enabled, every phase of the method is bracketed by CUDA
  * events recorded on the launching stream; sslic_profile_read waits for the
  * recorded events and returns the summed device time per phase.  The

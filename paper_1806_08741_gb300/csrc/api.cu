@@ -133,6 +133,7 @@ int ensure_ccl_capacity(sslic_ctx* c, int64_t m)
         if ((rc = dalloc(c, &w.lid, (size_t)g.V, "component ids"))) return rc;
         w.n_ccl_tiles = ccl_num_tiles(g);
         if ((rc = dalloc(c, &w.tile_base, (size_t)w.n_ccl_tiles, "tile bases"))) return rc;
+        if ((rc = dalloc(c, &w.tile_cnt, (size_t)w.n_ccl_tiles, "tile counts"))) return rc;
         if ((rc = dalloc(c, &w.counters, 4, "counters"))) return rc;
     }
     if (m <= w.m_cap) return SSLIC_OK;
@@ -163,7 +164,7 @@ static void free_all(sslic_ctx* c)
     dfree(w.resid_part); dfree(w.resid_cnt_part); dfree(w.resid_out);
     dfree(w.bin_count); dfree(w.bin_start); dfree(w.bin_cursor); dfree(w.bin_items); dfree(w.bin_of);
     dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count);
-    dfree(w.lid); dfree(w.tile_base); dfree(w.counters);
+    dfree(w.lid); dfree(w.tile_base); dfree(w.tile_cnt); dfree(w.counters);
     dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
     dfree(w.new_key); dfree(w.new_val); dfree(w.sort_key); dfree(w.sort_val);

@@ -23,10 +23,10 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "device_fns.cuh"
 
 namespace sslic {
 
-constexpr float kInf = __builtin_huge_valf();
 
 // ---------------------------------------------------------------------------
 // per-voxel kernel: any dtype / channel count / dimensionality, and the tiles
@@ -42,7 +42,6 @@ __global__ void assign_voxel_kernel(Geom g, const T* __restrict__ img, const flo
                                     int64_t ntx, int64_t nty, int tx_, int ty_, int tz_)
 {
     // tiles == nullptr: block b covers voxels [b * blockDim, ...) in raster order
-    const int C = g.C;
     const int tv = tx_ * ty_ * tz_;
     int64_t nwork;
     if (tiles) nwork = (int64_t)(*ntiles) * tv;
@@ -51,7 +50,7 @@ __global__ void assign_voxel_kernel(Geom g, const T* __restrict__ img, const flo
          w += (int64_t)gridDim.x * blockDim.x) {
         int64_t x, y, z;
         if (tiles) {
-            int64_t t = tiles[w / tv];
+            const int64_t t = tiles[w / tv] & ((1LL << 40) - 1);  // low bits: tile, high bits: request
             int e = (int)(w % tv);
             x = (t % ntx) * tx_ + e % tx_;
             y = ((t / ntx) % nty) * ty_ + (e / tx_) % ty_;
@@ -62,56 +61,7 @@ __global__ void assign_voxel_kernel(Geom g, const T* __restrict__ img, const flo
             y = (w / g.N[0]) % g.N[1];
             z = w / (g.N[0] * g.N[1]);
         }
-        const int64_t q = vidx(g, x, y, z);
-        const int64_t X[3] = {x, y, z};
-        int64_t blo[3], bhi[3];
-        for (int d = 0; d < 3; ++d) {
-            blo[d] = imax64(0, X[d] / g.S[d] - 1);
-            bhi[d] = imin64(g.nb[d] - 1, X[d] / g.S[d] + 1);
-        }
-        float best = kInf;
-        int bestk = -1;
-        for (int64_t bz = blo[2]; bz <= bhi[2]; ++bz)
-            for (int64_t by = blo[1]; by <= bhi[1]; ++by)
-                for (int64_t bx = blo[0]; bx <= bhi[0]; ++bx) {
-                    int64_t bin = bx + g.nb[0] * (by + g.nb[1] * bz);
-                    for (unsigned i = bin_start[bin]; i < bin_start[bin + 1]; ++i) {
-                        const int k = bin_items[i];
-                        const float* row = ctr + (int64_t)k * g.CW;
-                        bool inside = true;
-                        for (int d = 0; d < g.n; ++d) {
-                            int64_t lo = window_lo(row[C + d], g.S[d]);
-                            inside = inside && X[d] >= lo && X[d] <= lo + 2 * g.S[d] - 1;
-                        }
-                        if (!inside) continue;
-                        float dc = 0.0f;
-                        for (int c = 0; c < C; ++c) {
-                            float e = __fsub_rn((float)img[q * C + c], row[c]);
-                            float sq = __fmul_rn(e, e);
-                            dc = c == 0 ? sq : __fadd_rn(dc, sq);
-                        }
-                        float ds = 0.0f;
-                        for (int d = 0; d < g.n; ++d) {
-                            float dl = __fsub_rn((float)X[d], row[C + d]);
-                            float t = __fmul_rn(g.w[d], __fmul_rn(dl, dl));
-                            ds = d == 0 ? t : __fadd_rn(ds, t);
-                        }
-                        float D = __fadd_rn(dc, ds);
-                        if (D < best || (D == best && k < bestk)) { best = D; bestk = k; }
-                    }
-                }
-        labels[q] = bestk;
-        if (bestk >= 0) {
-            unsigned long long* a = acc + (int64_t)bestk * g.AW;
-            for (int c = 0; c < C; ++c) {
-                if (sizeof(T) == 4) atomicAdd(&facc[(int64_t)bestk * C + c], (double)img[q * C + c]);
-                else atomicAdd(&a[c], (unsigned long long)img[q * C + c]);
-            }
-            atomicAdd(&a[C], (unsigned long long)x);
-            atomicAdd(&a[C + 1], (unsigned long long)y);
-            atomicAdd(&a[C + 2], (unsigned long long)z);
-            atomicAdd(&a[C + 3], 1ull);
-        }
+        voxel_assign<T>(g, img, ctr, bin_start, bin_items, labels, acc, facc, x, y, z);
     }
 }
 
@@ -181,29 +131,8 @@ __global__ void finalize_kernel(Geom g, float* __restrict__ ctr, unsigned long l
                                 double* __restrict__ facc, double* __restrict__ rk,
                                 unsigned* __restrict__ ne)
 {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= g.K) return;
-    unsigned long long* a = acc + k * g.AW;
-    const unsigned long long cnt = a[g.C + 3];
-    float* row = ctr + k * g.CW;
-    double r = 0.0;
-    if (cnt) {
-        const double n = (double)cnt;
-        for (int j = 0; j < g.C + g.n; ++j) {
-            // features, then the real position axes
-            const double sum = (j < g.C && g.dtype == SSLIC_F32) ? facc[k * g.C + j] : (double)a[j];
-            const float v = __double2float_rn(__ddiv_rn(sum, n));
-            const double diff = (double)v - (double)row[j];
-            r = __dadd_rn(r, j < g.C ? __dmul_rn(diff, diff) : __dmul_rn(g.w64[j - g.C], __dmul_rn(diff, diff)));
-            row[j] = v;
-        }
-        r = sqrt(r);
-    }
-    rk[k] = r;
-    ne[k] = cnt ? 1u : 0u;
-    for (int j = 0; j < g.AW; ++j) a[j] = 0ull;
-    if (g.dtype == SSLIC_F32)
-        for (int c = 0; c < g.C; ++c) facc[k * g.C + c] = 0.0;
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < g.K) finalize_one(g, ctr, acc, facc, k, rk, ne);
 }
 
 // deterministic residual reduction: fixed-order block sums, then one block

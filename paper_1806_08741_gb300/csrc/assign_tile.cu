@@ -43,31 +43,30 @@ constexpr int kCap = 48;     // candidate centres per tile (a 32x16x8 tile at S 
 constexpr int kStage = 256;  // gathered centres before filtering
 constexpr int kSeg = 16;     // voxels per row segment in the label / sum sweep
 
-template <int NDIM>
-struct Cfg;
-template <>
-struct Cfg<3> {
-    static constexpr int TX = 32, TY = 16, TZ = 8;  // 4096 voxels
-    static constexpr int WX = 2, WY = 4, WZ = 4;    // lanes -> box 4x4x4 (pairs along x)
+// Tile shapes.  A tile must stay within kCap reaching centres: about
+// prod_d (T_d + 2 S_d - 1) / S_d of them, so small grids take small tiles.
+// Lanes: WX pairs along x times WY times WZ; a warp box is 2WX x WY x WZ.
+template <int NDIM_, int TX_, int TY_, int TZ_, int WX_, int WY_, int WZ_>
+struct Shape {
+    static constexpr int NDIM = NDIM_, TX = TX_, TY = TY_, TZ = TZ_, WX = WX_, WY = WY_, WZ = WZ_;
 };
-template <>
-struct Cfg<2> {
-    static constexpr int TX = 64, TY = 32, TZ = 1;  // 2048 pixels
-    static constexpr int WX = 4, WY = 8, WZ = 1;    // box 8x8
-};
+using Shape3L = Shape<3, 32, 16, 8, 2, 4, 4>;   // 4096 voxels, grids S >= 12
+using Shape3S = Shape<3, 16, 8, 8, 2, 4, 4>;    // 1024 voxels, smaller grids
+using Shape2L = Shape<2, 64, 32, 1, 4, 8, 1>;   // 2048 pixels
+using Shape2S = Shape<2, 32, 16, 1, 4, 8, 1>;   // 512 pixels
 
 // per-candidate record in shared memory
-template <int C, int NDIM>
+template <int C, typename SH>
 struct Cand {
-    float2 fe[C];              // (C_c, C_c)
-    float2 t1[Cfg<NDIM>::TY];  // (t_1, t_1) by local y
-    float2 t2[Cfg<NDIM>::TZ];  // (t_2, t_2) by local z
-    float t0[Cfg<NDIM>::TX];   // t_0 by local x
+    float2 fe[C];        // (C_c, C_c)
+    float2 t1[SH::TY];   // (t_1, t_1) by local y
+    float2 t2[SH::TZ];   // (t_2, t_2) by local z
+    float t0[SH::TX];    // t_0 by local x
 };
 
-template <typename T, int C, int NDIM>
+template <typename T, int C, typename SH>
 struct Smem {
-    using G = Cfg<NDIM>;
+    using G = SH;
     static constexpr int TX = G::TX, TY = G::TY, TZ = G::TZ, TV = TX * TY * TZ;
     // channel planes: row pitch 4 bytes past the row, plane pitch chosen so a
     // plane advances 4 banks -- the 4x4 (y, z) lanes of a warp box then hit
@@ -77,7 +76,7 @@ struct Smem {
     static constexpr int PPB = PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
     static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;
     static constexpr int NBOX = (TX / (2 * G::WX)) * (TY / G::WY) * (TZ / G::WZ);
-    Cand<C, NDIM> cd[kCap + 1];          // [kCap]: a dummy centre that reaches nothing
+    Cand<C, SH> cd[kCap + 1];          // [kCap]: a dummy centre that reaches nothing
     uint8_t blist[NBOX][kCap + 2];       // per warp box: reaching slots, ascending, even length
     uint8_t bcnt[NBOX];
     alignas(16) unsigned char planes[C * CPB];
@@ -91,10 +90,10 @@ struct Smem {
     int nstage, ncand;
 };
 
-template <typename T, int C, int NDIM>
-__device__ __forceinline__ unsigned plane_pair(const Smem<T, C, NDIM>& s, int c, int xl, int yl, int zl)
+template <typename T, int C, typename SH>
+__device__ __forceinline__ unsigned plane_pair(const Smem<T, C, SH>& s, int c, int xl, int yl, int zl)
 {
-    using S = Smem<T, C, NDIM>;
+    using S = Smem<T, C, SH>;
     const unsigned char* p = s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * (int)sizeof(T);
     if constexpr (sizeof(T) == 1) return *reinterpret_cast<const uint16_t*>(p);
     else return *reinterpret_cast<const uint32_t*>(p);
@@ -127,15 +126,24 @@ __device__ __forceinline__ void flush_run(unsigned (*acc)[C + 4], int cur, const
     atomicAdd(&acc[cur][C + 3], cnt);
 }
 
-template <typename T, int C, int NDIM>
-__global__ void __launch_bounds__(kThreads, 4)
-assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ ctr,
-                   const unsigned* __restrict__ bin_start, const int* __restrict__ bin_items,
-                   int32_t* __restrict__ labels, unsigned long long* __restrict__ acc,
-                   int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count, int ntx, int nty)
+// One tile of one image (request req): everything of steps 1-5 above.  A
+// tile reached by more than kCap centres is appended to the crowded-tile
+// list as (req << 40 | tile) and left to the per-voxel kernel.
+template <typename T, int C, typename SH>
+__device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t req, Smem<T, C, SH>& s,
+                                          int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
 {
-    using G = Cfg<NDIM>;
-    using S = Smem<T, C, NDIM>;
+    const Geom& g = a.g;
+    const T* __restrict__ img = (const T*)a.img;
+    const float* __restrict__ ctr = a.ctr;
+    const unsigned* __restrict__ bin_start = a.bin_start;
+    const int* __restrict__ bin_items = a.bin_items;
+    int32_t* __restrict__ labels = a.labels;
+    unsigned long long* __restrict__ acc = a.acc;
+    const int ntx = a.ntx, nty = a.nty;
+    constexpr int NDIM = SH::NDIM;
+    using G = SH;
+    using S = Smem<T, C, SH>;
     constexpr int TX = G::TX, TY = G::TY, TZ = G::TZ, TV = TX * TY * TZ;
     constexpr int WX = G::WX, WY = G::WY, WZ = G::WZ;
     constexpr int BX = 2 * WX, BY = WY, BZ = WZ;
@@ -148,11 +156,7 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     static_assert(NBX + NBY + NBZ <= 32, "box mask bits");
     static_assert(TX % kSeg == 0, "row segments");
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    S& s = *reinterpret_cast<S*>(smem_raw);
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
     const int X0 = (tile % ntx) * TX;
     const int Y0 = ((tile / ntx) % nty) * TY;
     const int Z0 = (tile / (ntx * nty)) * TZ;
@@ -247,7 +251,7 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     __syncthreads();
     const int nc = s.ncand;
     if (nst > kStage || nc > kCap) {
-        if (tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = tile;
+        if (tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = (req << 40) | (int64_t)tile;
         return;  // block-uniform: the per-voxel kernel takes this tile
     }
     for (int i = tid; i < nc; i += kThreads) {
@@ -293,14 +297,14 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     }
     for (int i = tid; i < nc; i += kThreads) {
         uint32_t m = 0;
-        const int NB[3] = {NBX, NBY, NBZ}, BB[3] = {BX, BY, BZ}, SH[3] = {0, NBX, NBX + NBY};
+        const int NB[3] = {NBX, NBY, NBZ}, BB[3] = {BX, BY, BZ}, SHF[3] = {0, NBX, NBX + NBY};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            if (d >= NDIM) { m |= 1u << SH[d]; continue; }
+            if (d >= NDIM) { m |= 1u << SHF[d]; continue; }
             const int lo = (int)ceilf(s.cpos[i][d]) - g.S[d], hi = lo + 2 * g.S[d] - 1;
             for (int b = 0; b < NB[d]; ++b) {
                 const int a0 = T0[d] + b * BB[d], a1 = a0 + BB[d] - 1;
-                if (lo <= a1 && hi >= a0) m |= 1u << (SH[d] + b);
+                if (lo <= a1 && hi >= a0) m |= 1u << (SHF[d] + b);
             }
         }
         s.bmask[i] = m;
@@ -333,7 +337,7 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     // ---- 3. warp boxes: assignment ------------------------------------------
     const int lx = lane % WX, ly = (lane / WX) % WY, lz = lane / (WX * WY);
     const uint32_t cdb = (uint32_t)__cvta_generic_to_shared(&s.cd[0]);
-    using CandT = Cand<C, NDIM>;
+    using CandT = Cand<C, SH>;
     constexpr int CDS = (int)sizeof(CandT);
     constexpr int kOffT1 = 8 * C;  // layout of Cand: fe, t1, t2, t0
     constexpr int kOffT2 = kOffT1 + 8 * TY;
@@ -517,31 +521,111 @@ assign_tile_kernel(Geom g, const T* __restrict__ img, const float* __restrict__ 
     }
 }
 
+// one image: one CTA per tile
+template <typename T, int C, typename SH>
+__global__ void __launch_bounds__(kThreads, 4)
+assign_tile_kernel(TileArgs a, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_body<T, C, SH>(a, blockIdx.x, 0, *reinterpret_cast<Smem<T, C, SH>*>(smem_raw), ovf_tiles, ovf_count);
+}
+
+// many images: a persistent grid walks one queue of (request, tile) work
+// items; request r owns global tile numbers [tpre[r], tpre[r + 1])
+template <typename T, int C, typename SH>
+__global__ void __launch_bounds__(kThreads, 4)
+assign_tile_queue_kernel(const TileArgs* __restrict__ reqs, const int64_t* __restrict__ tpre, int R,
+                         int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T, C, SH>& s = *reinterpret_cast<Smem<T, C, SH>*>(smem_raw);
+    const int64_t total = tpre[R];
+    for (int64_t i = blockIdx.x; i < total; i += gridDim.x) {
+        int lo = 0, hi = R - 1;  // last r with tpre[r] <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tpre[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        __syncthreads();  // the previous tile's shared state is no longer read
+        tile_body<T, C, SH>(reqs[lo], (int)(i - tpre[lo]), lo, s, ovf_tiles, ovf_count);
+    }
+}
+
 }  // namespace tile
 
-template <typename T, int C, int NDIM>
-int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+template <typename SH>
+static void tile_grid(const Geom& g, int& ntx, int& nty, int& ntz)
 {
-    using G = tile::Cfg<NDIM>;
+    ntx = (int)((g.N[0] + SH::TX - 1) / SH::TX);
+    nty = (int)((g.N[1] + SH::TY - 1) / SH::TY);
+    ntz = (int)((g.N[2] + SH::TZ - 1) / SH::TZ);
+}
+
+// expected number of centres reaching a tile of shape (tx, ty, tz)
+static double reach(const Geom& g, int tx, int ty, int tz)
+{
+    const int T[3] = {tx, ty, tz};
+    double r = 1.0;
+    for (int d = 0; d < g.n; ++d) r *= (double)(T[d] + 2 * g.S[d] - 1) / g.S[d];
+    return r;
+}
+
+int default_tile_shape(const Geom& g)
+{
+    // the large tile while it stays well inside the candidate capacity
+    const double lim = 0.75 * tile::kCap;
+    if (g.n == 3) return reach(g, tile::Shape3L::TX, tile::Shape3L::TY, tile::Shape3L::TZ) <= lim ? 0 : 1;
+    return reach(g, tile::Shape2L::TX, tile::Shape2L::TY, 1) <= lim ? 0 : 1;
+}
+
+template <typename T, int C, typename SH>
+static int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+{
     const Geom& g = c->g;
     Workspace& w = c->ws;
-    const int ntx = (int)((g.N[0] + G::TX - 1) / G::TX);
-    const int nty = (int)((g.N[1] + G::TY - 1) / G::TY);
-    const int ntz = (int)((g.N[2] + G::TZ - 1) / G::TZ);
+    int ntx, nty, ntz;
+    tile_grid<SH>(g, ntx, nty, ntz);
     const int64_t ntiles = (int64_t)ntx * nty * ntz;
-    const size_t smem = sizeof(tile::Smem<T, C, NDIM>);
-    int rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_kernel<T, C, NDIM>,
+    const size_t smem = sizeof(tile::Smem<T, C, SH>);
+    int rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_kernel<T, C, SH>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                         "smem attribute");
     if (rc) return rc;
     if ((rc = cuda_check(c, cudaMemsetAsync(w.ovf_count, 0, sizeof(unsigned), st), "memset ovf"))) return rc;
+    TileArgs a;
+    a.g = g;
+    a.img = img;
+    a.ctr = w.ctr;
+    a.bin_start = w.bin_start;
+    a.bin_items = w.bin_items;
+    a.labels = labels;
+    a.acc = w.acc;
+    a.facc = w.facc;
+    a.ntx = ntx;
+    a.nty = nty;
+    a.tx = SH::TX;
+    a.ty = SH::TY;
+    a.tz = SH::TZ;
     const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
-    tile::assign_tile_kernel<T, C, NDIM><<<(unsigned)ntiles, tile::kThreads, smem, st>>>(
-        g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc, w.ovf_tiles, w.ovf_count, ntx, nty);
+    tile::assign_tile_kernel<T, C, SH><<<(unsigned)ntiles, tile::kThreads, smem, st>>>(a, w.ovf_tiles, w.ovf_count);
     count_launch(c);
     prof_end(c, pr, st);
     if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_kernel"))) return rc;
-    return launch_voxel_tiles(c, img, labels, G::TX, G::TY, G::TZ, ntx, nty, st);
+    return launch_voxel_tiles(c, img, labels, SH::TX, SH::TY, SH::TZ, ntx, nty, st);
+}
+
+template <typename T, int C, int NDIM>
+int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+{
+    const int shape = c->tile_shape >= 0 ? c->tile_shape : default_tile_shape(c->g);
+    if constexpr (NDIM == 3) {
+        return shape == 0 ? launch_tile_shape<T, C, tile::Shape3L>(c, img, labels, st)
+                          : launch_tile_shape<T, C, tile::Shape3S>(c, img, labels, st);
+    } else {
+        return shape == 0 ? launch_tile_shape<T, C, tile::Shape2L>(c, img, labels, st)
+                          : launch_tile_shape<T, C, tile::Shape2S>(c, img, labels, st);
+    }
 }
 
 template int launch_tile_impl<uint8_t, 3, 3>(sslic_ctx*, const uint8_t*, int32_t*, cudaStream_t);
@@ -551,14 +635,60 @@ template int launch_tile_impl<uint8_t, 1, 2>(sslic_ctx*, const uint8_t*, int32_t
 template int launch_tile_impl<uint16_t, 1, 3>(sslic_ctx*, const uint16_t*, int32_t*, cudaStream_t);
 template int launch_tile_impl<uint16_t, 1, 2>(sslic_ctx*, const uint16_t*, int32_t*, cudaStream_t);
 
+// batched form: one persistent launch over the (request, tile) queue of all
+// requests of one type and shape; returns the CUDA error of the launch
+template <typename T, int C, typename SH>
+static cudaError_t launch_queue_shape(const TileArgs* reqs, const int64_t* tpre, int R, int64_t* ovf,
+                                      unsigned* ovf_count, int grid, cudaStream_t st)
+{
+    const size_t smem = sizeof(tile::Smem<T, C, SH>);
+    cudaError_t e = cudaFuncSetAttribute(tile::assign_tile_queue_kernel<T, C, SH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tile::assign_tile_queue_kernel<T, C, SH><<<grid, tile::kThreads, smem, st>>>(reqs, tpre, R, ovf, ovf_count);
+    return cudaGetLastError();
+}
+
+template <typename T, int C, int NDIM>
+cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, int R, int64_t* ovf,
+                              unsigned* ovf_count, int grid, cudaStream_t st)
+{
+    if constexpr (NDIM == 3)
+        return shape == 0 ? launch_queue_shape<T, C, tile::Shape3L>(reqs, tpre, R, ovf, ovf_count, grid, st)
+                          : launch_queue_shape<T, C, tile::Shape3S>(reqs, tpre, R, ovf, ovf_count, grid, st);
+    else
+        return shape == 0 ? launch_queue_shape<T, C, tile::Shape2L>(reqs, tpre, R, ovf, ovf_count, grid, st)
+                          : launch_queue_shape<T, C, tile::Shape2S>(reqs, tpre, R, ovf, ovf_count, grid, st);
+}
+
+template cudaError_t launch_tile_queue<uint8_t, 3, 3>(int, const TileArgs*, const int64_t*, int, int64_t*, unsigned*, int, cudaStream_t);
+template cudaError_t launch_tile_queue<uint8_t, 3, 2>(int, const TileArgs*, const int64_t*, int, int64_t*, unsigned*, int, cudaStream_t);
+template cudaError_t launch_tile_queue<uint8_t, 1, 3>(int, const TileArgs*, const int64_t*, int, int64_t*, unsigned*, int, cudaStream_t);
+template cudaError_t launch_tile_queue<uint8_t, 1, 2>(int, const TileArgs*, const int64_t*, int, int64_t*, unsigned*, int, cudaStream_t);
+template cudaError_t launch_tile_queue<uint16_t, 1, 3>(int, const TileArgs*, const int64_t*, int, int64_t*, unsigned*, int, cudaStream_t);
+template cudaError_t launch_tile_queue<uint16_t, 1, 2>(int, const TileArgs*, const int64_t*, int, int64_t*, unsigned*, int, cudaStream_t);
+
+// tile dimensions of a shape (host side)
+void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz)
+{
+    if (ndim == 3) {
+        *tx = shape == 0 ? tile::Shape3L::TX : tile::Shape3S::TX;
+        *ty = shape == 0 ? tile::Shape3L::TY : tile::Shape3S::TY;
+        *tz = shape == 0 ? tile::Shape3L::TZ : tile::Shape3S::TZ;
+    } else {
+        *tx = shape == 0 ? tile::Shape2L::TX : tile::Shape2S::TX;
+        *ty = shape == 0 ? tile::Shape2L::TY : tile::Shape2S::TY;
+        *tz = 1;
+    }
+}
+
+// the most tiles any shape cuts the image into (sizes the crowded-tile list)
 int64_t assign_num_tiles(const Geom& g)
 {
-    if (g.n == 3) {
-        using T3 = tile::Cfg<3>;
-        return ((g.N[0] + T3::TX - 1) / T3::TX) * ((g.N[1] + T3::TY - 1) / T3::TY) * ((g.N[2] + T3::TZ - 1) / T3::TZ);
-    }
-    using T2 = tile::Cfg<2>;
-    return ((g.N[0] + T2::TX - 1) / T2::TX) * ((g.N[1] + T2::TY - 1) / T2::TY) * g.N[2];
+    int ntx, nty, ntz;
+    if (g.n == 3) tile_grid<tile::Shape3S>(g, ntx, nty, ntz);
+    else tile_grid<tile::Shape2S>(g, ntx, nty, ntz);
+    return (int64_t)ntx * nty * ntz;
 }
 
 }  // namespace sslic

@@ -110,7 +110,7 @@ __device__ __forceinline__ int64_t ccl_tile_of(const Geom& g, int64_t x, int64_t
 template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restrict__ lid_img,
-                 int* __restrict__ tile_base, int* __restrict__ comp_label, unsigned* __restrict__ comp_size,
+                 int* __restrict__ tile_base, int* __restrict__ tile_cnt, int* __restrict__ comp_label, unsigned* __restrict__ comp_size,
                  unsigned long long* __restrict__ comp_first, int* __restrict__ gparent,
                  unsigned* __restrict__ counters, int64_t m_cap, int64_t ntx, int64_t nty)
 {
@@ -161,9 +161,20 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             uf_unite(par, e, e - TX * TY, &counters[3]);
     }
     __syncthreads();
-    for (int e = tid; e < kCclTV; e += kCclThreads)
-        if (par[e] >= 0) par[e] = uf_root(par, e, &counters[3]);
-    __syncthreads();
+    // compress by synchronous pointer jumping: each round halves every chain;
+    // a value read while another thread rewrites it is an ancestor either way
+    for (int round = 0; round < 32; ++round) {
+        int changed = 0;
+        for (int i = 0; i < kPerThread; ++i) {
+            const int e = e0 + i;
+            const int p = par[e];
+            if (p < 0) continue;
+            const int gp = par[p];
+            if (gp != p) { par[e] = gp; changed = 1; }
+        }
+        if (!__syncthreads_or(changed)) break;
+        if (round == 31) atomicExch(&counters[3], 1u);
+    }
     // rank the roots (the tile-raster-first voxel of each local component)
     unsigned mine = 0;
     for (int i = 0; i < kPerThread; ++i) {
@@ -201,7 +212,23 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const uint16_t l = lidv[par[e]];
         int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
-        atomicAdd(&sz[l], 1u);
+    }
+    // sizes: runs of one component along the thread's 8 consecutive voxels,
+    // one shared atomic per run
+    {
+        int cur = -1;
+        unsigned run = 0;
+        for (int i = 0; i < kPerThread; ++i) {
+            const int e = e0 + i;
+            const int l = par[e] < 0 ? -1 : (int)lidv[par[e]];
+            if (l != cur) {
+                if (cur >= 0) atomicAdd(&sz[cur], run);
+                cur = l;
+                run = 0;
+            }
+            ++run;
+        }
+        if (cur >= 0) atomicAdd(&sz[cur], run);
     }
     __syncthreads();
     for (int e = tid; e < kCclTV; e += kCclThreads) {
@@ -213,7 +240,10 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         comp_first[r] = (unsigned long long)vidx(g, X0 + xl, Y0 + yl, Z0 + zl);
         gparent[r] = r;
     }
-    if (tid == 0) tile_base[tile] = base;
+    if (tid == 0) {
+        tile_base[tile] = base;
+        tile_cnt[tile] = (int)total;
+    }
 }
 
 template <int NDIM>
@@ -239,7 +269,7 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
     for (int d = 0; d < 3; ++d) E[d] = (int)imin64(TT[d], g.N[d] - T0[d]);
     for (int d = 0; d < NDIM; ++d) {
         if (T0[d] == 0) continue;
-        const int a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+        const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 3 - d - a1;  // a1: the longer in-plane axis
         const int n = E[a1] * E[a2];
         for (int i = threadIdx.x; i < n; i += kCclThreads) {
             int64_t p[3];
@@ -435,22 +465,32 @@ __global__ void conn_resolve_kernel(const int* __restrict__ gparent, const int* 
 template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
-                    const int* __restrict__ gparent, const int* __restrict__ out_label,
-                    const int* __restrict__ comp_label, int32_t* __restrict__ labels_out, int inplace,
-                    int64_t ntx, int64_t nty)
+                    const int* __restrict__ tile_cnt, const int* __restrict__ gparent,
+                    const int* __restrict__ out_label, const int* __restrict__ comp_label,
+                    int32_t* __restrict__ labels_out, int inplace, int64_t ntx, int64_t nty)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY;
+    __shared__ int tab[kCclTV];       // local component -> output label
+    __shared__ uint8_t chg[kCclTV];   // ... and whether it differs from the input label
     const int64_t tile = blockIdx.x;
     const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * Cfg::TZ;
     const int base = tile_base[tile];
+    const int nloc = tile_cnt[tile];
+    for (int l = threadIdx.x; l < nloc; l += kCclThreads) {
+        const int r = base + l;
+        const int G = gparent[r];
+        const int o = out_label[G];
+        tab[l] = o;
+        chg[l] = (o != comp_label[r]) ? 1 : 0;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < kCclTV; e += kCclThreads) {
         int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
         if (x >= g.N[0] || y >= g.N[1] || z >= g.N[2]) continue;
         const int64_t q = vidx(g, x, y, z);
-        const int G = gparent[base + lid_img[q]];
-        const int o = out_label[G];
-        if (!inplace || o != comp_label[G]) labels_out[q] = o;
+        const int l = lid_img[q];
+        if (!inplace || chg[l]) labels_out[q] = tab[l];
     }
 }
 
@@ -471,7 +511,8 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
     for (int attempt = 0; attempt < 2; ++attempt) {
         if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
-        ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.comp_label,
+        ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
+                                                              w.comp_label,
                                                               w.comp_size, w.comp_first, w.gparent, w.counters,
                                                               w.m_cap, ntx, nty);
         count_launch(c);
@@ -553,8 +594,8 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     conn_resolve_kernel<<<gb, 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
-    conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.gparent, w.out_label,
-                                                              w.comp_label, labels_out,
+    conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,
+                                                              w.out_label, w.comp_label, labels_out,
                                                               labels_in == labels_out ? 1 : 0, ntx, nty);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;

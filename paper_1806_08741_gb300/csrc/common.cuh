@@ -93,6 +93,21 @@ __device__ __forceinline__ int64_t bin_of_coord(float c, int S, int64_t nb)
     return b >= nb ? nb - 1 : b;
 }
 
+// one image's arguments of the assignment kernels (one entry per request in
+// the batched form)
+struct TileArgs {
+    Geom g;
+    const void* img;
+    const float* ctr;
+    const unsigned* bin_start;
+    const int* bin_items;
+    int32_t* labels;
+    unsigned long long* acc;
+    double* facc;
+    int ntx, nty;     // tile grid of the tile shape in use
+    int tx, ty, tz;   // that shape's tile dimensions
+};
+
 // ---- context ---------------------------------------------------------------
 struct Workspace {
     // centres and update sums
@@ -119,7 +134,8 @@ struct Workspace {
     // connectivity
     uint16_t* lid = nullptr;            // V
     int64_t n_ccl_tiles = 0;
-    int* tile_base = nullptr;           // n_ccl_tiles
+    int* tile_base = nullptr;           // n_ccl_tiles: first component record of each tile
+    int* tile_cnt = nullptr;            // n_ccl_tiles: component records of each tile
     unsigned* counters = nullptr;       // [0] M, [1] overflow, [2] new count
     int64_t m_cap = 0;
     int* comp_label = nullptr;
@@ -158,6 +174,7 @@ struct sslic_ctx {
     int device = 0;
     int sms = 148;
     int busy = 0;
+    int tile_shape = -1;   // assignment tile shape: -1 = chosen from the grid, 0 = large, 1 = small
     char err[512] = {0};
     // tracing
     int prof_on = 0;
@@ -180,6 +197,11 @@ int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t 
 size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
+int default_tile_shape(const Geom& g);
+void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz);
+template <typename T, int C, int NDIM>
+cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, int R, int64_t* ovf,
+                              unsigned* ovf_count, int grid, cudaStream_t st);
 template <typename T, int C, int NDIM>
 int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st);
 template <typename T>

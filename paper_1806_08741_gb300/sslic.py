@@ -23,8 +23,10 @@ _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUSY",
 
 EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_run",
            "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
-           "sslic_connectivity", "sslic_iterate_static", "sslic_profile_enable",
-           "sslic_profile_read", "sslic_destroy", "sslic_strerror", "sslic_last_error")
+           "sslic_connectivity", "sslic_iterate_static", "sslic_server_create",
+           "sslic_server_submit", "sslic_server_wait", "sslic_server_stats_get",
+           "sslic_server_destroy", "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
+           "sslic_strerror", "sslic_last_error")
 PHASES = ("seed", "bins", "assign", "assign_voxel", "finalize", "connectivity")
 
 
@@ -55,6 +57,23 @@ class _Profile(ctypes.Structure):
         ("ms", ctypes.c_double * 8),
         ("calls", ctypes.c_int64 * 8),
         ("kernel_launches", ctypes.c_int64),
+    ]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("rejected", ctypes.c_int64),
+        ("rounds", ctypes.c_int64),
+        ("max_active", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("peak_bytes", ctypes.c_int64),
+        ("voxel_iters", ctypes.c_double),
+        ("busy_s", ctypes.c_double),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double),
     ]
 
 
@@ -91,6 +110,15 @@ def load(path: str = LIB_PATH):
     L.sslic_seed.argtypes = [C, vp, vp, vp]
     L.sslic_iterate.argtypes = [C, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sslic_connectivity.argtypes = [C, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    S_ = ctypes.c_void_p  # sslic_server*
+    L.sslic_server_create.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(S_)]
+    L.sslic_server_submit.argtypes = [S_, P, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.sslic_server_wait.argtypes = [S_, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
+    L.sslic_server_stats_get.argtypes = [S_, ctypes.POINTER(_ServerStats)]
+    L.sslic_server_destroy.argtypes = [S_]
+    L.sslic_server_destroy.restype = None
+    for f in ("sslic_server_create", "sslic_server_submit", "sslic_server_wait", "sslic_server_stats_get"):
+        getattr(L, f).restype = ctypes.c_int
     L.sslic_iterate_static.argtypes = [P, vp, vp, vp, vp, vp]
     L.sslic_iterate_static.restype = ctypes.c_int
     L.sslic_profile_enable.argtypes = [C, ctypes.c_int32]
@@ -356,6 +384,70 @@ def iterate_static(params: Params, image, centres_in, labels, centres_out, strea
                                 _ptr(labels), _ptr(centres_out), _stream(stream))
     if rc != SSLIC_OK:
         raise SSLICError(rc, "sslic_iterate_static")
+
+
+class Server:
+    """Continuous-batching server (sslic_server_*): requests of any size, grid
+    and type are kept on the device and advanced together, one iteration per
+    round, one launch per phase for the whole batch; admission is bounded by
+    a device-memory budget.  Host buffers passed to submit() must stay alive
+    until wait() returns for the ticket (this object keeps references)."""
+
+    def __init__(self, budget_bytes: int, max_active: int = 64):
+        self.lib = load()
+        self._s = ctypes.c_void_p(0)
+        rc = self.lib.sslic_server_create(int(budget_bytes), int(max_active), ctypes.byref(self._s))
+        if rc != SSLIC_OK:
+            raise SSLICError(rc, "sslic_server_create")
+        self._keep = {}
+
+    def submit(self, params: Params, image, labels, centres=None) -> int:
+        t = ctypes.c_int64(0)
+        rc = self.lib.sslic_server_submit(self._s, ctypes.byref(params.to_c()), _ptr(image), _ptr(labels),
+                                          _ptr(centres), ctypes.byref(t))
+        if rc != SSLIC_OK:
+            raise SSLICError(rc, "sslic_server_submit")
+        self._keep[int(t.value)] = (image, labels, centres)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0) -> float:
+        """Block until the ticket is done; returns its latency in ms."""
+        lat = ctypes.c_double(0.0)
+        import time
+        t_end = time.monotonic() + timeout_s
+        while True:
+            rc = self.lib.sslic_server_wait(self._s, int(ticket), 100, ctypes.byref(lat))
+            if rc == -4 and time.monotonic() < t_end:   # still running
+                continue
+            self._keep.pop(int(ticket), None)
+            if rc != SSLIC_OK:
+                raise SSLICError(rc, "sslic_server_wait")
+            return lat.value
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        rc = self.lib.sslic_server_stats_get(self._s, ctypes.byref(st))
+        if rc != SSLIC_OK:
+            raise SSLICError(rc, "sslic_server_stats_get")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._s:
+            self.lib.sslic_server_destroy(self._s)
+            self._s = ctypes.c_void_p(0)
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def segment(image, grid, stream=None, **kw):

@@ -1,0 +1,100 @@
+"""Batched / served form: each request's result in the mix equals the same
+request run alone through the single-image path (integer images: bit for
+bit), under a budget small enough that requests wait for admission; and the
+first small ones equal the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_08741_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(seed=3):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(10):
+        side = int(rng.integers(60, 400))
+        h = int(rng.integers(50, 300))
+        img = I.make_image(I.ImageSpec((side, h), 3, "u8", 100 + i, max(2, side * h // 3000), 6))
+        S = int(rng.choice([8, 16, 32]))
+        m = float(rng.choice([5.0, 10.0, 20.0]))
+        reqs.append((img, (S, S), m))
+    for i in range(4):
+        side = int(rng.integers(30, 72))
+        img = I.make_image(I.ImageSpec((side, side + 3, side - 5), 1, "u16", 200 + i, 12, 300))
+        S = int(rng.choice([8, 16]))
+        reqs.append((img, (S, S, S), 10.0))
+    # a type without a tile kernel (per-voxel path in the batch)
+    reqs.append((I.make_image(I.ImageSpec((90, 70), 2, "u8", 300, 10, 6)), (8, 8), 10.0))
+    return reqs
+
+
+def _alone(img, grid, m, iters):
+    import torch
+    from paper_1806_08741_gb300 import sslic as S
+    p = S.params_for(img, grid, m=m, max_iter=iters)
+    with S.Context(p) as ctx:
+        lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+        cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+        ctx.run(torch.from_numpy(img).cuda(), lab, cen)
+        return lab.cpu().numpy(), cen.cpu().numpy()
+
+
+@pytest.mark.parametrize("budget_mb", [2048, 24])
+def test_served_results_equal_alone(budget_mb):
+    import torch
+    from paper_1806_08741_gb300 import sslic as S
+    reqs = _mix()
+    iters = 6
+    outs = []
+    with S.Server(budget_mb << 20, max_active=8) as srv:
+        tickets = []
+        for img, grid, m in reqs:
+            p = S.params_for(img, grid, m=m, max_iter=iters)
+            lab = np.empty(img.shape[:-1], np.int32)
+            K = 1
+            for n, g in zip(p.size, p.grid):
+                K *= -(-n // g)
+            cen = np.empty((K, p.channels + p.ndim), np.float32)
+            tickets.append(srv.submit(p, img, lab, cen))
+            outs.append((lab, cen))
+        lat = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["completed"] == len(reqs) and st["status"] == 0
+    assert all(x > 0 for x in lat)
+    if budget_mb == 24:
+        assert st["max_active"] < len(reqs)   # admission had to wait for memory
+    for (img, grid, m), (lab, cen) in zip(reqs, outs):
+        ref_l, ref_c = _alone(img, grid, m, iters)
+        np.testing.assert_array_equal(lab, ref_l)
+        np.testing.assert_array_equal(cen, ref_c)
+
+
+def test_served_small_requests_equal_oracle():
+    from paper_1806_08741_gb300 import sslic as S
+    reqs = _mix(5)[:3]
+    with S.Server(512 << 20) as srv:
+        res = []
+        for img, grid, m in reqs:
+            p = S.params_for(img, grid, m=m, max_iter=4)
+            lab = np.empty(img.shape[:-1], np.int32)
+            res.append((srv.submit(p, img, lab), lab, img, grid, m))
+        for t, lab, img, grid, m in res:
+            srv.wait(t)
+            ref = O.slic(O.params_for(img, grid, m=m, max_iter=4), img)
+            np.testing.assert_array_equal(lab, ref["labels"])
+
+
+def test_server_rejects():
+    from paper_1806_08741_gb300 import sslic as S
+    img = np.zeros((512, 512, 3), np.uint8)
+    lab = np.empty((512, 512), np.int32)
+    with S.Server(1 << 20) as srv:
+        with pytest.raises(S.SSLICError) as e:
+            srv.submit(S.params_for(img, (16, 16)), img, lab)   # larger than the whole budget
+        assert e.value.code == -2
+        with pytest.raises(S.SSLICError) as e:
+            srv.submit(S.params_for(img, (16, 16), enforce_connectivity=True), img, lab)
+        assert e.value.code == -6

@@ -219,6 +219,13 @@ def run_ours(args, w):
     ctx = S.Context(p)
     centres = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device=dev)
     V = spec.voxels
+    # launch configuration: measured tile shape (before any timed work)
+    tune = None
+    if not args.no_autotune:
+        t = ctx.autotune(img, labels, reps=2, stream=stream)
+        info_s = S.tile_shape_info(p.ndim, t["best"])
+        tune = {"shape": t["best"], "dims": info_s["dims"], "voxels_per_lane": info_s["voxels_per_lane"],
+                "ms_per_shape": t["ms"]}
 
     for _ in range(args.warmup):
         info = ctx.run(img, labels, centres, stream=stream)
@@ -259,14 +266,19 @@ def run_ours(args, w):
         avg_s = a_ms / a_calls / 1e3
         algo = V * bytes_per_vox
         achieved = algo / avg_s / 1e9
-        src = _sha(os.path.join(ROOT, "paper_1806_08741_gb300", "csrc", "assign.cu"))
+        src = _sha(os.path.join(ROOT, "paper_1806_08741_gb300", "csrc", "assign_tile.cuh"))
         roof = {"kernel": "assign_tile_kernel (fused assign + map-update)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"of {peak_src}", "bytes_per_launch": algo,
                 "bytes_per_voxel": bytes_per_vox, "avg_launch_ms": a_ms / a_calls,
                 "traffic": TRAFFIC_BYTES.get((w.name, src))}
     phases = {k: {"ms_per_step": v[0] / args.steps, "calls_per_step": v[1] / args.steps}
-              for k, v in prof.items() if k != "kernel_launches"}
+              for k, v in prof.items() if k in S.PHASES}
+    # the iterated assign/update loop alone (bins + assignment + reduction),
+    # seeding and connectivity excluded
+    loop_ms = sum(prof[k][0] for k in ("bins", "assign", "assign_voxel", "finalize")) / args.steps
+    loop = {"value": V * iters / (loop_ms / 1e3) / 1e9 if loop_ms > 0 else None, "unit": UNIT,
+            "ms_per_step": loop_ms}
 
     # end to end through the host-buffer entry point
     e2e = None
@@ -314,6 +326,7 @@ def run_ours(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {**_config(w), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
+            "tile_shape": tune, "assign_update_loop": loop,
             "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }
@@ -459,6 +472,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="use the built-in tile shape")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
     ap.add_argument("--reference-edge", type=int, default=128,

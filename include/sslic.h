@@ -65,7 +65,12 @@ typedef struct {
     double  conv_threshold; /* stop once the centre residual drops below this; <= 0 disables (Sec. 3.1) */
     int32_t perturb;        /* 1: move seeds to the lowest gradient in the 3^n neighbourhood (Sec. 3.1) */
     int32_t enforce_connectivity; /* 1: run the connectivity enforcement of Sec. 3.1 stage 3 */
-    int32_t precision;      /* 0: exact FP32 distances (only value accepted by this build) */
+    int32_t precision;      /* 0: exact FP32 distances.  1: the feature term of float images with
+                             * 32..128 channels (2-D / 3-D) from BF16 tensor-core dot products,
+                             * with an exact FP32 recheck of every voxel whose candidates the
+                             * error bound does not separate, so labels equal those of 0.
+                             * SSLIC_EINVAL for C < 32, SSLIC_EUNSUPPORTED for other images.
+                             * This form goes beyond the paper (Sec. 2.1 only defines D). */
 } sslic_params;
 
 typedef struct {
@@ -159,10 +164,76 @@ SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const i
 SSLIC_API int sslic_iterate_static(const sslic_params* p, const void* image_dev, const float* centres_in_dev,
                                    int32_t* labels_dev, float* centres_out_dev, void* stream);
 
+/* Launch configuration of the assignment kernel.  The paper has no
+ * counterpart: its multi-threaded filter splits the image into regions per
+ * thread (Sec. 3.1), while here a tile shape fixes how voxels map to CUDA
+ * blocks and lanes.  A shape is a tile extent plus the voxels each lane
+ * handles (2 or 4 consecutive voxels along x); it changes speed only, never
+ * a label or a centre.  Shapes exist for 2-D and 3-D images of uint8 with 1
+ * or 3 channels and uint16 with 1 channel; other images use the per-voxel
+ * kernel and report shape -1.  Shape indices run over
+ * [0, sslic_num_tile_shapes(ndim)); -1 selects the measured shape from
+ * sslic_autotune if one was recorded for this (dtype, channels, dims, grid),
+ * else the built-in rule (the large tile unless too many centres reach it). */
+SSLIC_API int sslic_num_tile_shapes(int32_t ndim, int32_t* count);
+
+/* dims (host, 3 int32): tile extent along x, y, z; voxels_per_lane may be
+ * NULL.  SSLIC_EINVAL for an unknown shape. */
+SSLIC_API int sslic_tile_shape_info(int32_t ndim, int32_t shape, int32_t* dims, int32_t* voxels_per_lane);
+
+/* Fix the context's shape (-1: back to automatic).  SSLIC_EUNSUPPORTED if
+ * the image type has no tile kernel. */
+SSLIC_API int sslic_set_tile_shape(sslic_ctx* c, int32_t shape);
+
+/* The shape the next run will use (host int32). */
+SSLIC_API int sslic_get_tile_shape(const sslic_ctx* c, int32_t* shape);
+
+/* Measure every shape on this image and keep the fastest.  Seeds the image,
+ * then for each shape runs reps + 1 assign + update iterations from the
+ * same seeded centres (the first one warms up) and takes the median time of
+ * the rest, measured with CUDA events on `stream`.  The fastest shape is set
+ * on the context and recorded in a process-wide table for the image's
+ * (dtype, channels, dims, grid), which later contexts and servers use.
+ * labels_dev (V int32, device) is overwritten as scratch; best (host, may be
+ * NULL) receives the chosen index and ms_out (host, may be NULL, at least
+ * sslic_num_tile_shapes entries) the median milliseconds per shape.  Blocks
+ * until the measurements are done; allocates one centre table.  Returns
+ * SSLIC_EUNSUPPORTED for image types without a tile kernel. */
+SSLIC_API int sslic_autotune(sslic_ctx* c, const void* image_dev, int32_t* labels_dev, void* stream,
+                             int32_t reps, int32_t* best, float* ms_out);
+
+/* Diagnostic of the tensor-core form (precision = 1): runs its MMA on one
+ * assignment tile of the image (128 voxels: 16x8 in 2-D, 8x4x4 in 3-D, tiles
+ * numbered in raster order) with the given centres (device, K x (C+n)) and
+ * returns what the tensor core computed, before any decision:
+ *   dots_host  (host, 128 x 32 float): dots[v][j] = sum_c bf16(x_v,c - mu_c) *
+ *              bf16(C_j,c - mu_c), v = voxel of the tile in raster order
+ *              (x fastest), j = candidate slot; slots past the candidates hold 0
+ *   cand_host  (host, 32 int32): cluster index per slot (ascending), -1 = empty
+ *   mu_host    (host, C float): the shift mu (mean of the candidates' features)
+ * SSLIC_EINVAL if the context is not of the tensor-core form or the tile is
+ * out of range; SSLIC_EUNSUPPORTED if more than 32 centres reach the tile. */
+SSLIC_API int sslic_precision_probe(sslic_ctx* c, const void* image_dev, const float* centres_dev, int64_t tile,
+                                    float* dots_host, int32_t* cand_host, float* mu_host);
+
+/* Clear the process-wide table of measured shapes. */
+SSLIC_API int sslic_tune_forget(void);
+
+/* Write (shape >= 0) or read an entry of that table for the (dtype,
+ * channels, dims, grid) of p, e.g. to restore measurements saved by an
+ * earlier process.  Lookup gives -1 when there is no entry.  SSLIC_EINVAL
+ * for bad parameters or shape, SSLIC_EUNSUPPORTED for image types without a
+ * tile kernel.  Host only. */
+SSLIC_API int sslic_tune_record(const sslic_params* p, int32_t shape);
+SSLIC_API int sslic_tune_lookup(const sslic_params* p, int32_t* shape);
+
 /* Serving (continuous batching).  A server keeps requests on the device and
  * advances all admitted requests together, one assign/update iteration per
  * round, each round running one launch per phase over every request of the
- * batch (batched form of Sec. 3.1 step 2).  Requests that have done their
+ * batch (batched form of Sec. 3.1 step 2).  A round's kernels read their
+ * request counts from device tables, so each form of round (which image
+ * types and tile shapes, whether requests join or finish) is captured once
+ * as a CUDA graph and replayed.  Requests that have done their
  * iterations leave after the round and queued requests are admitted, first
  * come first served, as soon as the HBM budget has room for their image,
  * labels, centres, bins and sums.  Each request's labels and centres are the
@@ -179,6 +250,8 @@ typedef struct {
     double  voxel_iters;                     /* sum of voxels x iterations of completed requests */
     double  busy_s;                          /* first admission to last completion, seconds */
     double  p50_ms, p99_ms, mean_ms;         /* latency: submission to result in host memory */
+    int64_t graph_launches;                  /* rounds replayed from a captured CUDA graph */
+    int64_t graph_captures;                  /* distinct round forms captured */
 } sslic_server_stats;
 
 /* Start a server on the current device with a device-memory budget for
@@ -220,6 +293,7 @@ typedef struct {
     double ms[8];             /* device milliseconds per phase */
     int64_t calls[8];         /* timed executions per phase */
     int64_t kernel_launches;  /* kernels this context launched since the last enable */
+    int64_t rechecks;         /* voxels the tensor-core form re-evaluated in exact FP32 */
 } sslic_profile;
 
 /* Turn phase timing on (1) or off (0); both reset the counters. */

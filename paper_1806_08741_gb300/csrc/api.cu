@@ -84,7 +84,12 @@ static int validate(const sslic_params* p, Geom* g)
     if (p->max_iter < 1) return SSLIC_EINVAL;
     if (p->perturb != 0 && p->perturb != 1) return SSLIC_EINVAL;
     if (p->enforce_connectivity != 0 && p->enforce_connectivity != 1) return SSLIC_EINVAL;
-    if (p->precision != 0) return p->precision == 1 ? SSLIC_EUNSUPPORTED : SSLIC_EINVAL;
+    if (p->precision != 0 && p->precision != 1) return SSLIC_EINVAL;
+    if (p->precision == 1) {
+        // the tensor-core feature term: float images with 32..128 channels, 2-D / 3-D
+        if (p->channels < 32) return SSLIC_EINVAL;
+        if (p->dtype != SSLIC_F32 || p->channels > 128 || (p->ndim != 2 && p->ndim != 3)) return SSLIC_EUNSUPPORTED;
+    }
     Geom& G = *g;
     memset(&G, 0, sizeof(G));
     G.n = p->ndim;
@@ -163,7 +168,7 @@ static void free_all(sslic_ctx* c)
     dfree(w.ctr); dfree(w.acc); dfree(w.facc); dfree(w.resid_k); dfree(w.nonempty_k);
     dfree(w.resid_part); dfree(w.resid_cnt_part); dfree(w.resid_out);
     dfree(w.bin_count); dfree(w.bin_start); dfree(w.bin_cursor); dfree(w.bin_items); dfree(w.bin_of);
-    dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count);
+    dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count); dfree(w.hc_err); dfree(w.hc_rechecks);
     dfree(w.lid); dfree(w.tile_base); dfree(w.tile_cnt); dfree(w.counters);
     dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
@@ -193,6 +198,11 @@ static int alloc_core(sslic_ctx* c)
     w.scan_tmp_len = scan_tmp_needed((int64_t)K + 1);
     if ((rc = dalloc(c, &w.scan_tmp, w.scan_tmp_len, "scan"))) return rc;
     w.n_assign_tiles = assign_num_tiles(g);
+    if (hc_applies(g)) w.n_assign_tiles = imax64(w.n_assign_tiles, hc_num_tiles(g));
+    if ((rc = dalloc(c, &w.hc_err, 1, "status"))) return rc;
+    if ((rc = dalloc(c, &w.hc_rechecks, 1, "counters"))) return rc;
+    if ((rc = cuda_check(c, cudaMemset(w.hc_err, 0, sizeof(unsigned)), "memset"))) return rc;
+    if ((rc = cuda_check(c, cudaMemset(w.hc_rechecks, 0, sizeof(unsigned long long)), "memset"))) return rc;
     if ((rc = dalloc(c, &w.ovf_tiles, (size_t)w.n_assign_tiles, "tiles"))) return rc;
     if ((rc = dalloc(c, &w.ovf_count, 1, "tiles"))) return rc;
     if ((rc = cuda_check(c, cudaMemset(w.acc, 0, K * g.AW * sizeof(unsigned long long)), "memset sums"))) return rc;
@@ -205,12 +215,22 @@ static int alloc_core(sslic_ctx* c)
     return SSLIC_OK;
 }
 
-struct Busy {
-    sslic_ctx* c;
-    bool ok;
-    explicit Busy(sslic_ctx* c_) : c(c_) { ok = __sync_bool_compare_and_swap(&c->busy, 0, 1); }
-    ~Busy() { if (ok) __sync_lock_release(&c->busy); }
-};
+// the tensor-core form's bounded waits: a wait that ran out is reported
+// (and its flag cleared) after the stream has drained
+static int check_precision_status(sslic_ctx* c, cudaStream_t st)
+{
+    if (c->p.precision != 1) return SSLIC_OK;
+    unsigned h = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&h, c->ws.hc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                        "read status");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(st), "sync");
+    if (rc) return rc;
+    if (h) {
+        cudaMemsetAsync(c->ws.hc_err, 0, sizeof(unsigned), st);
+        return set_error(c, SSLIC_ETIMEOUT, "tensor-core assignment: a bounded wait ran out");
+    }
+    return SSLIC_OK;
+}
 
 static int read_residual(sslic_ctx* c, cudaStream_t st, double* r)
 {
@@ -236,6 +256,7 @@ static int run_loop(sslic_ctx* c, const void* image, int32_t* labels, float* cen
             if (res < c->p.conv_threshold) { ++it; break; }
         }
     }
+    if ((rc = check_precision_status(c, st))) return rc;
     int64_t nlab = c->g.K;
     if (c->p.enforce_connectivity) {
         if ((rc = ensure_ccl_capacity(c, 32 * c->g.K + c->g.V / 1024 + 4096))) return rc;
@@ -393,6 +414,7 @@ int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* centres_in_d
     if ((rc = launch_assign_update(c, image_dev, labels_dev, st))) return rc;
     if ((rc = launch_finalize(c, st))) return rc;
     if ((rc = launch_export_centres(c, centres_out_dev, st))) return rc;
+    if ((rc = check_precision_status(c, st))) return rc;
     if (residual_host) return read_residual(c, st, residual_host);
     return SSLIC_OK;
 }
@@ -419,7 +441,7 @@ int sslic_profile_enable(sslic_ctx* c, int32_t on)
     c->prof_on = on ? 1 : 0;
     c->prof.clear();
     c->launches = 0;
-    return SSLIC_OK;
+    return cuda_check(c, cudaMemset(c->ws.hc_rechecks, 0, sizeof(unsigned long long)), "reset counters");
 }
 
 int sslic_profile_read(sslic_ctx* c, sslic_profile* out)
@@ -437,7 +459,10 @@ int sslic_profile_read(sslic_ctx* c, sslic_profile* out)
         }
     }
     out->kernel_launches = c->launches;
-    return SSLIC_OK;
+    unsigned long long rk = 0;
+    int rc = cuda_check(c, cudaMemcpy(&rk, c->ws.hc_rechecks, sizeof(rk), cudaMemcpyDeviceToHost), "read counters");
+    out->rechecks = (int64_t)rk;
+    return rc;
 }
 
 void sslic_destroy(sslic_ctx* c)

@@ -86,6 +86,7 @@ template int launch_voxel_tiles<uint8_t>(sslic_ctx*, const uint8_t*, int32_t*, i
                                          cudaStream_t);
 template int launch_voxel_tiles<uint16_t>(sslic_ctx*, const uint16_t*, int32_t*, int, int, int, int, int,
                                           cudaStream_t);
+template int launch_voxel_tiles<float>(sslic_ctx*, const float*, int32_t*, int, int, int, int, int, cudaStream_t);
 
 template <typename T>
 static int launch_voxel(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
@@ -116,6 +117,7 @@ int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStr
         return g.n == 3 ? launch_tile_impl<uint16_t, 1, 3>(c, (const uint16_t*)img, labels, st)
                         : launch_tile_impl<uint16_t, 1, 2>(c, (const uint16_t*)img, labels, st);
     }
+    if (hc_applies(g)) return launch_hc(c, (const float*)img, labels, st);
     switch (g.dtype) {
     case SSLIC_U8: return launch_voxel<uint8_t>(c, (const uint8_t*)img, labels, st);
     case SSLIC_U16: return launch_voxel<uint16_t>(c, (const uint16_t*)img, labels, st);

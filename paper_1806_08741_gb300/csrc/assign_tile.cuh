@@ -1,0 +1,712 @@
+// assign_tile.cuh -- the fused assignment + map-update kernel for integer
+// images with 1 or 3 channels (2-D and 3-D): one SSLIC iteration's hot loop.
+// The kernel templates live here; assign_tile_<type>.cu files instantiate
+// them per image type (separate translation units compile in parallel) and
+// assign_tile.cu holds the shape table.
+//
+// Assignment (Sec. 2.1, 2.2, 3.1 step 2): every voxel takes the argmin of
+//     D^2 = sum_c (I_c - C_c)^2 + sum_d w_d (x_d - c_d)^2,  w_d = m^2 / S_d^2
+// over the centres whose window c_d - S_d <= x_d < c_d + S_d covers it, ties
+// to the lowest cluster index (the paper visits centres in ascending k and
+// replaces only on a strictly smaller distance).  D^2 is computed with one
+// IEEE single-precision rounding per operation in a fixed order, no fused
+// multiply-add:
+//     e_c = I_c - C_c;  dc = ((e_0^2 + e_1^2) + e_2^2);  t_d = w_d (x_d - c_d)^2
+//     ds = ((t_0 + t_1) + t_2);  D^2 = dc + ds
+// The map step of the update (Sec. 3.1) is fused: [I(x), x, 1] is summed
+// per label in the same pass, so the image is read once per iteration.
+//
+// Work decomposition.  A CTA (8 warps) owns a tile (32x16x8 voxels for the
+// large 3-D shape, 64x32 pixels for the large 2-D one):
+//  1. stages the tile's channels as bank-padded planes in shared memory;
+//  2. gathers the centres of the bins that can reach the tile (3 bins per
+//     axis around it), keeps those whose window meets the tile, sorts them by
+//     index, and builds per centre the feature pair (C_c, C_c) and per axis
+//     the table t_d(x_d) over the tile's coordinates, +inf outside the window
+//     (the window test is folded into the distance);
+//  3. each warp sweeps boxes of 32 lanes x VL voxels (VL = 2 or 4 consecutive
+//     voxels along x per lane, in packed .f32x2 pairs), visiting only the
+//     centres that reach its box, and leaves the winning slot of every voxel
+//     in shared memory;
+//  4. one sweep over 16-voxel row segments writes the int32 labels with
+//     16-byte stores and sums [I, x, y, z, 1] along runs of equal slots (a
+//     run of four equal slots takes one byte-sum instruction per channel)
+//     into per-tile accumulators;
+//  5. per-tile sums leave through one uint64 atomic per (centre, field).
+// Tiles reached by more than kCap centres are handed to the per-voxel kernel.
+#pragma once
+#include "common.cuh"
+
+namespace sslic {
+
+namespace tile {
+
+constexpr float kInf = __builtin_huge_valf();
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kCap = 48;     // candidate centres per tile (a 32x16x8 tile at S = 16 sees ~23, <= 40)
+constexpr int kStage = 256;  // gathered centres before filtering
+constexpr int kSeg = 16;     // voxels per row segment in the label / sum sweep
+
+// Tile shapes.  A tile must stay within kCap reaching centres: about
+// prod_d (T_d + 2 S_d - 1) / S_d of them, so small grids take small tiles.
+// Lanes: WX along x times WY times WZ, each lane VL consecutive voxels along
+// x (VL / 2 packed pairs); a warp box is VL WX x WY x WZ.  More voxels per
+// lane share each centre's shared-memory reads among more voxels; a larger
+// box is reached by a few more centres.
+template <int NDIM_, int TX_, int TY_, int TZ_, int WX_, int WY_, int WZ_, int VL_>
+struct Shape {
+    static constexpr int NDIM = NDIM_, TX = TX_, TY = TY_, TZ = TZ_, WX = WX_, WY = WY_, WZ = WZ_, VL = VL_;
+};
+using Shape3L = Shape<3, 32, 16, 8, 2, 4, 4, 2>;   // 4096 voxels, grids S >= 12
+using Shape3S = Shape<3, 16, 8, 8, 2, 4, 4, 2>;    // 1024 voxels, smaller grids
+using Shape3L4 = Shape<3, 32, 16, 8, 2, 4, 4, 4>;  // as 3L, 8x4x4 warp boxes
+using Shape3S4 = Shape<3, 16, 8, 8, 2, 4, 4, 4>;   // as 3S, 8x4x4 warp boxes
+using Shape2L = Shape<2, 64, 32, 1, 4, 8, 1, 2>;   // 2048 pixels
+using Shape2S = Shape<2, 32, 16, 1, 4, 8, 1, 2>;   // 512 pixels
+using Shape2L4 = Shape<2, 64, 32, 1, 4, 8, 1, 4>;  // as 2L, 16x8 warp boxes
+
+// Per-candidate record in shared memory, CDS bytes: t_0 by local x (float,
+// 16-byte aligned for the 4-voxel lanes), (t_1, t_1) by local y, (t_2, t_2)
+// by local z, (C_c, C_c) per channel.
+template <int C, typename SH>
+struct CandLayout {
+    static constexpr int kOffT0 = 0;
+    static constexpr int kOffT1 = kOffT0 + 4 * SH::TX;
+    static constexpr int kOffT2 = kOffT1 + 8 * SH::TY;
+    static constexpr int kOffFe = kOffT2 + 8 * SH::TZ;
+    static constexpr int CDS = ((kOffFe + 8 * C) + 15) / 16 * 16;
+    static_assert(SH::TX % 4 == 0, "t_0 alignment");
+};
+
+template <typename T, int C, typename SH>
+struct Smem {
+    using G = SH;
+    static constexpr int TX = G::TX, TY = G::TY, TZ = G::TZ, TV = TX * TY * TZ;
+    // channel planes: row pitch 4 bytes past the row, plane pitch chosen so a
+    // plane advances 4 banks -- the 4x4 (y, z) lanes of a warp box then hit
+    // distinct banks
+    static constexpr int RPB = TX * (int)sizeof(T) + 4;
+    static constexpr int PPB_RAW = TY * RPB;
+    static constexpr int PPB = PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
+    static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;
+    static constexpr int NBOX = (TX / (G::VL * G::WX)) * (TY / G::WY) * (TZ / G::WZ);
+    alignas(16) unsigned char cd[(kCap + 1) * CandLayout<C, SH>::CDS];  // [kCap]: a dummy that reaches nothing
+    uint8_t blist[NBOX][kCap + 2];       // per warp box: reaching slots, ascending, even length
+    uint8_t bcnt[NBOX];
+    alignas(16) unsigned char planes[C * CPB];
+    unsigned acc[kCap][C + 4];   // per-tile sums: features, x, y, z (local), count
+    float cpos[kCap][3];
+    int cand[kCap];
+    int tmp[kCap];
+    int stage[kStage];
+    uint32_t bmask[kCap];
+    alignas(16) uint8_t slot[TV];
+    int nstage, ncand;
+};
+
+template <typename T, int C, typename SH>
+__device__ __forceinline__ unsigned plane_pair(const Smem<T, C, SH>& s, int c, int xl, int yl, int zl)
+{
+    using S = Smem<T, C, SH>;
+    const unsigned char* p = s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * (int)sizeof(T);
+    if constexpr (sizeof(T) == 1) return *reinterpret_cast<const uint16_t*>(p);
+    else return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// typed views of one candidate record
+template <int C, typename SH, typename U>
+__device__ __forceinline__ U* cand_at(unsigned char* cd, int slot, int off)
+{
+    return reinterpret_cast<U*>(cd + slot * CandLayout<C, SH>::CDS + off);
+}
+
+__device__ __forceinline__ void lds128(uint32_t addr, uint64_t& a, uint64_t& b)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(addr));
+}
+
+__device__ __forceinline__ uint64_t lds64(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void split_pair(unsigned v, unsigned& lo, unsigned& hi)
+{
+    if constexpr (sizeof(T) == 1) { lo = v & 0xffu; hi = v >> 8; }
+    else { lo = v & 0xffffu; hi = v >> 16; }
+}
+
+template <int C>
+__device__ __forceinline__ void flush_run(unsigned (*acc)[C + 4], int cur, const unsigned* fs, unsigned xs,
+                                          unsigned cnt, int yl, int zl)
+{
+    if (cur == kNoSlot || cnt == 0) return;
+#pragma unroll
+    for (int c = 0; c < C; ++c) atomicAdd(&acc[cur][c], fs[c]);
+    atomicAdd(&acc[cur][C], xs);
+    atomicAdd(&acc[cur][C + 1], cnt * (unsigned)yl);
+    atomicAdd(&acc[cur][C + 2], cnt * (unsigned)zl);
+    atomicAdd(&acc[cur][C + 3], cnt);
+}
+
+// One tile of one image (request req): everything of steps 1-5 above.  A
+// tile reached by more than kCap centres is appended to the crowded-tile
+// list as (req << 40 | tile) and left to the per-voxel kernel.
+template <typename T, int C, typename SH>
+__device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t req, Smem<T, C, SH>& s,
+                                          int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+{
+    const Geom& g = a.g;
+    const T* __restrict__ img = (const T*)a.img;
+    const float* __restrict__ ctr = a.ctr;
+    const unsigned* __restrict__ bin_start = a.bin_start;
+    const int* __restrict__ bin_items = a.bin_items;
+    int32_t* __restrict__ labels = a.labels;
+    unsigned long long* __restrict__ acc = a.acc;
+    const int ntx = a.ntx, nty = a.nty;
+    constexpr int NDIM = SH::NDIM;
+    using G = SH;
+    using S = Smem<T, C, SH>;
+    using CL = CandLayout<C, SH>;
+    constexpr int TX = G::TX, TY = G::TY, TZ = G::TZ, TV = TX * TY * TZ;
+    constexpr int WX = G::WX, WY = G::WY, WZ = G::WZ, VL = G::VL, NP = VL / 2;
+    constexpr int BX = VL * WX, BY = WY, BZ = WZ;
+    static_assert(VL == 2 || VL == 4, "voxels per lane");
+    constexpr int NBX = TX / BX, NBY = TY / BY, NBZ = TZ / BZ;
+    constexpr int NBOX = NBX * NBY * NBZ;
+    constexpr int PASSES = NBOX / kWarps;
+    constexpr int F = C + 4;
+    constexpr int SPR = TX / kSeg;  // segments per row
+    static_assert(NBOX % kWarps == 0, "boxes per warp");
+    static_assert(NBX + NBY + NBZ <= 32, "box mask bits");
+    static_assert(TX % kSeg == 0, "row segments");
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int X0 = (tile % ntx) * TX;
+    const int Y0 = ((tile / ntx) % nty) * TY;
+    const int Z0 = (tile / (ntx * nty)) * TZ;
+    const int N0 = (int)g.N[0], N1 = (int)g.N[1], N2 = (int)g.N[2];
+    const int ex = min(TX, N0 - X0), ey = min(TY, N1 - Y0), ez = min(TZ, N2 - Z0);
+
+    if (tid == 0) { s.nstage = 0; s.ncand = 0; }
+    for (int i = tid; i < kCap * F; i += kThreads) (&s.acc[0][0])[i] = 0u;
+
+    // ---- 1. stage the tile as channel planes --------------------------------
+    if constexpr (sizeof(T) == 1 && C == 3) {
+        // full rows: 12-byte groups (4 voxels) -> one word per plane
+        const bool fast = (ex == TX) && ((N0 * 3) % 4 == 0) && (((uintptr_t)img & 3) == 0);
+        if (fast) {
+            constexpr int GPR = TX / 4;  // groups per row
+            for (int i = tid; i < TY * TZ * GPR; i += kThreads) {
+                const int r = i / GPR, gi = i % GPR, yl = r % TY, zl = r / TY;
+                uint32_t a = 0, b = 0, cc = 0;
+                if (yl < ey && zl < ez) {
+                    const uint32_t* src = reinterpret_cast<const uint32_t*>(
+                        img + (vidx(g, X0, Y0 + yl, Z0 + zl) + gi * 4) * 3);
+                    a = __ldg(src);
+                    b = __ldg(src + 1);
+                    cc = __ldg(src + 2);
+                }
+                // bytes: a = R0 G0 B0 R1, b = G1 B1 R2 G2, cc = B2 R3 G3 B3
+                const uint32_t R = __byte_perm(__byte_perm(a, b, 0x0630), cc, 0x5210);
+                const uint32_t Gv = __byte_perm(__byte_perm(a, b, 0x0741), cc, 0x6210);
+                const uint32_t B = __byte_perm(__byte_perm(a, b, 0x0052), cc, 0x7410);
+                unsigned char* row = s.planes + zl * S::PPB + yl * S::RPB + gi * 4;
+                *reinterpret_cast<uint32_t*>(row) = R;
+                *reinterpret_cast<uint32_t*>(row + S::CPB) = Gv;
+                *reinterpret_cast<uint32_t*>(row + 2 * S::CPB) = B;
+            }
+        } else {
+            for (int i = tid; i < TV; i += kThreads) {
+                const int xl = i % TX, yl = (i / TX) % TY, zl = i / (TX * TY);
+                uint8_t v[3] = {0, 0, 0};
+                if (xl < ex && yl < ey && zl < ez) {
+                    const int64_t q = vidx(g, X0 + xl, Y0 + yl, Z0 + zl) * 3;
+                    v[0] = img[q]; v[1] = img[q + 1]; v[2] = img[q + 2];
+                }
+                unsigned char* p = s.planes + zl * S::PPB + yl * S::RPB + xl;
+                p[0] = v[0]; p[S::CPB] = v[1]; p[2 * S::CPB] = v[2];
+            }
+        }
+    } else {
+        for (int i = tid; i < TV * C; i += kThreads) {
+            const int e = i / C, c = i % C;
+            const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+            T v = T(0);
+            if (xl < ex && yl < ey && zl < ez) v = img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl) * C + c];
+            *reinterpret_cast<T*>(s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * (int)sizeof(T)) = v;
+        }
+    }
+
+    // ---- 2. gather, filter, sort the centres that reach the tile -----------
+    const int T0[3] = {X0, Y0, Z0};
+    const int E[3] = {ex, ey, ez};
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = max(0, T0[d] / g.S[d] - 1);
+        bhi[d] = min((int)g.nb[d] - 1, (T0[d] + E[d] - 1) / g.S[d] + 1);
+    }
+    const int nbx = bhi[0] - blo[0] + 1, nby = bhi[1] - blo[1] + 1, nbz = bhi[2] - blo[2] + 1;
+    __syncthreads();
+    for (int b = tid; b < nbx * nby * nbz; b += kThreads) {
+        const int bx = blo[0] + b % nbx, by = blo[1] + (b / nbx) % nby, bz = blo[2] + b / (nbx * nby);
+        const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
+        const unsigned st = bin_start[bin], en = bin_start[bin + 1];
+        for (unsigned i = st; i < en; ++i) {
+            const int pos = atomicAdd(&s.nstage, 1);
+            if (pos < kStage) s.stage[pos] = bin_items[i];
+        }
+    }
+    __syncthreads();
+    const int nst = s.nstage;
+    for (int i = tid; i < min(nst, kStage); i += kThreads) {
+        const int k = s.stage[i];
+        const float* p = ctr + (int64_t)k * g.CW + C;
+        bool hit = true;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) {
+            const int lo = (int)ceilf(p[d]) - g.S[d];
+            hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
+        }
+        if (hit) {
+            const int pos = atomicAdd(&s.ncand, 1);
+            if (pos < kCap) s.tmp[pos] = k;
+        }
+    }
+    __syncthreads();
+    const int nc = s.ncand;
+    if (nst > kStage || nc > kCap) {
+        if (tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = (req << 40) | (int64_t)tile;
+        return;  // block-uniform: the per-voxel kernel takes this tile
+    }
+    for (int i = tid; i < nc; i += kThreads) {
+        const int k = s.tmp[i];
+        int r = 0;
+        for (int j = 0; j < nc; ++j) r += (s.tmp[j] < k);
+        s.cand[r] = k;
+        const float* row = ctr + (int64_t)k * g.CW;
+#pragma unroll
+        for (int c = 0; c < C; ++c) cand_at<C, SH, float2>(s.cd, r, CL::kOffFe)[c] = make_float2(row[c], row[c]);
+        s.cpos[r][0] = row[C];
+        s.cpos[r][1] = row[C + 1];
+        s.cpos[r][2] = row[C + 2];
+    }
+    __syncthreads();
+
+    // ---- per-centre tables and warp-box reach masks -------------------------
+    // t_d entry: w_d (x - c)^2 with one rounding per operation, +inf outside
+    auto entry = [&](int d, int j, float c) -> float {
+        const int lo = (int)ceilf(c) - g.S[d];
+        const int x = T0[d] + j;
+        if (x < lo || x > lo + 2 * g.S[d] - 1) return kInf;
+        const float dl = __fsub_rn((float)x, c);
+        return __fmul_rn(g.w[d], __fmul_rn(dl, dl));
+    };
+    for (int i = tid; i < nc * TX; i += kThreads) {
+        const int sl = i / TX, j = i % TX;
+        cand_at<C, SH, float>(s.cd, sl, CL::kOffT0)[j] = entry(0, j, s.cpos[sl][0]);
+    }
+    if constexpr (NDIM >= 2) {
+        for (int i = tid; i < nc * TY; i += kThreads) {
+            const int sl = i / TY, j = i % TY;
+            const float t = entry(1, j, s.cpos[sl][1]);
+            cand_at<C, SH, float2>(s.cd, sl, CL::kOffT1)[j] = make_float2(t, t);
+        }
+    }
+    if constexpr (NDIM >= 3) {
+        for (int i = tid; i < nc * TZ; i += kThreads) {
+            const int sl = i / TZ, j = i % TZ;
+            const float t = entry(2, j, s.cpos[sl][2]);
+            cand_at<C, SH, float2>(s.cd, sl, CL::kOffT2)[j] = make_float2(t, t);
+        }
+    }
+    for (int i = tid; i < nc; i += kThreads) {
+        uint32_t m = 0;
+        const int NB[3] = {NBX, NBY, NBZ}, BB[3] = {BX, BY, BZ}, SHF[3] = {0, NBX, NBX + NBY};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d >= NDIM) { m |= 1u << SHF[d]; continue; }
+            const int lo = (int)ceilf(s.cpos[i][d]) - g.S[d], hi = lo + 2 * g.S[d] - 1;
+            for (int b = 0; b < NB[d]; ++b) {
+                const int a0 = T0[d] + b * BB[d], a1 = a0 + BB[d] - 1;
+                if (lo <= a1 && hi >= a0) m |= 1u << (SHF[d] + b);
+            }
+        }
+        s.bmask[i] = m;
+    }
+    for (int i = tid; i < TX; i += kThreads) cand_at<C, SH, float>(s.cd, kCap, CL::kOffT0)[i] = kInf;
+    for (int i = tid; i < TY; i += kThreads) cand_at<C, SH, float2>(s.cd, kCap, CL::kOffT1)[i] = make_float2(kInf, kInf);
+    for (int i = tid; i < TZ; i += kThreads) cand_at<C, SH, float2>(s.cd, kCap, CL::kOffT2)[i] = make_float2(kInf, kInf);
+    if (tid < C) cand_at<C, SH, float2>(s.cd, kCap, CL::kOffFe)[tid] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    // per warp box: the slots whose window reaches it, ascending, padded to
+    // an even count with the dummy so the sweep takes two centres per step
+    for (int wb = warp; wb < NBOX; wb += kWarps) {
+        const int bxi = wb % NBX, byi = (wb / NBX) % NBY, bzi = wb / (NBX * NBY);
+        const uint32_t want = (1u << bxi) | (1u << (NBX + byi)) | (1u << (NBX + NBY + bzi));
+        const bool h0 = lane < nc && (s.bmask[lane] & want) == want;
+        const bool h1 = lane + 32 < nc && (s.bmask[lane + 32] & want) == want;
+        const uint32_t m0 = __ballot_sync(0xffffffffu, h0);
+        const uint32_t m1 = __ballot_sync(0xffffffffu, h1);
+        const uint32_t lt = (1u << lane) - 1u;
+        const int n0 = __popc(m0), n = n0 + __popc(m1);
+        if (h0) s.blist[wb][__popc(m0 & lt)] = (uint8_t)lane;
+        if (h1) s.blist[wb][n0 + __popc(m1 & lt)] = (uint8_t)(lane + 32);
+        if (lane == 0) {
+            if (n & 1) s.blist[wb][n] = (uint8_t)kCap;
+            s.bcnt[wb] = (uint8_t)((n + 1) & ~1);
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. warp boxes: assignment ------------------------------------------
+    const int lx = lane % WX, ly = (lane / WX) % WY, lz = lane / (WX * WY);
+    const uint32_t cdb = (uint32_t)__cvta_generic_to_shared(&s.cd[0]);
+    constexpr int CDS = CL::CDS;
+#pragma unroll 1
+    for (int pass = 0; pass < PASSES; ++pass) {
+        const int wb = warp + pass * kWarps;
+        const int bxi = wb % NBX, byi = (wb / NBX) % NBY, bzi = wb / (NBX * NBY);
+        const int xl = bxi * BX + lx * VL, yl = byi * BY + ly, zl = bzi * BZ + lz;
+        uint64_t Fp[C][NP];  // the lane's voxels xl .. xl + VL - 1, in pairs
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                unsigned lo, hi;
+                split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), lo, hi);
+                Fp[c][q] = pk2((float)lo, (float)hi);
+            }
+        float bd[VL];
+        int bs[VL];
+#pragma unroll
+        for (int v = 0; v < VL; ++v) { bd[v] = kInf; bs[v] = kNoSlot; }
+        const uint32_t a0 = cdb + CL::kOffT0 + xl * 4;
+        const uint32_t a1 = cdb + CL::kOffT1 + yl * 8;
+        const uint32_t a2 = cdb + CL::kOffT2 + zl * 8;
+        const uint32_t af = cdb + CL::kOffFe;
+        const int nb = s.bcnt[wb];
+        const uint16_t* lst = reinterpret_cast<const uint16_t*>(&s.blist[wb][0]);
+        // D^2 of the lane's voxels against the centre in slot sl
+        auto dist2 = [&](int sl, uint64_t (&D)[NP]) {
+            const uint32_t so = (uint32_t)(sl * CDS);
+            uint64_t t0[NP];
+            if constexpr (NP == 1) t0[0] = lds64(a0 + so);
+            else lds128(a0 + so, t0[0], t0[1]);
+            uint64_t t1 = 0, t2 = 0;
+            if (NDIM >= 2) t1 = lds64(a1 + so);
+            if (NDIM >= 3) t2 = lds64(a2 + so);
+            uint64_t fe[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) fe[c] = lds64(af + so + c * 8);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                uint64_t dc;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint64_t e = sub2(Fp[c][q], fe[c]);
+                    const uint64_t sq = mul2(e, e);
+                    dc = c == 0 ? sq : add2(dc, sq);
+                }
+                uint64_t ds = t0[q];
+                if (NDIM >= 2) ds = add2(ds, t1);
+                if (NDIM >= 3) ds = add2(ds, t2);
+                D[q] = add2(dc, ds);
+            }
+        };
+        auto take = [&](const uint64_t (&D)[NP], int sl) {
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float d0, d1;
+                upk2(D[q], d0, d1);
+                if (d0 < bd[2 * q]) { bd[2 * q] = d0; bs[2 * q] = sl; }
+                if (d1 < bd[2 * q + 1]) { bd[2 * q + 1] = d1; bs[2 * q + 1] = sl; }
+            }
+        };
+#pragma unroll 1
+        for (int i = 0; i < nb; i += 2) {
+            const unsigned two = lst[i >> 1];
+            const int sa = (int)(two & 0xffu), sb = (int)(two >> 8);
+            uint64_t Da[NP], Db[NP];
+            dist2(sa, Da);
+            dist2(sb, Db);
+            take(Da, sa);
+            take(Db, sb);
+        }
+        uint8_t* so = &s.slot[(zl * TY + yl) * TX + xl];
+        if constexpr (VL == 2) *reinterpret_cast<uint16_t*>(so) = (uint16_t)(bs[0] | (bs[1] << 8));
+        else *reinterpret_cast<uint32_t*>(so) = (uint32_t)bs[0] | ((uint32_t)bs[1] << 8) | ((uint32_t)bs[2] << 16) |
+                                                ((uint32_t)bs[3] << 24);
+    }
+    __syncthreads();
+
+    // ---- 4. row segments: labels out, run sums in -------------------------------
+    const bool vec_ok = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
+    for (int sg = tid; sg < TY * TZ * SPR; sg += kThreads) {
+        // lanes of a warp take segments in different z planes (different
+        // labels, fewer same-address flushes); 2-D: consecutive segments
+        int h, yl, zl;
+        if constexpr (TZ > 1) {
+            zl = sg % TZ;
+            h = (sg / TZ) % SPR;
+            yl = sg / (TZ * SPR);
+        } else {
+            h = sg % SPR;
+            yl = sg / SPR;
+            zl = 0;
+        }
+        const int r = zl * TY + yl;
+        if (yl >= ey || zl >= ez) continue;
+        const int xs0 = h * kSeg;
+        const int n = min(kSeg, ex - xs0);
+        if (n <= 0) continue;
+        int32_t* lrow = labels + vidx(g, X0 + xs0, Y0 + yl, Z0 + zl);
+        const unsigned char* prow = s.planes + zl * S::PPB + yl * S::RPB;
+        // the segment's slots, read word by word in a lane-rotated order
+        // (spreads the lanes of a warp over the banks)
+        uint32_t sw[kSeg / 4];
+        const uint32_t* sp = reinterpret_cast<const uint32_t*>(&s.slot[r * TX + xs0]);
+#pragma unroll
+        for (int j = 0; j < kSeg / 4; ++j) {
+            const int jj = (j + (TZ > 1 ? (lane & 7) : (lane >> 3))) & (kSeg / 4 - 1);
+            sw[jj] = sp[jj];
+        }
+        int cur = kNoSlot, curlab = -1;
+        unsigned fs[C], xs = 0, cnt = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) fs[c] = 0;
+        // start a new run at slot sl (flushing the previous one)
+        auto next_run = [&](int sl) {
+            flush_run<C>(s.acc, cur, fs, xs, cnt, yl, zl);
+            cur = sl;
+            curlab = sl == kNoSlot ? -1 : s.cand[sl];
+#pragma unroll
+            for (int c = 0; c < C; ++c) fs[c] = 0;
+            xs = 0;
+            cnt = 0;
+        };
+        if (n == kSeg) {
+#pragma unroll
+            for (int j = 0; j < kSeg / 4; ++j) {
+                const uint32_t w = sw[j];
+                const int xq = xs0 + 4 * j;
+                int lab4[4];
+                if (sizeof(T) == 1 && w == (w & 0xffu) * 0x01010101u) {
+                    // four voxels, one slot: byte sums of the planes' words
+                    const int sl = (int)(w & 0xffu);
+                    if (sl != cur) next_run(sl);
+                    if (sl != kNoSlot) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            fs[c] += __vsadu4(*reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq), 0u);
+                        xs += 4u * (unsigned)xq + 6u;
+                        cnt += 4u;
+                    }
+                    lab4[0] = lab4[1] = lab4[2] = lab4[3] = curlab;
+                } else {
+                    uint32_t pw[C];
+                    if constexpr (sizeof(T) == 1) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            pw[c] = *reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int sl = (int)((w >> (8 * b)) & 0xffu);
+                        if (sl != cur) next_run(sl);
+                        if (sl != kNoSlot) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c) {
+                                if constexpr (sizeof(T) == 1) fs[c] += (pw[c] >> (8 * b)) & 0xffu;
+                                else fs[c] += (unsigned)*reinterpret_cast<const T*>(
+                                    prow + c * S::CPB + (xq + b) * (int)sizeof(T));
+                            }
+                            xs += (unsigned)(xq + b);
+                            cnt += 1u;
+                        }
+                        lab4[b] = curlab;
+                    }
+                }
+                if (vec_ok) {
+                    *reinterpret_cast<int4*>(lrow + 4 * j) = make_int4(lab4[0], lab4[1], lab4[2], lab4[3]);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) lrow[4 * j + b] = lab4[b];
+                }
+            }
+        } else {
+            for (int b = 0; b < n; ++b) {
+                const uint32_t wb = b < 4 ? sw[0] : (b < 8 ? sw[1] : (b < 12 ? sw[2] : sw[3]));
+                const int sl = (int)((wb >> (8 * (b & 3))) & 0xffu);
+                if (sl != cur) next_run(sl);
+                if (sl != kNoSlot) {
+#pragma unroll
+                    for (int c = 0; c < C; ++c)
+                        fs[c] += (unsigned)*reinterpret_cast<const T*>(prow + c * S::CPB + (xs0 + b) * (int)sizeof(T));
+                    xs += (unsigned)(xs0 + b);
+                    cnt += 1u;
+                }
+                lrow[b] = curlab;
+            }
+        }
+        flush_run<C>(s.acc, cur, fs, xs, cnt, yl, zl);
+    }
+    __syncthreads();
+
+    // ---- 5. per-tile sums, shifted to global coordinates ----------------------
+    for (int i = tid; i < nc * F; i += kThreads) {
+        const int sl = i / F, f = i % F;
+        const unsigned long long cnt = s.acc[sl][C + 3];
+        if (!cnt) continue;
+        unsigned long long v = s.acc[sl][f];
+        if (f == C) v += cnt * (unsigned long long)X0;
+        if (f == C + 1) v += cnt * (unsigned long long)Y0;
+        if (f == C + 2) v += cnt * (unsigned long long)Z0;
+        atomicAdd(&acc[(int64_t)s.cand[sl] * F + f], v);
+    }
+}
+
+// one image: one CTA per tile
+template <typename T, int C, typename SH>
+__global__ void __launch_bounds__(kThreads, 4)
+assign_tile_kernel(TileArgs a, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_body<T, C, SH>(a, blockIdx.x, 0, *reinterpret_cast<Smem<T, C, SH>*>(smem_raw), ovf_tiles, ovf_count);
+}
+
+// many images: a persistent grid walks one queue of (request, tile) work
+// items; request r owns global tile numbers [tpre[r], tpre[r + 1])
+template <typename T, int C, typename SH>
+__global__ void __launch_bounds__(kThreads, 4)
+assign_tile_queue_kernel(const TileArgs* __restrict__ reqs, const int64_t* __restrict__ tpre,
+                         const int* __restrict__ nR, int64_t* __restrict__ ovf_tiles,
+                         unsigned* __restrict__ ovf_count)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T, C, SH>& s = *reinterpret_cast<Smem<T, C, SH>*>(smem_raw);
+    const int R = *nR;
+    const int64_t total = tpre[R];
+    for (int64_t i = blockIdx.x; i < total; i += gridDim.x) {
+        int lo = 0, hi = R - 1;  // last r with tpre[r] <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tpre[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        __syncthreads();  // the previous tile's shared state is no longer read
+        tile_body<T, C, SH>(reqs[lo], (int)(i - tpre[lo]), lo, s, ovf_tiles, ovf_count);
+    }
+}
+
+}  // namespace tile
+
+template <typename SH>
+inline void tile_grid(const Geom& g, int& ntx, int& nty, int& ntz)
+{
+    ntx = (int)((g.N[0] + SH::TX - 1) / SH::TX);
+    nty = (int)((g.N[1] + SH::TY - 1) / SH::TY);
+    ntz = (int)((g.N[2] + SH::TZ - 1) / SH::TZ);
+}
+
+// calls f(SH{}) with the shape type of shape index `shape` (see tile_dims)
+template <int NDIM, typename F>
+inline auto with_shape(int shape, F&& f)
+{
+    if constexpr (NDIM == 3) {
+        switch (shape) {
+        case 1: return f(tile::Shape3S{});
+        case 2: return f(tile::Shape3L4{});
+        case 3: return f(tile::Shape3S4{});
+        default: return f(tile::Shape3L{});
+        }
+    } else {
+        switch (shape) {
+        case 1: return f(tile::Shape2S{});
+        case 2: return f(tile::Shape2L4{});
+        default: return f(tile::Shape2L{});
+        }
+    }
+}
+
+template <typename T, int C, typename SH>
+inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    int ntx, nty, ntz;
+    tile_grid<SH>(g, ntx, nty, ntz);
+    const int64_t ntiles = (int64_t)ntx * nty * ntz;
+    const size_t smem = sizeof(tile::Smem<T, C, SH>);
+    int rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_kernel<T, C, SH>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                        "smem attribute");
+    if (rc) return rc;
+    if ((rc = cuda_check(c, cudaMemsetAsync(w.ovf_count, 0, sizeof(unsigned), st), "memset ovf"))) return rc;
+    TileArgs a;
+    a.g = g;
+    a.img = img;
+    a.ctr = w.ctr;
+    a.bin_start = w.bin_start;
+    a.bin_items = w.bin_items;
+    a.labels = labels;
+    a.acc = w.acc;
+    a.facc = w.facc;
+    a.ntx = ntx;
+    a.nty = nty;
+    a.tx = SH::TX;
+    a.ty = SH::TY;
+    a.tz = SH::TZ;
+    const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
+    tile::assign_tile_kernel<T, C, SH><<<(unsigned)ntiles, tile::kThreads, smem, st>>>(a, w.ovf_tiles, w.ovf_count);
+    count_launch(c);
+    prof_end(c, pr, st);
+    if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_kernel"))) return rc;
+    return launch_voxel_tiles(c, img, labels, SH::TX, SH::TY, SH::TZ, ntx, nty, st);
+}
+
+template <typename T, int C, int NDIM>
+int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+{
+    int shape = c->tile_shape;
+    if (shape < 0) shape = tuned_tile_shape(c->g);
+    if (shape < 0) shape = default_tile_shape(c->g);
+    return with_shape<NDIM>(shape, [&](auto sh) { return launch_tile_shape<T, C, decltype(sh)>(c, img, labels, st); });
+}
+
+// batched form: one persistent launch over the (request, tile) queue of all
+// requests of one type and shape (*nR of them, read on the device); returns
+// the CUDA error of the launch.  With reqs == nullptr it only sets the
+// kernel's shared-memory limit (done before a stream capture).
+template <typename T, int C, typename SH>
+inline cudaError_t launch_queue_shape(const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
+                                      unsigned* ovf_count, int grid, cudaStream_t st)
+{
+    const size_t smem = sizeof(tile::Smem<T, C, SH>);
+    if (!reqs)
+        return cudaFuncSetAttribute(tile::assign_tile_queue_kernel<T, C, SH>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tile::assign_tile_queue_kernel<T, C, SH><<<grid, tile::kThreads, smem, st>>>(reqs, tpre, nR, ovf, ovf_count);
+    return cudaGetLastError();
+}
+
+template <typename T, int C, int NDIM>
+cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
+                              unsigned* ovf_count, int grid, cudaStream_t st)
+{
+    return with_shape<NDIM>(shape, [&](auto sh) {
+        return launch_queue_shape<T, C, decltype(sh)>(reqs, tpre, nR, ovf, ovf_count, grid, st);
+    });
+}
+
+}  // namespace sslic
+
+// explicit instantiation of both launchers for one image type
+#define SSLIC_TILE_INSTANTIATE(T, C, NDIM)                                                                  \
+    template int sslic::launch_tile_impl<T, C, NDIM>(sslic_ctx*, const T*, int32_t*, cudaStream_t);         \
+    template cudaError_t sslic::launch_tile_queue<T, C, NDIM>(int, const sslic::TileArgs*, const int64_t*, \
+                                                              const int*, int64_t*, unsigned*, int, cudaStream_t);

@@ -52,8 +52,9 @@ struct Req {
 
 // ---- kernels -----------------------------------------------------------------
 template <typename T>
-__global__ void b_seed(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, int R)
+__global__ void b_seed(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = kpre[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(kpre, R, i);
@@ -63,8 +64,9 @@ __global__ void b_seed(const Req* __restrict__ reqs, const int64_t* __restrict__
 }
 
 // zero bin counts (K + 1 per request) and cursors (K per request)
-__global__ void b_zero_bins(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre1, int R)
+__global__ void b_zero_bins(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre1, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = kpre1[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(kpre1, R, i);
@@ -74,8 +76,9 @@ __global__ void b_zero_bins(const Req* __restrict__ reqs, const int64_t* __restr
     }
 }
 
-__global__ void b_bin_count(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, int R)
+__global__ void b_bin_count(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = kpre[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(kpre, R, i);
@@ -93,8 +96,9 @@ __global__ void b_bin_count(const Req* __restrict__ reqs, const int64_t* __restr
 // segmented exclusive scan of every request's K + 1 bin counts: chunks of
 // 2048 items, then each request's chunk sums, then the chunk offsets
 __global__ void __launch_bounds__(kBScanThreads)
-b_scan_chunks(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, int R)
+b_scan_chunks(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = cpre[R];
     for (int64_t i = blockIdx.x; i < tot; i += gridDim.x) {
         const int r = prefix_find(cpre, R, i);
@@ -107,16 +111,18 @@ b_scan_chunks(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, in
 }
 
 __global__ void __launch_bounds__(kBScanThreads)
-b_scan_sums(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, int R)
+b_scan_sums(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     for (int r = blockIdx.x; r < R; r += gridDim.x) {
         const int nch = (int)(cpre[r + 1] - cpre[r]);  // <= 2048 (K + 1 <= 2^22)
         block_scan_2048(reqs[r].chunk, reqs[r].chunk, nch, nullptr);
     }
 }
 
-__global__ void b_scan_add(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, int R)
+__global__ void b_scan_add(const Req* __restrict__ reqs, const int64_t* __restrict__ cpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = cpre[R];
     for (int64_t i = blockIdx.x; i < tot; i += gridDim.x) {
         const int r = prefix_find(cpre, R, i);
@@ -130,8 +136,9 @@ __global__ void b_scan_add(const Req* __restrict__ reqs, const int64_t* __restri
     }
 }
 
-__global__ void b_bin_scatter(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, int R)
+__global__ void b_bin_scatter(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = kpre[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(kpre, R, i);
@@ -145,8 +152,9 @@ __global__ void b_bin_scatter(const Req* __restrict__ reqs, const int64_t* __res
 
 // per-voxel assignment of every voxel of a group (image types without a tile kernel)
 template <typename T>
-__global__ void b_voxel_all(const TileArgs* __restrict__ reqs, const int64_t* __restrict__ vpre, int R)
+__global__ void b_voxel_all(const TileArgs* __restrict__ reqs, const int64_t* __restrict__ vpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = vpre[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(vpre, R, i);
@@ -180,8 +188,9 @@ __global__ void b_voxel_tiles(const TileArgs* __restrict__ reqs, const int64_t* 
     }
 }
 
-__global__ void b_finalize(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, int R)
+__global__ void b_finalize(const Req* __restrict__ reqs, const int64_t* __restrict__ kpre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = kpre[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(kpre, R, i);
@@ -191,8 +200,9 @@ __global__ void b_finalize(const Req* __restrict__ reqs, const int64_t* __restri
 }
 
 // public centre tables K x (C + n) of the requests that are done
-__global__ void b_export(const Req* __restrict__ reqs, const int64_t* __restrict__ epre, int R)
+__global__ void b_export(const Req* __restrict__ reqs, const int64_t* __restrict__ epre, const int* __restrict__ nR)
 {
+    const int R = *nR;
     const int64_t tot = epre[R];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(epre, R, i);
@@ -301,7 +311,45 @@ static size_t footprint(const Geom& g)
 }
 
 // group key: dtype, channels, dims, tile shape (-1 for the per-voxel kernel)
-static int group_key(const Geom& g, int shape) { return ((g.dtype * 512 + g.C) * 4 + g.n) * 4 + (shape + 1); }
+static int group_key(const Geom& g, int shape) { return ((g.dtype * 512 + g.C) * 8 + g.n) * 8 + (shape + 1); }
+static int key_dtype(int key) { return key / (512 * 64); }
+static int key_channels(int key) { return (key / 64) % 512; }
+static int key_ndim(int key) { return (key / 8) % 8; }
+static int key_shape(int key) { return key % 8 - 1; }
+
+constexpr int kMaxGroups = 16;  // assignment groups (image type + tile shape) per round
+
+// counts of one round, read by the kernels on the device (so a captured
+// round replays for any number of requests)
+struct RoundHdr {
+    int R;                  // requests advanced by the round
+    int Rf;                 // requests finishing with it
+    int nseed[3];           // joining requests per dtype
+    int ngrp[kMaxGroups];   // requests per assignment group
+};
+
+// Fixed layout of one round's tables for at most M requests: every table
+// sits at the same device address in every round of the same parity.
+struct TabLayout {
+    size_t hdr, kpre, kpre1, cpre, req, fpre, fin, seed_req[3], seed_pre[3], grp_ta[kMaxGroups],
+        grp_pre[kMaxGroups], end;
+    void init(int M)
+    {
+        size_t o = 0;
+        auto put = [&](size_t bytes) { o = (o + 15) / 16 * 16; const size_t r = o; o += bytes; return r; };
+        const size_t P = (size_t)(M + 1) * sizeof(int64_t);
+        hdr = put(sizeof(RoundHdr));
+        kpre = put(P);
+        kpre1 = put(P);
+        cpre = put(P);
+        req = put((size_t)M * sizeof(Req));
+        fpre = put(P);
+        fin = put((size_t)M * sizeof(Req));
+        for (int t = 0; t < 3; ++t) { seed_req[t] = put((size_t)M * sizeof(Req)); seed_pre[t] = put(P); }
+        for (int g = 0; g < kMaxGroups; ++g) { grp_ta[g] = put((size_t)M * sizeof(TileArgs)); grp_pre[g] = put(P); }
+        end = (o + 255) / 256 * 256;
+    }
+};
 
 }  // namespace batch
 }  // namespace sslic
@@ -317,13 +365,15 @@ struct sslic_server {
     Arena arena;
     cudaStream_t cs = nullptr, up = nullptr;  // compute, upload
     // device + pinned staging of the round tables, double buffered
-    size_t tab_bytes = 0;
+    TabLayout lay;
     unsigned char* tab_dev[2] = {nullptr, nullptr};
     unsigned char* tab_host[2] = {nullptr, nullptr};
     cudaEvent_t round_ev[2] = {nullptr, nullptr};
     bool round_pending[2] = {false, false};
+    // captured rounds, by (parity, joining dtypes, finishing, groups)
+    std::map<std::vector<int>, cudaGraphExec_t> graphs;
+    int64_t graph_captures = 0, graph_launches = 0;
     // crowded-tile lists, one per group slot in a round
-    static constexpr int kMaxGroups = 16;
     int64_t* ovf[kMaxGroups] = {};
     unsigned* ovf_cnt = nullptr;  // kMaxGroups counters
     int64_t ovf_cap = 0;
@@ -399,38 +449,86 @@ void place(sslic_server* s, Slot* q)
     d.perturb = q->p.perturb;
 }
 
-// launch the assignment of one group
+// the assignment of one group; with ta == nullptr only the kernels' launch
+// attributes are set (before a capture)
 template <typename T>
-cudaError_t launch_group(sslic_server* s, const Geom& g0, int shape, const TileArgs* targs, const int64_t* pre,
-                         int R, int gi)
+cudaError_t launch_group(sslic_server* s, int C, int n, int shape, const TileArgs* ta, const int64_t* tp,
+                         const int* nR, int gi)
 {
     const int grid = s->sms * 4;
     cudaError_t e;
     if (shape < 0) {
-        b_voxel_all<T><<<grid, 256, 0, s->cs>>>(targs, pre, R);
+        if (!ta) return cudaSuccess;
+        b_voxel_all<T><<<grid, 256, 0, s->cs>>>(ta, tp, nR);
         return cudaGetLastError();
     }
-    if ((e = cudaMemsetAsync(s->ovf_cnt + gi, 0, sizeof(unsigned), s->cs)) != cudaSuccess) return e;
+    if (ta && (e = cudaMemsetAsync(s->ovf_cnt + gi, 0, sizeof(unsigned), s->cs)) != cudaSuccess) return e;
     if constexpr (sizeof(T) == 1) {
-        if (g0.C == 3) e = g0.n == 3 ? launch_tile_queue<uint8_t, 3, 3>(shape, targs, pre, R, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
-                                     : launch_tile_queue<uint8_t, 3, 2>(shape, targs, pre, R, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
-        else e = g0.n == 3 ? launch_tile_queue<uint8_t, 1, 3>(shape, targs, pre, R, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
-                           : launch_tile_queue<uint8_t, 1, 2>(shape, targs, pre, R, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
+        if (C == 3) e = n == 3 ? launch_tile_queue<uint8_t, 3, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
+                               : launch_tile_queue<uint8_t, 3, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
+        else e = n == 3 ? launch_tile_queue<uint8_t, 1, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
+                        : launch_tile_queue<uint8_t, 1, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
     } else {
-        e = g0.n == 3 ? launch_tile_queue<uint16_t, 1, 3>(shape, targs, pre, R, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
-                      : launch_tile_queue<uint16_t, 1, 2>(shape, targs, pre, R, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
+        e = n == 3 ? launch_tile_queue<uint16_t, 1, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
+                   : launch_tile_queue<uint16_t, 1, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
     }
-    if (e != cudaSuccess) return e;
-    b_voxel_tiles<T><<<grid, 256, 0, s->cs>>>(targs, s->ovf[gi], s->ovf_cnt + gi);
+    if (e != cudaSuccess || !ta) return e;
+    b_voxel_tiles<T><<<grid, 256, 0, s->cs>>>(ta, s->ovf[gi], s->ovf_cnt + gi);
     return cudaGetLastError();
 }
 
-// table layout helper: bump allocator inside one staging buffer
-struct Lay {
-    size_t off = 0;
-    template <typename P>
-    size_t put(size_t n) { off = (off + 15) / 16 * 16; const size_t r = off; off += n * sizeof(P); return r; }
-};
+cudaError_t group_launch(sslic_server* s, int key, const TileArgs* ta, const int64_t* tp, const int* nR, int gi)
+{
+    const int dt = key_dtype(key), C = key_channels(key), n = key_ndim(key), sh = key_shape(key);
+    if (dt == SSLIC_U8) return launch_group<uint8_t>(s, C, n, sh, ta, tp, nR, gi);
+    if (dt == SSLIC_U16) return launch_group<uint16_t>(s, C, n, sh, ta, tp, nR, gi);
+    return launch_group<float>(s, C, n, sh, ta, tp, nR, gi);
+}
+
+// every kernel of one round, on the compute stream, reading the tables of
+// parity par: seeding of the joining requests (one launch per dtype present),
+// the bin grid, the assignment of each group, the reduction, the export of
+// the finishing requests
+cudaError_t issue_round(sslic_server* s, int par, int seed_mask, bool has_fin, const std::vector<int>& keys)
+{
+    const TabLayout& L = s->lay;
+    unsigned char* D = s->tab_dev[par];
+    const RoundHdr* h = (const RoundHdr*)(D + L.hdr);
+    const int grid = s->sms * 8;
+    const Req* dreq = (const Req*)(D + L.req);
+    const int64_t *dk = (const int64_t*)(D + L.kpre), *dk1 = (const int64_t*)(D + L.kpre1),
+                  *dc = (const int64_t*)(D + L.cpre);
+    for (int t = 0; t < 3; ++t) {
+        if (!(seed_mask >> t & 1)) continue;
+        const Req* r = (const Req*)(D + L.seed_req[t]);
+        const int64_t* pr = (const int64_t*)(D + L.seed_pre[t]);
+        if (t == SSLIC_U8) b_seed<uint8_t><<<grid, 128, 0, s->cs>>>(r, pr, &h->nseed[t]);
+        else if (t == SSLIC_U16) b_seed<uint16_t><<<grid, 128, 0, s->cs>>>(r, pr, &h->nseed[t]);
+        else b_seed<float><<<grid, 128, 0, s->cs>>>(r, pr, &h->nseed[t]);
+    }
+    b_zero_bins<<<grid, 256, 0, s->cs>>>(dreq, dk1, &h->R);
+    b_bin_count<<<grid, 256, 0, s->cs>>>(dreq, dk, &h->R);
+    b_scan_chunks<<<grid, kBScanThreads, 0, s->cs>>>(dreq, dc, &h->R);
+    b_scan_sums<<<std::min(s->max_active, 1024), kBScanThreads, 0, s->cs>>>(dreq, dc, &h->R);
+    b_scan_add<<<grid, 256, 0, s->cs>>>(dreq, dc, &h->R);
+    b_bin_scatter<<<grid, 256, 0, s->cs>>>(dreq, dk, &h->R);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int gi = 0; gi < (int)keys.size(); ++gi) {
+        e = group_launch(s, keys[gi], (const TileArgs*)(D + L.grp_ta[gi]), (const int64_t*)(D + L.grp_pre[gi]),
+                         &h->ngrp[gi], gi);
+        if (e != cudaSuccess) return e;
+    }
+    b_finalize<<<grid, 256, 0, s->cs>>>(dreq, dk, &h->R);
+    if (has_fin) b_export<<<grid, 256, 0, s->cs>>>((const Req*)(D + L.fin), (const int64_t*)(D + L.fpre), &h->Rf);
+    return cudaGetLastError();
+}
+
+void drop_graphs(sslic_server* s)
+{
+    for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+    s->graphs.clear();
+}
 
 // one round: seed the joining requests, one iteration for all, export the finished
 int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act)
@@ -443,30 +541,24 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
     }
     std::vector<Slot*> all(act);
     all.insert(all.end(), join.begin(), join.end());
-    const int R = (int)all.size(), Rn = (int)join.size();
+    const int R = (int)all.size();
     std::vector<Slot*> fin;
     for (Slot* q : all)
         if (q->iter + 1 >= q->p.max_iter) fin.push_back(q);
     const int Rf = (int)fin.size();
-    // groups
     std::map<int, std::vector<Slot*>> groups;
     for (Slot* q : all) groups[q->group].push_back(q);
-    if ((int)groups.size() > sslic_server::kMaxGroups) return server_fail(s, SSLIC_EUNSUPPORTED, "too many image types");
-    // layout
-    Lay L;
-    const size_t o_req = L.put<Req>(R), o_kpre = L.put<int64_t>(R + 1), o_kpre1 = L.put<int64_t>(R + 1),
-                 o_cpre = L.put<int64_t>(R + 1);
-    const size_t o_fin = L.put<Req>(Rf), o_fpre = L.put<int64_t>(Rf + 1);
-    std::vector<size_t> o_ta, o_tp;
-    for (auto& kv : groups) {
-        o_ta.push_back(L.put<TileArgs>(kv.second.size()));
-        o_tp.push_back(L.put<int64_t>(kv.second.size() + 1));
-    }
-    if (L.off > s->tab_bytes) return server_fail(s, SSLIC_ENOMEM, "round tables");
+    if ((int)groups.size() > kMaxGroups) return server_fail(s, SSLIC_EUNSUPPORTED, "too many image types");
+    if (R > s->max_active) return server_fail(s, SSLIC_EINVAL, "round larger than the request cap");
+    // tables
+    const TabLayout& L = s->lay;
     unsigned char* H = s->tab_host[par];
-    unsigned char* D = s->tab_dev[par];
-    Req* hreq = (Req*)(H + o_req);
-    int64_t *kpre = (int64_t*)(H + o_kpre), *kpre1 = (int64_t*)(H + o_kpre1), *cpre = (int64_t*)(H + o_cpre);
+    RoundHdr* hdr = (RoundHdr*)(H + L.hdr);
+    memset(hdr, 0, sizeof(*hdr));
+    hdr->R = R;
+    hdr->Rf = Rf;
+    Req* hreq = (Req*)(H + L.req);
+    int64_t *kpre = (int64_t*)(H + L.kpre), *kpre1 = (int64_t*)(H + L.kpre1), *cpre = (int64_t*)(H + L.cpre);
     kpre[0] = kpre1[0] = cpre[0] = 0;
     for (int i = 0; i < R; ++i) {
         hreq[i] = all[i]->d;
@@ -474,89 +566,80 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
         kpre1[i + 1] = kpre1[i] + all[i]->g.K + 1;
         cpre[i + 1] = cpre[i] + all[i]->nchunks;
     }
-    Req* hfin = (Req*)(H + o_fin);
-    int64_t* fpre = (int64_t*)(H + o_fpre);
+    Req* hfin = (Req*)(H + L.fin);
+    int64_t* fpre = (int64_t*)(H + L.fpre);
     fpre[0] = 0;
     for (int i = 0; i < Rf; ++i) { hfin[i] = fin[i]->d; fpre[i + 1] = fpre[i] + fin[i]->g.K * (fin[i]->g.C + fin[i]->g.n); }
-    int gi = 0;
+    int seed_mask = 0;
+    for (Slot* q : join) {
+        const int t = q->g.dtype;
+        Req* hr = (Req*)(H + L.seed_req[t]);
+        int64_t* hp = (int64_t*)(H + L.seed_pre[t]);
+        const int i = hdr->nseed[t]++;
+        if (i == 0) hp[0] = 0;
+        hr[i] = q->d;
+        hp[i + 1] = hp[i] + q->g.K;
+        seed_mask |= 1 << t;
+    }
+    std::vector<int> keys;
     int64_t ovf_need = 0;
     for (auto& kv : groups) {
-        TileArgs* ta = (TileArgs*)(H + o_ta[gi]);
-        int64_t* tp = (int64_t*)(H + o_tp[gi]);
+        const int gi = (int)keys.size();
+        keys.push_back(kv.first);
+        TileArgs* ta = (TileArgs*)(H + L.grp_ta[gi]);
+        int64_t* tp = (int64_t*)(H + L.grp_pre[gi]);
         tp[0] = 0;
         for (size_t i = 0; i < kv.second.size(); ++i) {
             Slot* q = kv.second[i];
             ta[i] = q->d.a;
             tp[i + 1] = tp[i] + (q->shape < 0 ? q->g.V : q->ntiles);
         }
+        hdr->ngrp[gi] = (int)kv.second.size();
         if (kv.second[0]->shape >= 0) ovf_need = std::max(ovf_need, tp[kv.second.size()]);
-        ++gi;
     }
     if (ovf_need > s->ovf_cap) {
-        for (int i = 0; i < sslic_server::kMaxGroups; ++i) { cudaFree(s->ovf[i]); s->ovf[i] = nullptr; }
+        // the lists move: every captured round that points at them goes
+        if ((e = cudaStreamSynchronize(s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "sync", e);
+        drop_graphs(s);
+        for (int i = 0; i < kMaxGroups; ++i) { cudaFree(s->ovf[i]); s->ovf[i] = nullptr; }
         s->ovf_cap = 0;
-        for (int i = 0; i < sslic_server::kMaxGroups; ++i)
+        for (int i = 0; i < kMaxGroups; ++i)
             if ((e = cudaMalloc(&s->ovf[i], ovf_need * sizeof(int64_t))) != cudaSuccess)
                 return server_fail(s, SSLIC_ENOMEM, "crowded-tile lists", e);
         s->ovf_cap = ovf_need;
     }
-    if ((e = cudaMemcpyAsync(D, H, L.off, cudaMemcpyHostToDevice, s->cs)) != cudaSuccess)
+    const size_t used = keys.empty() ? L.grp_ta[0] : L.grp_pre[keys.size() - 1] + (size_t)(s->max_active + 1) * 8;
+    if ((e = cudaMemcpyAsync(s->tab_dev[par], H, used, cudaMemcpyHostToDevice, s->cs)) != cudaSuccess)
         return server_fail(s, SSLIC_ECUDA, "tables", e);
-    const int grid = s->sms * 8;
-    const Req* dreq = (const Req*)(D + o_req);
-    const int64_t *dk = (const int64_t*)(D + o_kpre), *dk1 = (const int64_t*)(D + o_kpre1), *dc = (const int64_t*)(D + o_cpre);
-    // joining requests: wait for their upload, then seed them (one launch per dtype)
-    if (Rn) {
-        for (Slot* q : join)
-            if ((e = cudaStreamWaitEvent(s->cs, q->ev_up, 0)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "wait", e);
-        std::vector<Slot*> by[3];
-        for (Slot* q : join) by[q->g.dtype].push_back(q);
-        // sub-tables per dtype, placed after the round tables in the same staging
-        size_t extra = L.off;
-        for (int t = 0; t < 3; ++t) {
-            if (by[t].empty()) continue;
-            extra = (extra + 15) / 16 * 16;
-            const size_t o_r = extra;
-            extra += by[t].size() * sizeof(Req);
-            extra = (extra + 15) / 16 * 16;
-            const size_t o_p = extra;
-            extra += (by[t].size() + 1) * sizeof(int64_t);
-            if (extra > s->tab_bytes) return server_fail(s, SSLIC_ENOMEM, "round tables");
-            Req* hr = (Req*)(H + o_r);
-            int64_t* hp = (int64_t*)(H + o_p);
-            hp[0] = 0;
-            for (size_t i = 0; i < by[t].size(); ++i) { hr[i] = by[t][i]->d; hp[i + 1] = hp[i] + by[t][i]->g.K; }
-            if ((e = cudaMemcpyAsync(D + o_r, H + o_r, extra - o_r, cudaMemcpyHostToDevice, s->cs)) != cudaSuccess)
-                return server_fail(s, SSLIC_ECUDA, "tables", e);
-            const int nr = (int)by[t].size();
-            if (t == SSLIC_U8) b_seed<uint8_t><<<grid, 128, 0, s->cs>>>((const Req*)(D + o_r), (const int64_t*)(D + o_p), nr);
-            else if (t == SSLIC_U16) b_seed<uint16_t><<<grid, 128, 0, s->cs>>>((const Req*)(D + o_r), (const int64_t*)(D + o_p), nr);
-            else b_seed<float><<<grid, 128, 0, s->cs>>>((const Req*)(D + o_r), (const int64_t*)(D + o_p), nr);
+    for (Slot* q : join)
+        if ((e = cudaStreamWaitEvent(s->cs, q->ev_up, 0)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "wait", e);
+    // the round's kernels: replayed from a captured graph of the same form
+    std::vector<int> sig{par, seed_mask, Rf > 0 ? 1 : 0};
+    sig.insert(sig.end(), keys.begin(), keys.end());
+    auto it = s->graphs.find(sig);
+    if (it == s->graphs.end()) {
+        for (int gi = 0; gi < (int)keys.size(); ++gi)
+            if ((e = group_launch(s, keys[gi], nullptr, nullptr, nullptr, gi)) != cudaSuccess)
+                return server_fail(s, SSLIC_ECUDA, "kernel attributes", e);
+        if (s->graphs.size() >= 64) drop_graphs(s);
+        cudaGraph_t gr = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        if ((e = cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return server_fail(s, SSLIC_ECUDA, "begin capture", e);
+        const cudaError_t ei = issue_round(s, par, seed_mask, Rf > 0, keys);
+        e = cudaStreamEndCapture(s->cs, &gr);
+        if (ei != cudaSuccess || e != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return server_fail(s, SSLIC_ECUDA, "capture", ei != cudaSuccess ? ei : e);
         }
+        e = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "instantiate", e);
+        it = s->graphs.emplace(sig, ex).first;
+        s->graph_captures += 1;
     }
-    // one iteration: bins, assignment + map update, reduce
-    b_zero_bins<<<grid, 256, 0, s->cs>>>(dreq, dk1, R);
-    b_bin_count<<<grid, 256, 0, s->cs>>>(dreq, dk, R);
-    b_scan_chunks<<<grid, kBScanThreads, 0, s->cs>>>(dreq, dc, R);
-    b_scan_sums<<<std::min(R, 1024), kBScanThreads, 0, s->cs>>>(dreq, dc, R);
-    b_scan_add<<<grid, 256, 0, s->cs>>>(dreq, dc, R);
-    b_bin_scatter<<<grid, 256, 0, s->cs>>>(dreq, dk, R);
-    if ((e = cudaGetLastError()) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "bins", e);
-    gi = 0;
-    for (auto& kv : groups) {
-        const Slot* q0 = kv.second[0];
-        const TileArgs* ta = (const TileArgs*)(D + o_ta[gi]);
-        const int64_t* tp = (const int64_t*)(D + o_tp[gi]);
-        const int n = (int)kv.second.size();
-        if (q0->g.dtype == SSLIC_U8) e = launch_group<uint8_t>(s, q0->g, q0->shape, ta, tp, n, gi);
-        else if (q0->g.dtype == SSLIC_U16) e = launch_group<uint16_t>(s, q0->g, q0->shape, ta, tp, n, gi);
-        else e = launch_group<float>(s, q0->g, q0->shape, ta, tp, n, gi);
-        if (e != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "assign", e);
-        ++gi;
-    }
-    b_finalize<<<grid, 256, 0, s->cs>>>(dreq, dk, R);
-    if (Rf) b_export<<<grid, 256, 0, s->cs>>>((const Req*)(D + o_fin), (const int64_t*)(D + o_fpre), Rf);
-    if ((e = cudaGetLastError()) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "finalize", e);
+    if ((e = cudaGraphLaunch(it->second, s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "round launch", e);
+    s->graph_launches += 1;
     for (Slot* q : fin) {
         const Geom& g = q->g;
         if ((e = cudaMemcpyAsync(q->h_lab, q->d.a.labels, (size_t)g.V * 4, cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
@@ -674,13 +757,13 @@ int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, sslic_serv
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
-    s->tab_bytes = (size_t)(max_active + 8) * (2 * sizeof(Req) + sizeof(TileArgs) + 64) * 2 + (1 << 20);
+    s->lay.init(max_active);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaMalloc(&s->tab_dev[i], s->tab_bytes);
-        if (e == cudaSuccess) e = cudaMallocHost(&s->tab_host[i], s->tab_bytes);
+        e = cudaMalloc(&s->tab_dev[i], s->lay.end);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->tab_host[i], s->lay.end);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->round_ev[i], cudaEventDisableTiming);
     }
-    if (e == cudaSuccess) e = cudaMalloc(&s->ovf_cnt, sslic_server::kMaxGroups * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&s->ovf_cnt, kMaxGroups * sizeof(unsigned));
     if (e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? SSLIC_ENOMEM : SSLIC_ECUDA;
     if (rc == SSLIC_OK) rc = s->arena.init((size_t)hbm_budget_bytes);
     if (rc != SSLIC_OK) {
@@ -706,7 +789,8 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     if (!q) return SSLIC_ENOMEM;
     q->p = *p;
     q->g = g;
-    q->shape = tile_type(g) ? default_tile_shape(g) : -1;
+    q->shape = tile_type(g) ? tuned_tile_shape(g) : -1;
+    if (tile_type(g) && q->shape < 0) q->shape = default_tile_shape(g);
     if (q->shape >= 0) {
         tile_dims(g.n, q->shape, &q->tx, &q->ty, &q->tz);
         q->ntx = (int)((g.N[0] + q->tx - 1) / q->tx);
@@ -787,6 +871,8 @@ int sslic_server_stats_get(sslic_server* s, sslic_server_stats* out)
         for (double x : v) sum += x;
         out->mean_ms = sum / (double)v.size();
     }
+    out->graph_launches = s->graph_launches;
+    out->graph_captures = s->graph_captures;
     out->status = s->error;
     return SSLIC_OK;
 }
@@ -812,7 +898,8 @@ void sslic_server_destroy(sslic_server* s)
         if (s->tab_host[i]) cudaFreeHost(s->tab_host[i]);
         if (s->round_ev[i]) cudaEventDestroy(s->round_ev[i]);
     }
-    for (int i = 0; i < sslic_server::kMaxGroups; ++i)
+    drop_graphs(s);
+    for (int i = 0; i < kMaxGroups; ++i)
         if (s->ovf[i]) cudaFree(s->ovf[i]);
     if (s->ovf_cnt) cudaFree(s->ovf_cnt);
     if (s->cs) cudaStreamDestroy(s->cs);

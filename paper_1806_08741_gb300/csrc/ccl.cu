@@ -13,10 +13,11 @@
 // labels count up from K in raster order of the components' first voxels.
 //
 // Parallel form, equal to that sequential walk:
-//  1. ccl_local: per tile (2048 voxels), union-find in shared memory with
-//     atomicMin linking; local roots are the tile-raster-first voxels and
-//     get dense local ids (uint16 per voxel) and global record ids
-//     (tile base + local id) with label, size and first voxel.
+//  1. ccl_local: per tile (2048 voxels), union-find in shared memory over
+//     the row runs with atomicMin linking; local roots are the
+//     tile-raster-first voxels and get dense local ids (uint16 per voxel)
+//     and global record ids (tile base + local id) with label, size and
+//     first voxel.
 //  2. ccl_faces: union of the records across tile faces (global union-find).
 //  3. flatten + root statistics: component size = sum, first voxel = min.
 //  4. phase 1 (per centre) sets the final flag of its component.
@@ -38,13 +39,12 @@ struct CclCfg;
 template <>
 struct CclCfg<3> { static constexpr int TX = 32, TY = 8, TZ = 8; };
 template <>
-struct CclCfg<2> { static constexpr int TX = 64, TY = 32, TZ = 1; };
+struct CclCfg<2> { static constexpr int TX = 32, TY = 64, TZ = 1; };
 template <>
 struct CclCfg<1> { static constexpr int TX = 2048, TY = 1, TZ = 1; };
 
 constexpr int kCclThreads = 256;
 constexpr int kCclTV = 2048;
-constexpr int kPerThread = kCclTV / kCclThreads;  // 8 consecutive voxels per thread
 
 // ---- union-find with atomicMin linking (parents only ever decrease) --------
 // Parent indices strictly decrease along every chain, so walks end within
@@ -107,6 +107,18 @@ __device__ __forceinline__ int64_t ccl_tile_of(const Geom& g, int64_t x, int64_t
     return x / Cfg::TX + ntx * (y / Cfg::TY + nty * (z / Cfg::TZ));
 }
 
+// Tile-local components.  The tile is handled as 64 rows of 32 voxels (one
+// row = one warp instruction, lane = x; in 1-D a row is a 32-voxel chunk and
+// consecutive chunks touch):
+//  A. runs of equal labels along a row come from one ballot; every voxel's
+//     parent is the first voxel of its run;
+//  B. each run is united with the runs it touches in the previous row along
+//     y and along z -- once per pair of touching runs, at the first voxel of
+//     the overlap;
+//  C. every voxel resolves its root (read-only walks after the unions);
+//  D. roots (the tile-raster-first voxel of each local component) are ranked
+//     by ballots and a scan over the rows;
+//  E. local ids go out per voxel, component sizes are summed per run.
 template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restrict__ lid_img,
@@ -116,125 +128,130 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
+    constexpr int kRows = kCclTV / 32, kWarpsL = kCclThreads / 32, RPW = kRows / kWarpsL;
     static_assert(TX * TY * TZ == kCclTV, "tile size");
+    static_assert(NDIM == 1 || TX == 32, "a row is the tile's extent along x");
     __shared__ int lab[kCclTV];
     __shared__ int par[kCclTV];
     __shared__ uint16_t lidv[kCclTV];
     __shared__ unsigned sz[kCclTV];
-    __shared__ unsigned wsum[kCclThreads / 32];
+    __shared__ unsigned rowoff[kRows];
+    __shared__ unsigned s_total;
     __shared__ int s_base;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t tile = blockIdx.x;
     const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * TZ;
     const int ex = (int)imin64(TX, g.N[0] - X0);
     const int ey = (int)imin64(TY, g.N[1] - Y0);
     const int ez = (int)imin64(TZ, g.N[2] - Z0);
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned* err = &counters[3];
 
-    for (int e = tid; e < kCclTV; e += kCclThreads) {
-        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
-        bool v = xl < ex && yl < ey && zl < ez;
-        lab[e] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
-        sz[e] = 0;
-    }
-    __syncthreads();
-    // runs along x inside the thread's 8 consecutive voxels: plain links
-    const int e0 = tid * kPerThread;
-    for (int i = 0; i < kPerThread; ++i) {
-        const int e = e0 + i;
-        const int L = lab[e];
-        par[e] = L == INT_MIN ? -1 : ((i > 0 && lab[e - 1] == L) ? par[e - 1] : e);
-    }
-    __syncthreads();
-    // unions: across the thread boundary along x, and with the voxel below
-    // along y / z unless the left neighbour already carries the same link
-    for (int i = 0; i < kPerThread; ++i) {
-        const int e = e0 + i;
-        const int L = lab[e];
-        if (L == INT_MIN) continue;
+    // A. labels in, run heads
+    unsigned starts[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
-        if (i == 0 && xl > 0 && lab[e - 1] == L) uf_unite(par, e, e - 1, &counters[3]);
-        const bool left = xl > 0 && lab[e - 1] == L;
-        if (NDIM >= 2 && yl > 0 && lab[e - TX] == L && !(left && lab[e - 1 - TX] == L))
-            uf_unite(par, e, e - TX, &counters[3]);
-        if (NDIM >= 3 && zl > 0 && lab[e - TX * TY] == L && !(left && lab[e - 1 - TX * TY] == L))
-            uf_unite(par, e, e - TX * TY, &counters[3]);
+        const bool v = xl < ex && yl < ey && zl < ez;
+        const int L = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
+        const int Lp = __shfl_up_sync(0xffffffffu, L, 1);
+        const unsigned m = __ballot_sync(0xffffffffu, lane == 0 || L != Lp);
+        starts[i] = m;
+        lab[e] = L;
+        sz[e] = 0u;
+        const int head = 31 - __clz(m & (lt | (1u << lane)));
+        par[e] = L == INT_MIN ? -1 : (e - lane + head);
     }
     __syncthreads();
-    // compress by synchronous pointer jumping: each round halves every chain;
-    // a value read while another thread rewrites it is an ancestor either way
-    for (int round = 0; round < 32; ++round) {
-        int changed = 0;
-        for (int i = 0; i < kPerThread; ++i) {
-            const int e = e0 + i;
-            const int p = par[e];
-            if (p < 0) continue;
-            const int gp = par[p];
-            if (gp != p) { par[e] = gp; changed = 1; }
+    // B. unions with the touching runs of the previous rows
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
+        const int L = lab[e];
+        const int yl = (e / TX) % TY, zl = e / (TX * TY);
+        if constexpr (NDIM == 1) {
+            if (lane == 0 && e > 0 && L != INT_MIN && lab[e - 1] == L) uf_unite(par, e, e - 1, err);
+        } else {
+            // a pair of touching runs is united where its overlap starts: the
+            // voxel matches the one below and either the voxel before it does
+            // not, or it starts a new run
+            const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
+            if ((my & (starts[i] | ~(my << 1))) >> lane & 1u) uf_unite(par, e, e - TX, err);
+            if constexpr (NDIM >= 3) {
+                const unsigned mz = __ballot_sync(0xffffffffu, zl > 0 && L != INT_MIN && lab[e - TX * TY] == L);
+                if ((mz & (starts[i] | ~(mz << 1))) >> lane & 1u) uf_unite(par, e, e - TX * TY, err);
+            }
         }
-        if (!__syncthreads_or(changed)) break;
-        if (round == 31) atomicExch(&counters[3], 1u);
-    }
-    // rank the roots (the tile-raster-first voxel of each local component)
-    unsigned mine = 0;
-    for (int i = 0; i < kPerThread; ++i) {
-        int e = tid * kPerThread + i;
-        mine += (par[e] == e) ? 1u : 0u;
-    }
-    const int lane = tid & 31, warp = tid >> 5;
-    unsigned incl = mine;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    unsigned woff = 0, total = 0;
-    for (int w = 0; w < kCclThreads / 32; ++w) {
-        if (w < warp) woff += wsum[w];
-        total += wsum[w];
-    }
-    if (tid == 0) {
-        unsigned base = atomicAdd(&counters[0], total);
-        if ((int64_t)base + total > m_cap) atomicExch(&counters[1], 1u);
-        s_base = (int)base;
-    }
-    unsigned rank = woff + incl - mine;
-    for (int i = 0; i < kPerThread; ++i) {
-        int e = tid * kPerThread + i;
-        if (par[e] == e) lidv[e] = (uint16_t)(rank++);
     }
     __syncthreads();
+    // C. roots: read-only walks, then one store each
+    int root[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
+        root[i] = par[e] < 0 ? -1 : uf_root(par, par[e], err);
+    }
+    __syncthreads();
+    // D. rank the roots
+    unsigned rmask[RPW];
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
+        par[e] = root[i];
+        rmask[i] = __ballot_sync(0xffffffffu, root[i] == e);
+        if (lane == 0) rowoff[warp * RPW + i] = __popc(rmask[i]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        static_assert(kRows == 64, "two rows per lane");
+        const unsigned a0 = rowoff[2 * lane], a1 = rowoff[2 * lane + 1];
+        unsigned incl = a0 + a1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const unsigned excl = incl - a0 - a1;
+        rowoff[2 * lane] = excl;
+        rowoff[2 * lane + 1] = excl + a0;
+        if (lane == 31) {
+            s_total = incl;
+            const unsigned base = atomicAdd(&counters[0], incl);
+            if ((int64_t)base + incl > m_cap) atomicExch(&counters[1], 1u);
+            s_base = (int)base;
+        }
+    }
+    __syncthreads();
+    const unsigned total = s_total;
     const int base = s_base;
     if ((int64_t)base + total > m_cap) return;  // host grows the records and reruns
-    for (int e = tid; e < kCclTV; e += kCclThreads) {
-        if (par[e] < 0) continue;
-        const uint16_t l = lidv[par[e]];
-        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
-        lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
+        if (root[i] == e) lidv[e] = (uint16_t)(rowoff[warp * RPW + i] + __popc(rmask[i] & lt));
     }
-    // sizes: runs of one component along the thread's 8 consecutive voxels,
-    // one shared atomic per run
-    {
-        int cur = -1;
-        unsigned run = 0;
-        for (int i = 0; i < kPerThread; ++i) {
-            const int e = e0 + i;
-            const int l = par[e] < 0 ? -1 : (int)lidv[par[e]];
-            if (l != cur) {
-                if (cur >= 0) atomicAdd(&sz[cur], run);
-                cur = l;
-                run = 0;
-            }
-            ++run;
+    __syncthreads();
+    // E. local ids out; sizes per run
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
+        if (root[i] < 0) continue;
+        const uint16_t l = lidv[root[i]];
+        const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
+        if (starts[i] >> lane & 1u) {
+            const unsigned later = starts[i] & ~(lt | (1u << lane));
+            const int len = (later ? __ffs(later) - 1 : 32) - lane;
+            atomicAdd(&sz[l], (unsigned)len);
         }
-        if (cur >= 0) atomicAdd(&sz[cur], run);
     }
     __syncthreads();
     for (int e = tid; e < kCclTV; e += kCclThreads) {
         if (par[e] != e) continue;
         const int r = base + lidv[e];
-        int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+        const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         comp_label[r] = lab[e];
         comp_size[r] = sz[lidv[e]];
         comp_first[r] = (unsigned long long)vidx(g, X0 + xl, Y0 + yl, Z0 + zl);

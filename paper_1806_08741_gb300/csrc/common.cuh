@@ -127,6 +127,9 @@ struct Workspace {
     int* bin_of = nullptr;              // K
     unsigned* scan_tmp = nullptr;       // scan block sums (all levels)
     size_t scan_tmp_len = 0;
+    // precision form: error flag of bounded waits, rechecked-voxel count
+    unsigned* hc_err = nullptr;
+    unsigned long long* hc_rechecks = nullptr;
     // assign tile overflow list
     int64_t n_assign_tiles = 0;
     int64_t* ovf_tiles = nullptr;
@@ -174,7 +177,7 @@ struct sslic_ctx {
     int device = 0;
     int sms = 148;
     int busy = 0;
-    int tile_shape = -1;   // assignment tile shape: -1 = chosen from the grid, 0 = large, 1 = small
+    int tile_shape = -1;   // assignment tile shape index, -1 = chosen from the grid (assign_tile.cu)
     char err[512] = {0};
     // tracing
     int prof_on = 0;
@@ -197,10 +200,17 @@ int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t 
 size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
+// high-channel float images (hc.cu)
+bool hc_applies(const Geom& g);
+int64_t hc_num_tiles(const Geom& g);
+int launch_hc(sslic_ctx* c, const float* img, int32_t* labels, cudaStream_t st);
+int launch_hc_probe(sslic_ctx* c, const float* img, int32_t* labels, int64_t tile, float* dots, int* cand,
+                    float* mu, cudaStream_t st);
 int default_tile_shape(const Geom& g);
+int num_tile_shapes(int ndim);
 void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz);
 template <typename T, int C, int NDIM>
-cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, int R, int64_t* ovf,
+cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
                               unsigned* ovf_count, int grid, cudaStream_t st);
 template <typename T, int C, int NDIM>
 int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st);
@@ -214,5 +224,14 @@ int make_geom(const sslic_params* p, Geom* g);
 int prof_begin(sslic_ctx* c, int phase, cudaStream_t st);
 void prof_end(sslic_ctx* c, int rec, cudaStream_t st);
 inline void count_launch(sslic_ctx* c, int n = 1) { c->launches += n; }
+// tile shape measured by sslic_autotune for this image type and grid, or -1
+int tuned_tile_shape(const Geom& g);
+// holds the context for one call; ok = false when another call holds it
+struct Busy {
+    sslic_ctx* c;
+    bool ok;
+    explicit Busy(sslic_ctx* c_) : c(c_) { ok = __sync_bool_compare_and_swap(&c->busy, 0, 1); }
+    ~Busy() { if (ok) __sync_lock_release(&c->busy); }
+};
 int cuda_check(sslic_ctx* c, cudaError_t e, const char* what);
 }  // namespace sslic

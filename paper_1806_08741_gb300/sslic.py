@@ -25,7 +25,10 @@ EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_
            "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
            "sslic_connectivity", "sslic_iterate_static", "sslic_server_create",
            "sslic_server_submit", "sslic_server_wait", "sslic_server_stats_get",
-           "sslic_server_destroy", "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
+           "sslic_server_destroy", "sslic_num_tile_shapes", "sslic_tile_shape_info",
+           "sslic_set_tile_shape", "sslic_get_tile_shape", "sslic_autotune", "sslic_tune_forget",
+           "sslic_tune_record", "sslic_tune_lookup", "sslic_precision_probe",
+           "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
            "sslic_strerror", "sslic_last_error")
 PHASES = ("seed", "bins", "assign", "assign_voxel", "finalize", "connectivity")
 
@@ -57,6 +60,7 @@ class _Profile(ctypes.Structure):
         ("ms", ctypes.c_double * 8),
         ("calls", ctypes.c_int64 * 8),
         ("kernel_launches", ctypes.c_int64),
+        ("rechecks", ctypes.c_int64),
     ]
 
 
@@ -74,6 +78,8 @@ class _ServerStats(ctypes.Structure):
         ("p50_ms", ctypes.c_double),
         ("p99_ms", ctypes.c_double),
         ("mean_ms", ctypes.c_double),
+        ("graph_launches", ctypes.c_int64),
+        ("graph_captures", ctypes.c_int64),
     ]
 
 
@@ -118,6 +124,21 @@ def load(path: str = LIB_PATH):
     L.sslic_server_destroy.argtypes = [S_]
     L.sslic_server_destroy.restype = None
     for f in ("sslic_server_create", "sslic_server_submit", "sslic_server_wait", "sslic_server_stats_get"):
+        getattr(L, f).restype = ctypes.c_int
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.sslic_num_tile_shapes.argtypes = [ctypes.c_int32, i32p]
+    L.sslic_tile_shape_info.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p]
+    L.sslic_set_tile_shape.argtypes = [C, ctypes.c_int32]
+    L.sslic_get_tile_shape.argtypes = [C, i32p]
+    L.sslic_autotune.argtypes = [C, vp, vp, vp, ctypes.c_int32, i32p, ctypes.POINTER(ctypes.c_float)]
+    L.sslic_tune_forget.argtypes = []
+    L.sslic_tune_record.argtypes = [P, ctypes.c_int32]
+    L.sslic_tune_lookup.argtypes = [P, i32p]
+    L.sslic_precision_probe.argtypes = [C, vp, vp, ctypes.c_int64, vp, vp, vp]
+    L.sslic_precision_probe.restype = ctypes.c_int
+    for f in ("sslic_num_tile_shapes", "sslic_tile_shape_info", "sslic_set_tile_shape",
+              "sslic_get_tile_shape", "sslic_autotune", "sslic_tune_forget", "sslic_tune_record",
+              "sslic_tune_lookup"):
         getattr(L, f).restype = ctypes.c_int
     L.sslic_iterate_static.argtypes = [P, vp, vp, vp, vp, vp]
     L.sslic_iterate_static.restype = ctypes.c_int
@@ -334,6 +355,44 @@ class Context:
                     "sslic_connectivity")
         return int(n.value)
 
+    # -- launch configuration --------------------------------------------------------
+    @property
+    def tile_shape(self) -> int:
+        """Tile shape index the next run uses (-1: per-voxel kernel)."""
+        v = ctypes.c_int32(0)
+        self._check(self.lib.sslic_get_tile_shape(self._c, ctypes.byref(v)), "sslic_get_tile_shape")
+        return int(v.value)
+
+    @tile_shape.setter
+    def tile_shape(self, shape: int) -> None:
+        self._check(self.lib.sslic_set_tile_shape(self._c, int(shape)), "sslic_set_tile_shape")
+
+    def autotune(self, image, labels, reps: int = 3, stream=None) -> dict:
+        """Time every tile shape on this image (sslic_autotune); the fastest
+        becomes this context's shape.  Returns {'best': i, 'ms': [...]}."""
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image")
+        self._need(labels, V, "labels")
+        n = num_tile_shapes(self.params.ndim)
+        ms = (ctypes.c_float * max(n, 1))()
+        best = ctypes.c_int32(-1)
+        self._check(self.lib.sslic_autotune(self._c, _ptr(image), _ptr(labels), _stream(stream), int(reps),
+                                            ctypes.byref(best), ms), "sslic_autotune")
+        return {"best": int(best.value), "ms": [float(ms[i]) for i in range(n)]}
+
+    def precision_probe(self, image, centres, tile: int, stream=None) -> dict:
+        """What the tensor-core form's MMA computes on one 128-voxel tile
+        (sslic_precision_probe): {'dots': (128, 32), 'cand': (32,), 'mu': (C,)}."""
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image")
+        self._need(centres, self.K * self.centre_width, "centres")
+        dots = np.zeros((128, 32), np.float32)
+        cand = np.zeros(32, np.int32)
+        mu = np.zeros(self.params.channels, np.float32)
+        self._check(self.lib.sslic_precision_probe(self._c, _ptr(image), _ptr(centres), int(tile),
+                                                   _ptr(dots), _ptr(cand), _ptr(mu)), "sslic_precision_probe")
+        return {"dots": dots, "cand": cand, "mu": mu}
+
     def profile_enable(self, on: bool = True) -> None:
         """Start (or stop) per-phase CUDA-event timing; resets the counters."""
         self._check(self.lib.sslic_profile_enable(self._c, int(bool(on))), "sslic_profile_enable")
@@ -344,6 +403,7 @@ class Context:
         self._check(self.lib.sslic_profile_read(self._c, ctypes.byref(p)), "sslic_profile_read")
         out = {name: (p.ms[i], int(p.calls[i])) for i, name in enumerate(PHASES)}
         out["kernel_launches"] = int(p.kernel_launches)
+        out["rechecks"] = int(p.rechecks)
         return out
 
     def close(self):
@@ -362,6 +422,45 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def num_tile_shapes(ndim: int) -> int:
+    v = ctypes.c_int32(0)
+    rc = load().sslic_num_tile_shapes(int(ndim), ctypes.byref(v))
+    if rc != SSLIC_OK:
+        raise SSLICError(rc, "sslic_num_tile_shapes")
+    return int(v.value)
+
+
+def tile_shape_info(ndim: int, shape: int) -> dict:
+    dims = (ctypes.c_int32 * 3)()
+    vl = ctypes.c_int32(0)
+    rc = load().sslic_tile_shape_info(int(ndim), int(shape), dims, ctypes.byref(vl))
+    if rc != SSLIC_OK:
+        raise SSLICError(rc, "sslic_tile_shape_info")
+    return {"dims": tuple(int(d) for d in dims), "voxels_per_lane": int(vl.value)}
+
+
+def tune_forget() -> None:
+    """Forget every shape measured by autotune in this process."""
+    load().sslic_tune_forget()
+
+
+def tune_record(params: Params, shape: int) -> None:
+    """Record a tile shape for the image type and grid of ``params`` (used
+    by later contexts and servers), e.g. one measured in an earlier run."""
+    rc = load().sslic_tune_record(ctypes.byref(params.to_c()), int(shape))
+    if rc != SSLIC_OK:
+        raise SSLICError(rc, "sslic_tune_record")
+
+
+def tune_lookup(params: Params) -> int:
+    """The recorded tile shape for ``params``' image type and grid, or -1."""
+    v = ctypes.c_int32(-1)
+    rc = load().sslic_tune_lookup(ctypes.byref(params.to_c()), ctypes.byref(v))
+    if rc != SSLIC_OK:
+        raise SSLICError(rc, "sslic_tune_lookup")
+    return int(v.value)
 
 
 def iterate_static(params: Params, image, centres_in, labels, centres_out, stream=None) -> None:

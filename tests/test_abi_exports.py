@@ -75,5 +75,49 @@ def test_create_rejects_bad_sizes(lib):
     for size, grid in [((0, 4), (2, 2)), ((1 << 25, 4), (2, 2)), ((4, 4), (0, 2))]:
         p = S.Params(size=size, grid=grid).to_c()
         assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -1
-    p = S.Params(size=(64, 64), grid=(8, 8), precision=1).to_c()
+    # the tensor-core form: float images with 32..128 channels in 2-D / 3-D
+    p = S.Params(size=(64, 64), grid=(8, 8), precision=1).to_c()           # C = 3 < 32
+    assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -1
+    for kw in (dict(channels=64, dtype=S.U8), dict(channels=200, dtype=S.F32)):
+        p = S.Params(size=(64, 64), grid=(8, 8), precision=1, **kw).to_c()
+        assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -6
+    p = S.Params(size=(640,), grid=(8,), precision=1, channels=64, dtype=S.F32).to_c()
     assert lib.sslic_create(ctypes.byref(p), ctypes.byref(out)) == -6
+
+
+def test_tile_shape_table_host_only(lib):
+    from paper_1806_08741_gb300 import sslic as S
+    assert S.num_tile_shapes(3) == 4 and S.num_tile_shapes(2) == 3 and S.num_tile_shapes(1) == 0
+    seen = set()
+    for nd in (2, 3):
+        for s in range(S.num_tile_shapes(nd)):
+            info = S.tile_shape_info(nd, s)
+            tx, ty, tz = info["dims"]
+            assert info["voxels_per_lane"] in (2, 4)
+            assert tx % 16 == 0 and (tz == 1) == (nd == 2)
+            seen.add((nd, info["dims"], info["voxels_per_lane"]))
+    assert len(seen) == 7  # every index names a different configuration
+    dims = (ctypes.c_int32 * 3)()
+    assert lib.sslic_tile_shape_info(3, 4, dims, None) == -1
+    assert lib.sslic_tile_shape_info(1, 0, dims, None) == -1
+    assert lib.sslic_set_tile_shape(None, 0) == -1
+    assert lib.sslic_autotune(None, None, None, None, 1, None, None) == -1
+
+
+def test_tune_table_host_only(lib):
+    from paper_1806_08741_gb300 import sslic as S
+    S.tune_forget()
+    p = S.Params(size=(300, 200, 100), grid=(16, 16, 16))
+    assert S.tune_lookup(p) == -1
+    S.tune_record(p, 3)
+    assert S.tune_lookup(p) == 3
+    assert S.tune_lookup(S.Params(size=(300, 200, 100), grid=(8, 8, 8))) == -1   # keyed by grid
+    assert S.tune_lookup(S.Params(size=(50, 60, 70), grid=(16, 16, 16))) == 3    # not by size
+    for bad in (-1, 4):
+        with pytest.raises(S.SSLICError):
+            S.tune_record(p, bad)
+    with pytest.raises(S.SSLICError) as e:
+        S.tune_record(S.Params(size=(64, 64), grid=(8, 8), channels=4, dtype=S.F32), 0)
+    assert e.value.code == -6
+    S.tune_forget()
+    assert S.tune_lookup(p) == -1

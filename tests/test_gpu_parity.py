@@ -112,6 +112,8 @@ ITER_CASES = [
     ("1d", lambda: _synth((1000,), 3), (7,), 10.0),
     ("2d_u8_c2_generic", lambda: _rand_img((40, 50, 2), np.uint8, 4), (5, 5), 10.0),
     ("2d_f32_c4", lambda: _rand_img((60, 70, 4), np.float32, 3), (6, 6), 0.5),
+    ("2d_f32_c32_tile", lambda: _rand_img((70, 53, 32), np.float32, 5), (8, 8), 0.5),
+    ("3d_f32_c16_tile", lambda: _rand_img((20, 19, 11, 16), np.float32, 6), (5, 5, 5), 0.5),
 ]
 
 
@@ -130,6 +132,70 @@ def test_iterate_parity(name, mk, grid, m, after):
     else:
         np.testing.assert_array_equal(got_cen, ref_cen)
     assert res == pytest.approx(ref_res, rel=1e-9, abs=1e-12)
+
+
+def _gpu_iterate_shape(img, grid, centres, m, shape):
+    torch, S = _torch(), _S()
+    p = S.params_for(img, grid, m=m, max_iter=1)
+    with S.Context(p) as ctx:
+        ctx.tile_shape = shape
+        assert ctx.tile_shape == shape
+        cin = _dev(centres.astype(np.float32))
+        lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+        cout = torch.empty_like(cin)
+        ctx.iterate(_dev(img), cin, lab, cout)
+        return lab.cpu().numpy(), cout.cpu().numpy().astype(np.float64)
+
+
+SHAPE_CASES = [c for c in ITER_CASES if c[0] in
+               ("2d_256", "2d_ragged", "2d_S8", "3d_S16", "3d_ragged_S8", "3d_small_S_overflow", "3d_aniso",
+                "3d_u16", "2d_gray_u8")]
+
+
+@pytest.mark.parametrize("name,mk,grid,m", SHAPE_CASES, ids=[c[0] for c in SHAPE_CASES])
+def test_every_tile_shape_is_exact(name, mk, grid, m):
+    """Every tile extent and voxels-per-lane choice gives the oracle's labels
+    and centres (the launch configuration never changes a result)."""
+    S = _S()
+    img = mk()
+    p = O.params_for(img, grid, m=m, max_iter=2, perturb=True)
+    cen = O.slic(p, img)["centres"]
+    ref_lab = O.assign(p, img, cen)
+    ref_cen, _, _ = O.update(p, img, ref_lab, cen)
+    for shape in range(S.num_tile_shapes(img.ndim - 1)):
+        lab, got = _gpu_iterate_shape(img, grid, cen, m, shape)
+        np.testing.assert_array_equal(lab, ref_lab, err_msg=f"shape {shape}")
+        np.testing.assert_array_equal(got, ref_cen, err_msg=f"shape {shape}")
+
+
+def test_autotune_picks_a_measured_shape_and_keeps_results():
+    torch, S = _torch(), _S()
+    S.tune_forget()
+    img = _synth((96, 80, 48))
+    p = S.params_for(img, (16, 16, 16), max_iter=4)
+    ref = O.slic(O.params_for(img, (16, 16, 16), max_iter=4), img)
+    with S.Context(p) as ctx:
+        dimg = _dev(img)
+        lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+        t = ctx.autotune(dimg, lab, reps=2)
+        assert 0 <= t["best"] < S.num_tile_shapes(3)
+        assert len(t["ms"]) == 4 and all(v > 0 for v in t["ms"])
+        assert t["ms"][t["best"]] == min(t["ms"])
+        assert ctx.tile_shape == t["best"]
+        cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+        ctx.run(dimg, lab, cen)
+        np.testing.assert_array_equal(lab.cpu().numpy(), ref["labels"])
+        np.testing.assert_array_equal(cen.cpu().numpy().astype(np.float64), ref["centres"])
+    # a new context of the same type and grid starts from the measured shape
+    with S.Context(p) as ctx2:
+        assert ctx2.tile_shape == t["best"]
+    S.tune_forget()
+    # image types without a tile kernel refuse
+    fimg = _rand_img((30, 40, 4), np.float32, 1)
+    with S.Context(S.params_for(fimg, (6, 6))) as ctx3:
+        assert ctx3.tile_shape == -1
+        with pytest.raises(S.SSLICError):
+            ctx3.autotune(_dev(fimg), torch.empty((30, 40), dtype=torch.int32, device="cuda"))
 
 
 def test_iterate_random_centres_ties():
@@ -192,6 +258,66 @@ def test_connectivity_uncovered_and_blocky():
     got, n = _gpu_conn(shape, grid, cen, lab)
     np.testing.assert_array_equal(got, ref)
     assert n == nref
+
+
+def _spiral(h, w):
+    """1 on a one-pixel-wide square spiral (one long winding component that
+    crosses every row and tile boundary many times), 0 elsewhere."""
+    a = np.zeros((h, w), np.int32)
+    y, x, dy, dx = 0, 0, 0, 1
+    a[0, 0] = 1
+    turns = 0
+    while turns < 2:
+        ny, nx = y + dy, x + dx
+        fy, fx = y + 2 * dy, x + 2 * dx   # keep one free pixel to the next arm
+        ok = 0 <= ny < h and 0 <= nx < w and not a[ny, nx] and not (0 <= fy < h and 0 <= fx < w and a[fy, fx])
+        if ok:
+            y, x = ny, nx
+            a[y, x] = 1
+            turns = 0
+        else:
+            dy, dx = dx, -dy
+            turns += 1
+    return a
+
+
+@pytest.mark.parametrize("case", ["checker2d", "checker3d", "spiral2d", "spiral3d", "stripes1d"])
+def test_connectivity_adversarial_patterns(case):
+    """Every voxel its own component (the most local components a tile can
+    hold), and thin winding components that cross tiles and rows many times."""
+    if case == "checker2d":
+        y, x = np.mgrid[0:97, 0:131]
+        lab = ((x + y) % 2).astype(np.int32)
+        grid = (16, 16)
+    elif case == "checker3d":
+        z, y, x = np.mgrid[0:21, 0:19, 0:70]
+        lab = ((x + y + z) % 2).astype(np.int32)
+        grid = (8, 8, 8)
+    elif case == "spiral2d":
+        lab = _spiral(150, 203)
+        grid = (32, 32)
+    elif case == "spiral3d":
+        sp = _spiral(40, 70)
+        lab = np.stack([sp if z % 2 == 0 else 1 - sp for z in range(12)]).astype(np.int32)
+        grid = (16, 16, 4)
+    else:
+        lab = (np.arange(5000) // 3 % 2).astype(np.int32)
+        grid = (50,)
+    shape = lab.shape
+    n = len(shape)
+    size = tuple(reversed(shape))
+    nb = [-(-size[d] // grid[d]) for d in range(n)]
+    K = int(np.prod(nb))
+    cen = np.zeros((K, 3 + n))
+    for k in range(K):
+        j = np.unravel_index(k, tuple(reversed(nb)))[::-1]   # x fastest
+        for d in range(n):
+            cen[k, 3 + d] = min(size[d] - 1, j[d] * grid[d] + grid[d] / 2)
+    p = O.Params(size=tuple(reversed(shape)), grid=grid, channels=3)
+    ref, nref = O.connectivity(p, cen, lab)
+    got, nn = _gpu_conn(shape, grid, cen, lab)
+    assert nn == nref
+    np.testing.assert_array_equal(got, ref)
 
 
 def test_connectivity_many_components_and_capacity_growth():

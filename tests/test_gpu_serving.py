@@ -64,6 +64,8 @@ def test_served_results_equal_alone(budget_mb):
         st = srv.stats()
     assert st["completed"] == len(reqs) and st["status"] == 0
     assert all(x > 0 for x in lat)
+    # every round ran as a replay of a captured graph; forms repeat
+    assert st["graph_launches"] == st["rounds"] and 1 <= st["graph_captures"] <= st["rounds"]
     if budget_mb == 24:
         assert st["max_active"] < len(reqs)   # admission had to wait for memory
     for (img, grid, m), (lab, cen) in zip(reqs, outs):
@@ -98,3 +100,33 @@ def test_server_rejects():
         with pytest.raises(S.SSLICError) as e:
             srv.submit(S.params_for(img, (16, 16), enforce_connectivity=True), img, lab)
         assert e.value.code == -6
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_served_results_equal_alone_for_each_recorded_shape(shape):
+    """The tile shape recorded for an image type (as by autotune) is the one
+    the batched form uses; no shape changes a result."""
+    from paper_1806_08741_gb300 import sslic as S
+    reqs = _mix(11)[:8]
+    iters = 3
+    S.tune_forget()
+    try:
+        for img, grid, m in reqs:
+            p = S.params_for(img, grid, m=m, max_iter=iters)
+            if (p.dtype, p.channels) in ((S.U8, 3), (S.U8, 1), (S.U16, 1)):
+                S.tune_record(p, shape)
+        outs = []
+        with S.Server(1 << 30, max_active=8) as srv:
+            tickets = []
+            for img, grid, m in reqs:
+                p = S.params_for(img, grid, m=m, max_iter=iters)
+                lab = np.empty(img.shape[:-1], np.int32)
+                tickets.append(srv.submit(p, img, lab))
+                outs.append(lab)
+            for t in tickets:
+                srv.wait(t)
+    finally:
+        S.tune_forget()
+    for (img, grid, m), lab in zip(reqs, outs):
+        ref = O.slic(O.params_for(img, grid, m=m, max_iter=iters), img)
+        np.testing.assert_array_equal(lab, ref["labels"])

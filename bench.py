@@ -69,6 +69,23 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (the slowest rank sets the job's time);
+    x itself when running alone."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, voxels, iters, seconds):
+    """Whole-job Gvoxel-iterations/s: every rank segments its own image of
+    `voxels` voxels for `iters` iterations in `seconds` (the max over ranks)."""
+    return world * voxels * iters / seconds / 1e9
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -221,7 +238,12 @@ def run_ours(args, w):
     V = spec.voxels
     # launch configuration: measured tile shape (before any timed work)
     tune = None
-    if not args.no_autotune:
+    if args.tile_shape is not None:
+        ctx.tile_shape = args.tile_shape
+        info_s = S.tile_shape_info(p.ndim, args.tile_shape)
+        tune = {"shape": args.tile_shape, "dims": info_s["dims"], "voxels_per_lane": info_s["voxels_per_lane"],
+                "ms_per_shape": None}
+    elif not args.no_autotune:
         t = ctx.autotune(img, labels, reps=2, stream=stream)
         info_s = S.tile_shape_info(p.ndim, t["best"])
         tune = {"shape": t["best"], "dims": info_s["dims"], "voxels_per_lane": info_s["voxels_per_lane"],
@@ -247,14 +269,11 @@ def run_ours(args, w):
     clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
-    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
         dist.barrier()
     iters = info["iterations"]
-    value = world * V * iters / (ms_step / 1e3) / 1e9
+    value = job_throughput(world, V, iters, ms_step / 1e3)
 
     # roofline of the dominant kernel: the fused assign + update tile kernel
     esz = 1 if spec.dtype == "u8" else 2
@@ -295,17 +314,17 @@ def run_ours(args, w):
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             ctx.run_host(h_img, h_lab, h_cen, stream=stream)
-        dt = (time.perf_counter() - t0) / n_e2e
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, dist, dev)
         same = bool(torch.equal(h_lab, labels.cpu()))
-        e2e = {"value": world * V * iters / dt / 1e9, "unit": UNIT,
+        e2e = {"value": job_throughput(world, V, iters, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(h_img.numel() * h_img.element_size()),
                "d2h_bytes_per_step": int(h_lab.numel() * 4 + h_cen.numel() * 4),
                "ms_per_step": dt * 1e3, "labels_equal_device_run": same}
         del h_img, h_lab, h_cen
+
+    precision = None
+    if rank == 0 and world == 1 and not args.no_precision:
+        precision = precision_bench(steps=max(3, args.steps))
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
@@ -328,6 +347,7 @@ def run_ours(args, w):
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
             "tile_shape": tune, "assign_update_loop": loop,
             "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
+            "precision": precision,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -335,6 +355,64 @@ def run_ours(args, w):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# precision form: the 64-band float workload, exact FP32 vs BF16 tensor core
+# ---------------------------------------------------------------------------
+def precision_bench(steps=3, warmup=2):
+    """hyper64_1024 (1024x1024 x 64 float32, S = 16, m = 0.1, 10 iterations):
+    whole runs of the exact form (precision 0) and of the tensor-core form
+    (precision 1), device time per run, the assignment kernel's achieved HBM
+    bandwidth (C x 4 + 4 bytes per voxel), the share of voxels re-evaluated
+    in exact FP32, and the label agreement of the two forms' final labels."""
+    import numpy as np
+    import torch
+
+    from paper_1806_08741_gb300 import inputs
+    from paper_1806_08741_gb300 import sslic as S
+
+    w = inputs.WORKLOADS["hyper64_1024"]
+    host = inputs.make_hyperspectral(size=w.float_image["size"], bands=w.float_image["bands"])
+    img = torch.from_numpy(host).cuda()
+    V = host.shape[0] * host.shape[1]
+    C = host.shape[2]
+    peak, peak_src = _peaks()
+    out = {"workload": w.name, "size": list(reversed(host.shape[:2])), "channels": C, "grid": list(w.grid),
+           "m": w.m, "iterations": w.max_iter}
+    labs = {}
+    stream = torch.cuda.current_stream()
+    for prec in (0, 1):
+        p = S.params_for(host, w.grid, m=w.m, max_iter=w.max_iter, perturb=w.perturb, precision=prec)
+        with S.Context(p) as ctx:
+            lab = torch.empty(host.shape[:2], dtype=torch.int32, device="cuda")
+            cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+            for _ in range(warmup):
+                ctx.run(img, lab, cen, stream=stream)
+            torch.cuda.synchronize()
+            ctx.profile_enable(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.run(img, lab, cen, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof = ctx.profile_read()
+            ms = e0.elapsed_time(e1) / steps
+            a_ms, a_calls = prof["assign"]
+            bpv = C * 4 + 4
+            achieved = V * bpv / (a_ms / a_calls / 1e3) / 1e9 if a_calls else None
+            labs[prec] = lab.cpu().numpy()
+            out["fp32" if prec == 0 else "bf16_tcgen05"] = {
+                "value": V * w.max_iter / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_run": ms,
+                "assign_ms_per_iter": a_ms / a_calls if a_calls else None,
+                "assign_gbs": achieved, "assign_frac_hbm": achieved / peak if achieved else None,
+                "peak_source": f"of {peak_src}", "bytes_per_voxel": bpv,
+                "rechecked_fraction": prof["rechecks"] / (V * w.max_iter * steps)}
+    out["label_agreement"] = float((labs[0] == labs[1]).mean())
+    del img
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -473,6 +551,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the built-in tile shape")
+    ap.add_argument("--tile-shape", type=int, default=None, help="fix the tile shape (no autotuning)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the 64-band float workload")
+    ap.add_argument("--precision-only", action="store_true", help="only the 64-band float workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
     ap.add_argument("--reference-edge", type=int, default=128,
@@ -482,6 +563,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream benchmark")
     ap.add_argument("--serve-requests", type=int, default=200)
     args = ap.parse_args()
+    if args.precision_only:
+        print(json.dumps({"precision": precision_bench(steps=max(3, args.steps))}), flush=True)
+        return 0
     if args.serve:
         import torch
         torch.cuda.set_device(_env_int("LOCAL_RANK", 0))

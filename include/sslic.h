@@ -206,9 +206,10 @@ SSLIC_API int sslic_autotune(sslic_ctx* c, const void* image_dev, int32_t* label
  * assignment tile of the image (128 voxels: 16x8 in 2-D, 8x4x4 in 3-D, tiles
  * numbered in raster order) with the given centres (device, K x (C+n)) and
  * returns what the tensor core computed, before any decision:
- *   dots_host  (host, 128 x 32 float): dots[v][j] = sum_c bf16(x_v,c - mu_c) *
- *              bf16(C_j,c - mu_c), v = voxel of the tile in raster order
- *              (x fastest), j = candidate slot; slots past the candidates hold 0
+ *   dots_host  (host, 128 x 32 float): dots[v][j] = sum_c (xh xh' + xh xl' + xl xh')
+ *              with xh = bf16(x_v,c - mu_c), xl = bf16(x_v,c - mu_c - xh) and
+ *              xh', xl' the same split of C_j,c - mu_c; v = voxel of the tile in
+ *              raster order (x fastest), j = candidate slot; empty slots hold 0
  *   cand_host  (host, 32 int32): cluster index per slot (ascending), -1 = empty
  *   mu_host    (host, C float): the shift mu (mean of the candidates' features)
  * SSLIC_EINVAL if the context is not of the tensor-core form or the tile is

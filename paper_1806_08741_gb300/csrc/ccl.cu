@@ -19,7 +19,7 @@
 //     and global record ids (tile base + local id) with label, size and
 //     first voxel.
 //  2. ccl_faces: union of the records across tile faces (global union-find).
-//  3. flatten + root statistics: component size = sum, first voxel = min.
+//  3. flatten, with the root statistics: component size = sum, first voxel = min.
 //  4. phase 1 (per centre) sets the final flag of its component.
 //  5. phase 2 (per component): final -> own label; large or at the origin ->
 //     new, ranked by first voxel (sort); otherwise a link to the component
@@ -85,7 +85,7 @@ __device__ __forceinline__ int uf_root(const int* par, int x, unsigned* err)
     return x;
 }
 
-__device__ __forceinline__ void uf_unite(int* par, int a, int b, unsigned* err)
+__device__ __noinline__ void uf_unite(int* par, int a, int b, unsigned* err)
 {
     a = uf_find(par, a, err);
     b = uf_find(par, b, err);
@@ -148,61 +148,111 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     const unsigned lt = (1u << lane) - 1u;
     unsigned* err = &counters[3];
 
-    // A. labels in, run heads
-    unsigned starts[RPW];
+    // A. labels in (all of the warp's rows in flight at once), run heads
+    int Lr[RPW];
 #pragma unroll
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         const bool v = xl < ex && yl < ey && zl < ez;
-        const int L = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
+        Lr[i] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
+    }
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+        const int e = (warp * RPW + i) * 32 + lane;
+        const int L = Lr[i];
         const int Lp = __shfl_up_sync(0xffffffffu, L, 1);
         const unsigned m = __ballot_sync(0xffffffffu, lane == 0 || L != Lp);
-        starts[i] = m;
         lab[e] = L;
         sz[e] = 0u;
         const int head = 31 - __clz(m & (lt | (1u << lane)));
         par[e] = L == INT_MIN ? -1 : (e - lane + head);
     }
+    __syncwarp();
+    // B1. unions with the previous row inside the warp's own rows (a z-plane
+    //     in 3-D, 8 consecutive rows in 2-D), so that B2 may rely on them.  A
+    //     pair of touching runs is united where its overlap starts: the voxel
+    //     matches the one below and either the voxel before it does not, or
+    //     it starts a new run.
+    if constexpr (NDIM == 1) {
+#pragma unroll 1
+        for (int i = 1; i < RPW; ++i) {
+            const int e = (warp * RPW + i) * 32 + lane;
+            if (lane == 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite(par, e, e - 1, err);
+        }
+    } else {
+#pragma unroll 1
+        for (int i = 1; i < RPW; ++i) {
+            const int e = (warp * RPW + i) * 32 + lane;
+            const int L = lab[e];
+            const int yl = (e / TX) % TY;
+            const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
+            const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
+            if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite(par, e, e - TX, err);
+        }
+    }
     __syncthreads();
-    // B. unions with the touching runs of the previous rows
-#pragma unroll
+    // B2. unions across warps (atomic linking): along z in 3-D, along y at
+    //     the first row of each warp in 2-D, along x between the warps' chunks
+    //     in 1-D.  A z-pair is skipped when the row before it has the same two
+    //     labels across the same faces (that path is already united).
+    if (NDIM == 1) {
+        const int e = warp * RPW * 32;
+        if (lane == 0 && e > 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite(par, e, e - 1, err);
+    } else if (NDIM == 2) {
+        const int e = warp * RPW * 32 + lane;
+        const int L = lab[e];
+        const int yl = (e / TX) % TY;
+        const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
+        const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
+        if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite(par, e, e - TX, err);
+    } else {
+        constexpr int P = TX * TY;
+#pragma unroll 1
+        for (int i = 0; i < RPW; ++i) {
+            const int e = (warp * RPW + i) * 32 + lane;
+            const int L = lab[e];
+            const int yl = (e / TX) % TY, zl = e / P;
+            const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
+            const bool zm = zl > 0 && L != INT_MIN && lab[e - P] == L;
+            const bool via_y = zm && yl > 0 && lab[e - TX] == L && lab[e - TX - P] == L;
+            const unsigned mz = __ballot_sync(0xffffffffu, zm);
+            const unsigned want = mz & (starts | ~(mz << 1)) & ~__ballot_sync(0xffffffffu, via_y);
+            if (want >> lane & 1u) uf_unite(par, e, e - P, err);
+        }
+    }
+    __syncthreads();
+    // C. roots: every run head (the first voxel of a run; path halving may
+    //    have moved its parent) finds its root and compresses its path to
+    //    it -- no unions run any more, so every store writes a final root.
+    //    Every parent pointer names a run head, so afterwards any voxel's
+    //    root is par[par[e]].
+#pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
         const int L = lab[e];
-        const int yl = (e / TX) % TY, zl = e / (TX * TY);
-        if constexpr (NDIM == 1) {
-            if (lane == 0 && e > 0 && L != INT_MIN && lab[e - 1] == L) uf_unite(par, e, e - 1, err);
-        } else {
-            // a pair of touching runs is united where its overlap starts: the
-            // voxel matches the one below and either the voxel before it does
-            // not, or it starts a new run
-            const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
-            if ((my & (starts[i] | ~(my << 1))) >> lane & 1u) uf_unite(par, e, e - TX, err);
-            if constexpr (NDIM >= 3) {
-                const unsigned mz = __ballot_sync(0xffffffffu, zl > 0 && L != INT_MIN && lab[e - TX * TY] == L);
-                if ((mz & (starts[i] | ~(mz << 1))) >> lane & 1u) uf_unite(par, e, e - TX * TY, err);
+        if (L != INT_MIN && (lane == 0 || L != lab[e - (lane > 0)])) {
+            const int r = uf_root(par, e, err);
+            for (int x = e, n = 0; x != r && n < kWalkLimit; ++n) {
+                const int nx = par[x];
+                par[x] = r;
+                x = nx;
             }
         }
     }
     __syncthreads();
-    // C. roots: read-only walks, then one store each
-    int root[RPW];
-#pragma unroll
+    unsigned cnt_row = 0;  // lane i < RPW: roots in row warp * RPW + i
+#pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
-        root[i] = par[e] < 0 ? -1 : uf_root(par, par[e], err);
+        const int h = par[e];
+        const int r = h < 0 ? -1 : par[h];
+        if (r >= 0 && par[r] != r) atomicExch(err, 1u);  // broken invariant: reported, never used as an index
+        const unsigned rm = __ballot_sync(0xffffffffu, r == e);
+        if (lane == i) cnt_row = __popc(rm);
     }
-    __syncthreads();
-    // D. rank the roots
-    unsigned rmask[RPW];
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-        const int e = (warp * RPW + i) * 32 + lane;
-        par[e] = root[i];
-        rmask[i] = __ballot_sync(0xffffffffu, root[i] == e);
-        if (lane == 0) rowoff[warp * RPW + i] = __popc(rmask[i]);
-    }
+    // D. rank the roots (raster order = row order, then lane order)
+    if (lane < RPW) rowoff[warp * RPW + lane] = cnt_row;
     __syncthreads();
     if (warp == 0) {
         static_assert(kRows == 64, "two rows per lane");
@@ -227,24 +277,34 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     const unsigned total = s_total;
     const int base = s_base;
     if ((int64_t)base + total > m_cap) return;  // host grows the records and reruns
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
-        if (root[i] == e) lidv[e] = (uint16_t)(rowoff[warp * RPW + i] + __popc(rmask[i] & lt));
+        const int h = par[e];
+        const int r = h < 0 ? -1 : par[h];
+        const unsigned rm = __ballot_sync(0xffffffffu, r == e);
+        if (r == e) lidv[e] = (uint16_t)(rowoff[warp * RPW + i] + __popc(rm & lt));
     }
     __syncthreads();
-    // E. local ids out; sizes per run
-#pragma unroll
+    // E. local ids out; sizes per run; par[] becomes the root of every voxel
+#pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
-        if (root[i] < 0) continue;
-        const uint16_t l = lidv[root[i]];
+        const int h = par[e];
+        int r = h < 0 ? -1 : par[h];
+        if (r >= 0 && par[r] != r) r = -1;  // flagged above
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
-        lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
-        if (starts[i] >> lane & 1u) {
-            const unsigned later = starts[i] & ~(lt | (1u << lane));
-            const int len = (later ? __ffs(later) - 1 : 32) - lane;
-            atomicAdd(&sz[l], (unsigned)len);
+        const int L = lab[e];
+        const bool head = lane == 0 || L != lab[e - (lane > 0)];  // first voxel of a run (of any label)
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        if (r >= 0) {
+            const uint16_t l = lidv[r];
+            lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
+            if (head) {
+                const unsigned later = hm & ~(lt | (1u << lane));
+                const int len = (later ? __ffs(later) - 1 : 32) - lane;
+                atomicAdd(&sz[l], (unsigned)len);
+            }
         }
     }
     __syncthreads();
@@ -270,7 +330,14 @@ __device__ __forceinline__ int gid_of(const Geom& g, const uint16_t* lid_img, co
     return tile_base[ccl_tile_of<NDIM>(g, x, y, z, ntx, nty)] + (int)lid_img[vidx(g, x, y, z)];
 }
 
-// union across the low faces of every tile
+// Union across the low faces of every tile.  Each face pixel whose label
+// equals that of its neighbour across the face names a pair of component
+// records; a pixel whose predecessor along the face's longer axis has the
+// same two labels names the same pair and is skipped, and the remaining
+// pairs are deduplicated in a shared hash set, so each distinct pair of
+// records is united once per tile.
+constexpr int kFaceHash = 2048;  // > 3 faces x 576 pixels / 2: load factor < 1
+
 template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __restrict__ lid_img,
@@ -279,51 +346,61 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
+    __shared__ unsigned hset[kFaceHash];
     const int64_t tile = blockIdx.x;
-    const int64_t T0[3] = {(tile % ntx) * TX, ((tile / ntx) % nty) * TY, (tile / (ntx * nty)) * TZ};
-    const int TT[3] = {TX, TY, TZ};
-    int E[3];
-    for (int d = 0; d < 3; ++d) E[d] = (int)imin64(TT[d], g.N[d] - T0[d]);
-    for (int d = 0; d < NDIM; ++d) {
-        if (T0[d] == 0) continue;
-        const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 3 - d - a1;  // a1: the longer in-plane axis
-        const int n = E[a1] * E[a2];
-        for (int i = threadIdx.x; i < n; i += kCclThreads) {
-            int64_t p[3];
-            p[d] = T0[d];
-            p[a1] = T0[a1] + i % E[a1];
-            p[a2] = T0[a2] + i / E[a1];
-            int64_t q[3] = {p[0], p[1], p[2]};
-            q[d] -= 1;
-            const int64_t ia = vidx(g, p[0], p[1], p[2]), ib = vidx(g, q[0], q[1], q[2]);
-            const int L = labels[ia];
-            if (L != labels[ib]) continue;
-            if (p[a1] > T0[a1]) {  // the previous pair along a1 already links these two sets
-                const int64_t st = a1 == 0 ? 1 : (a1 == 1 ? g.N[0] : g.N[0] * g.N[1]);
-                if (labels[ia - st] == L && labels[ib - st] == L) continue;
-            }
-            uf_unite(gparent, gid_of<NDIM>(g, lid_img, tile_base, p[0], p[1], p[2], ntx, nty),
-                     gid_of<NDIM>(g, lid_img, tile_base, q[0], q[1], q[2], ntx, nty), &counters[3]);
+    const int64_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+    const int64_t X0 = tx * TX, Y0 = ty * TY, Z0 = tz * TZ;
+    const int EX = (int)imin64(TX, g.N[0] - X0), EY = (int)imin64(TY, g.N[1] - Y0), EZ = (int)imin64(TZ, g.N[2] - Z0);
+    for (int i = threadIdx.x; i < kFaceHash; i += kCclThreads) hset[i] = 0u;
+    __syncthreads();
+    const int base_here = tile_base[tile];
+    const int64_t sy = g.N[0], sz = g.N[0] * g.N[1];
+    // the faces that exist (the tile is not on the image's low border there)
+    const bool has[3] = {X0 > 0, NDIM >= 2 && Y0 > 0, NDIM >= 3 && Z0 > 0};
+    const int nf[3] = {has[0] ? EY * EZ : 0, has[1] ? EX * EZ : 0, has[2] ? EX * EY : 0};
+    const int n_all = nf[0] + nf[1] + nf[2];
+    const int64_t p0 = vidx(g, X0, Y0, Z0);
+    // one pixel of one face per thread and step; its loads are issued together
+    for (int idx = threadIdx.x; idx < n_all; idx += kCclThreads) {
+        const int d = idx < nf[0] ? 0 : (idx < nf[0] + nf[1] ? 1 : 2);
+        const int i = idx - (d == 0 ? 0 : (d == 1 ? nf[0] : nf[0] + nf[1]));
+        // in-face axes: u (the longer one) and w
+        const int nu = d == 0 ? EY : EX;
+        const int64_t su = d == 0 ? sy : 1, sw = d == 2 ? sy : sz;
+        const int64_t st = d == 0 ? 1 : (d == 1 ? sy : sz);
+        const int iu = i % nu, iw = i / nu;
+        const int64_t ia = p0 + iu * su + iw * sw, ib = ia - st;
+        const int64_t ja = iu > 0 ? ia - su : ia, jb = iu > 0 ? ib - su : ib;
+        const int L = labels[ia], Lb = labels[ib], La1 = labels[ja], Lb1 = labels[jb];
+        const unsigned la = lid_img[ia], lb = lid_img[ib];
+        if (L != Lb) continue;
+        if (iu > 0 && La1 == L && Lb1 == L) continue;  // same pair as the predecessor along u
+        const int64_t nb = d == 0 ? tile - 1 : (d == 1 ? tile - ntx : tile - ntx * nty);
+        const unsigned key = 1u + ((unsigned)d << 22 | la << 11 | lb);
+        unsigned h = (key * 2654435761u) >> 21;  // 11 bits
+        bool fresh = false;
+        for (int probe = 0; probe < kFaceHash; ++probe) {
+            const unsigned old = atomicCAS(&hset[h], 0u, key);
+            if (old == 0u) { fresh = true; break; }
+            if (old == key) break;
+            h = (h + 1) & (kFaceHash - 1);
         }
+        if (fresh) uf_unite(gparent, base_here + (int)la, tile_base[nb] + (int)lb, &counters[3]);
     }
 }
 
-__global__ void ccl_flatten_kernel(int* gparent, unsigned* counters)
-{
-    const int64_t M = counters[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
-        gparent[i] = uf_root(gparent, (int)i, &counters[3]);
-}
-
-__global__ void ccl_rootstats_kernel(const int* __restrict__ gparent, const unsigned* __restrict__ comp_size,
-                                     const unsigned long long* __restrict__ comp_first,
-                                     unsigned long long* __restrict__ root_size,
-                                     unsigned long long* __restrict__ root_first,
-                                     const unsigned* __restrict__ counters)
+// every record's parent becomes its root (read-only walks: a concurrent
+// store only ever replaces a parent by the root), and the root collects the
+// component's size and first voxel
+__global__ void ccl_flatten_kernel(int* gparent, const unsigned* __restrict__ comp_size,
+                                   const unsigned long long* __restrict__ comp_first,
+                                   unsigned long long* __restrict__ root_size,
+                                   unsigned long long* __restrict__ root_first, unsigned* counters)
 {
     const int64_t M = counters[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = gparent[i];
+        const int r = uf_root(gparent, (int)i, &counters[3]);
+        gparent[i] = r;
         atomicAdd(&root_size[r], (unsigned long long)comp_size[i]);
         atomicMin(&root_first[r], comp_first[i]);
     }
@@ -464,8 +541,9 @@ __global__ void conn_resolve_kernel(const int* __restrict__ gparent, const int* 
                                     volatile int* out_label, unsigned* counters)
 {
     const int64_t M = counters[0];
+    const int* ol = const_cast<const int*>(out_label);  // plain loads for the filter
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        if (gparent[i] != (int)i || out_label[i] != kPendingMerge) continue;
+        if (gparent[i] != (int)i || ol[i] != kPendingMerge) continue;
         int j = link[i];
         int o = out_label[j];
         // pending merge: follow its link (first voxels strictly decrease, so
@@ -494,14 +572,17 @@ conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __r
     const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * Cfg::TZ;
     const int base = tile_base[tile];
     const int nloc = tile_cnt[tile];
+    int any = 0;
     for (int l = threadIdx.x; l < nloc; l += kCclThreads) {
         const int r = base + l;
         const int G = gparent[r];
         const int o = out_label[G];
         tab[l] = o;
         chg[l] = (o != comp_label[r]) ? 1 : 0;
+        any |= chg[l];
     }
-    __syncthreads();
+    // in place, a tile none of whose components changes label is left alone
+    if (!__syncthreads_or(any) && inplace) return;
     for (int e = threadIdx.x; e < kCclTV; e += kCclThreads) {
         int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
         if (x >= g.N[0] || y >= g.N[1] || z >= g.N[2]) continue;
@@ -552,13 +633,10 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     const int gb = c->sms * 8;
-    ccl_flatten_kernel<<<gb, 256, 0, st>>>(w.gparent, w.counters);
+    ccl_flatten_kernel<<<gb, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
+                                           w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
-    ccl_rootstats_kernel<<<gb, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
-                                             w.counters);
-    count_launch(c);
-    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_rootstats_kernel"))) return rc;
     conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,
                                                                  w.gparent, w.root_size, w.fin, ntx, nty);
     count_launch(c);
@@ -621,7 +699,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
         return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
     prof_end(c, pr, st);
-    if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a union-find walk exceeded its bound");
+    if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a bounded walk ran out or an internal check failed");
     if (num_labels) *num_labels = g.K + Mn;
     return SSLIC_OK;
 }

@@ -34,6 +34,15 @@ def _bf16(a):
     return r.astype(np.uint32).view(np.float32)
 
 
+def _split(a):
+    """Two-part BF16 split of float32 values: hi = bf16(a), lo = bf16(a - hi)
+    (a - hi is exact in float32), both returned as float64."""
+    a = np.ascontiguousarray(a, np.float32)
+    hi = _bf16(a)
+    lo = _bf16(a - hi)
+    return hi.astype(np.float64), lo.astype(np.float64)
+
+
 def test_bf16_rounding_helper():
     # bfloat16 keeps 8 significant bits: the spacing above 1.0 is 2^-7
     x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, 1.0 + 2 ** -8 + 2 ** -20, -2.5],
@@ -68,7 +77,8 @@ def _reaching(cen, C, grid, T0, E, n):
                                              ((20, 18, 10), 32, (8, 8, 8))])
 def test_probe_dots_are_bf16_products(size, bands, grid):
     """The tensor core's x~.c~ for every voxel and candidate slot of a tile
-    equals the sum of the BF16-rounded products (within FP32 accumulation),
+    equals hi.hi + hi.lo + lo.hi of the two-part BF16 splits (within FP32
+    accumulation),
     the slots hold the reaching centres in ascending order, and mu is their
     mean feature."""
     torch, S = _torch(), _S()
@@ -94,8 +104,8 @@ def test_probe_dots_are_bf16_products(size, bands, grid):
             mu_ref = cen[ks, :C].astype(np.float64).mean(axis=0)
             np.testing.assert_allclose(r["mu"], mu_ref, rtol=1e-5, atol=1e-6)
             mu = r["mu"].astype(np.float32)
-            cb = np.zeros((32, C), np.float32)
-            cb[:len(ks)] = _bf16(cen[ks, :C] - mu)
+            ch, cl = np.zeros((32, C), np.float64), np.zeros((32, C), np.float64)
+            ch[:len(ks)], cl[:len(ks)] = _split(cen[ks, :C] - mu)
             for v in range(128):
                 xl, yl, zl = v % TX, (v // TX) % TY, v // (TX * TY)
                 X = (T0[0] + xl, T0[1] + yl, T0[2] + zl)
@@ -104,10 +114,11 @@ def test_probe_dots_are_bf16_products(size, bands, grid):
                     x = img[X[1], X[0]] if inside else np.zeros(C, np.float32)
                 else:
                     x = img[X[2], X[1], X[0]] if inside else np.zeros(C, np.float32)
-                xb = _bf16(x - mu).astype(np.float64)
-                prod = xb[None, :] * cb.astype(np.float64)
-                want = prod.sum(axis=1)
-                tol = (C + 2) * 2.0 ** -22 * np.abs(prod).sum(axis=1) + 1e-30
+                xh, xl_ = _split(x - mu)
+                terms = xh[None, :] * ch + xh[None, :] * cl + xl_[None, :] * ch
+                want = terms.sum(axis=1)
+                tol = (3 * C + 2) * 2.0 ** -22 * (np.abs(xh[None, :] * ch) + np.abs(xh[None, :] * cl) +
+                                                  np.abs(xl_[None, :] * ch)).sum(axis=1) + 1e-30
                 got = r["dots"][v].astype(np.float64)
                 assert (np.abs(got - want) <= tol).all(), (tile, v, np.abs(got - want).max())
 

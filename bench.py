@@ -242,12 +242,12 @@ def run_ours(args, w):
         ctx.tile_shape = args.tile_shape
         info_s = S.tile_shape_info(p.ndim, args.tile_shape)
         tune = {"shape": args.tile_shape, "dims": info_s["dims"], "voxels_per_lane": info_s["voxels_per_lane"],
-                "ms_per_shape": None}
+                "tma_staged": info_s["tma_staged"], "ms_per_shape": None}
     elif not args.no_autotune:
         t = ctx.autotune(img, labels, reps=2, stream=stream)
         info_s = S.tile_shape_info(p.ndim, t["best"])
         tune = {"shape": t["best"], "dims": info_s["dims"], "voxels_per_lane": info_s["voxels_per_lane"],
-                "ms_per_shape": t["ms"]}
+                "tma_staged": info_s["tma_staged"], "ms_per_shape": t["ms"]}
 
     for _ in range(args.warmup):
         info = ctx.run(img, labels, centres, stream=stream)

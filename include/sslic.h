@@ -167,9 +167,11 @@ SSLIC_API int sslic_iterate_static(const sslic_params* p, const void* image_dev,
 /* Launch configuration of the assignment kernel.  The paper has no
  * counterpart: its multi-threaded filter splits the image into regions per
  * thread (Sec. 3.1), while here a tile shape fixes how voxels map to CUDA
- * blocks and lanes.  A shape is a tile extent plus the voxels each lane
- * handles (2 or 4 consecutive voxels along x); it changes speed only, never
- * a label or a centre.  Shapes exist for 2-D and 3-D images of uint8 with 1
+ * blocks and lanes.  A shape is a tile extent, the voxels each lane handles
+ * (2 or 4 consecutive voxels along x) and how a tile reaches shared memory
+ * (plain loads, or a TMA copy of the next tile issued while the current one
+ * is computed -- where image rows are 16-byte multiples, otherwise plain);
+ * it changes speed only, never a label or a centre.  Shapes exist for 2-D and 3-D images of uint8 with 1
  * or 3 channels and uint16 with 1 channel; other images use the per-voxel
  * kernel and report shape -1.  Shape indices run over
  * [0, sslic_num_tile_shapes(ndim)); -1 selects the measured shape from
@@ -177,9 +179,11 @@ SSLIC_API int sslic_iterate_static(const sslic_params* p, const void* image_dev,
  * else the built-in rule (the large tile unless too many centres reach it). */
 SSLIC_API int sslic_num_tile_shapes(int32_t ndim, int32_t* count);
 
-/* dims (host, 3 int32): tile extent along x, y, z; voxels_per_lane may be
- * NULL.  SSLIC_EINVAL for an unknown shape. */
-SSLIC_API int sslic_tile_shape_info(int32_t ndim, int32_t shape, int32_t* dims, int32_t* voxels_per_lane);
+/* dims (host, 3 int32): tile extent along x, y, z; voxels_per_lane and
+ * tma_staged (1 = TMA-staged tiles) may be NULL.  SSLIC_EINVAL for an
+ * unknown shape. */
+SSLIC_API int sslic_tile_shape_info(int32_t ndim, int32_t shape, int32_t* dims, int32_t* voxels_per_lane,
+                                    int32_t* tma_staged);
 
 /* Fix the context's shape (-1: back to automatic).  SSLIC_EUNSUPPORTED if
  * the image type has no tile kernel. */

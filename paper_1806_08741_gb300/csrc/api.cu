@@ -215,11 +215,12 @@ static int alloc_core(sslic_ctx* c)
     return SSLIC_OK;
 }
 
-// the tensor-core form's bounded waits: a wait that ran out is reported
-// (and its flag cleared) after the stream has drained
+// bounded device waits (tensor-core MMA completion, TMA copies): a wait
+// that ran out is reported (and its flag cleared) after the stream drains
 static int check_precision_status(sslic_ctx* c, cudaStream_t st)
 {
-    if (c->p.precision != 1) return SSLIC_OK;
+    if (c->p.precision != 1 && !c->status_pending) return SSLIC_OK;
+    c->status_pending = 0;
     unsigned h = 0;
     int rc = cuda_check(c, cudaMemcpyAsync(&h, c->ws.hc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
                         "read status");
@@ -227,7 +228,7 @@ static int check_precision_status(sslic_ctx* c, cudaStream_t st)
     if (rc) return rc;
     if (h) {
         cudaMemsetAsync(c->ws.hc_err, 0, sizeof(unsigned), st);
-        return set_error(c, SSLIC_ETIMEOUT, "tensor-core assignment: a bounded wait ran out");
+        return set_error(c, SSLIC_ETIMEOUT, "assignment: a bounded device wait ran out");
     }
     return SSLIC_OK;
 }

@@ -2,13 +2,18 @@
 //
 // Shape indices: 3-D 0 = 32x16x8 / 2 voxels per lane, 1 = 16x8x8 / 2,
 // 2 = 32x16x8 / 4, 3 = 16x8x8 / 4; 2-D 0 = 64x32 / 2, 1 = 32x16 / 2,
-// 2 = 64x32 / 4.  The default follows the expected number of centres that
-// reach a tile; sslic_autotune measures the shapes instead.
+// 2 = 64x32 / 4.  Each base shape comes twice: index b stages the tile with
+// plain loads, index b + (number of base shapes) with a TMA copy of the next
+// tile in flight while the current one is computed (used where the image
+// rows are 16-byte multiples; otherwise it is the plain form).  The default
+// follows the expected number of centres that reach a tile; sslic_autotune
+// measures the shapes instead.
 #include "assign_tile.cuh"
 
 namespace sslic {
 
-int num_tile_shapes(int ndim) { return ndim == 3 ? 4 : (ndim == 2 ? 3 : 0); }
+int num_base_shapes(int ndim) { return ndim == 3 ? 4 : (ndim == 2 ? 3 : 0); }
+int num_tile_shapes(int ndim) { return 2 * num_base_shapes(ndim); }
 
 void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz)
 {
@@ -19,8 +24,9 @@ void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz)
         *tz = SH::TZ;
         return 0;
     };
-    if (ndim == 3) with_shape<3>(shape, f);
-    else with_shape<2>(shape, f);
+    const int b = num_base_shapes(ndim);
+    if (ndim == 3) with_shape<3>(shape % b, f);
+    else with_shape<2>(shape % b, f);
 }
 
 // expected number of centres reaching a tile of shape (tx, ty, tz)
@@ -44,7 +50,7 @@ int default_tile_shape(const Geom& g)
 int64_t assign_num_tiles(const Geom& g)
 {
     int64_t best = 0;
-    for (int s = 0; s < num_tile_shapes(g.n == 3 ? 3 : 2); ++s) {
+    for (int s = 0; s < num_base_shapes(g.n == 3 ? 3 : 2); ++s) {
         int tx, ty, tz;
         tile_dims(g.n == 3 ? 3 : 2, s, &tx, &ty, &tz);
         const int64_t n = ((g.N[0] + tx - 1) / tx) * ((g.N[1] + ty - 1) / ty) * ((g.N[2] + tz - 1) / tz);

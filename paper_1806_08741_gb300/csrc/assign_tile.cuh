@@ -35,7 +35,10 @@
 //  5. per-tile sums leave through one uint64 atomic per (centre, field).
 // Tiles reached by more than kCap centres are handed to the per-voxel kernel.
 #pragma once
+#include <cuda.h>
+
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace sslic {
 
@@ -95,7 +98,7 @@ struct Smem {
     uint8_t blist[NBOX][kCap + 2];       // per warp box: reaching slots, ascending, even length
     uint8_t bcnt[NBOX];
     alignas(16) unsigned char planes[C * CPB];
-    unsigned acc[kCap][C + 4];   // per-tile sums: features, x, y, z (local), count
+    unsigned pk[kCap][C + 2];        // per-tile sums: features, then two packed words (see PackedSums)
     float cpos[kCap][3];
     int cand[kCap];
     int tmp[kCap];
@@ -140,23 +143,30 @@ __device__ __forceinline__ void split_pair(unsigned v, unsigned& lo, unsigned& h
     else { lo = v & 0xffffu; hi = v >> 16; }
 }
 
-template <int C>
-__device__ __forceinline__ void flush_run(unsigned (*acc)[C + 4], int cur, const unsigned* fs, unsigned xs,
+// Per-tile sums of one slot: one 32-bit word per feature, then sum x (17
+// bits) with the count (13 bits) in one word and sum y (16 bits) with sum z
+// (15 bits) in another, so a run of equal labels leaves through C + 2
+// shared atomics.  The widths hold a whole tile: at most 4096 voxels, local
+// x < 64, y < 32, z < 8.
+struct PackedSums {
+    static constexpr int kCnt = 17, kZ = 16;
+};
+
+template <typename T, int C>
+__device__ __forceinline__ void flush_run(unsigned (*pk)[C + 2], int cur, const unsigned* fs, unsigned xs,
                                           unsigned cnt, int yl, int zl)
 {
     if (cur == kNoSlot || cnt == 0) return;
 #pragma unroll
-    for (int c = 0; c < C; ++c) atomicAdd(&acc[cur][c], fs[c]);
-    atomicAdd(&acc[cur][C], xs);
-    atomicAdd(&acc[cur][C + 1], cnt * (unsigned)yl);
-    atomicAdd(&acc[cur][C + 2], cnt * (unsigned)zl);
-    atomicAdd(&acc[cur][C + 3], cnt);
+    for (int c = 0; c < C; ++c) atomicAdd(&pk[cur][c], fs[c]);
+    atomicAdd(&pk[cur][C], xs | (cnt << PackedSums::kCnt));
+    atomicAdd(&pk[cur][C + 1], (cnt * (unsigned)yl) | ((cnt * (unsigned)zl) << PackedSums::kZ));
 }
 
 // One tile of one image (request req): everything of steps 1-5 above.  A
 // tile reached by more than kCap centres is appended to the crowded-tile
 // list as (req << 40 | tile) and left to the per-voxel kernel.
-template <typename T, int C, typename SH>
+template <typename T, int C, typename SH, bool STAGED = false>
 __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t req, Smem<T, C, SH>& s,
                                           int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
 {
@@ -182,6 +192,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     constexpr int F = C + 4;
     constexpr int SPR = TX / kSeg;  // segments per row
     static_assert(NBOX % kWarps == 0, "boxes per warp");
+    static_assert(TV <= 4096 && TX <= 64 && TY <= 32 && TZ <= 8, "packed per-tile sums");
     static_assert(NBX + NBY + NBZ <= 32, "box mask bits");
     static_assert(TX % kSeg == 0, "row segments");
 
@@ -193,10 +204,11 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     const int ex = min(TX, N0 - X0), ey = min(TY, N1 - Y0), ez = min(TZ, N2 - Z0);
 
     if (tid == 0) { s.nstage = 0; s.ncand = 0; }
-    for (int i = tid; i < kCap * F; i += kThreads) (&s.acc[0][0])[i] = 0u;
+    for (int i = tid; i < kCap * (C + 2); i += kThreads) (&s.pk[0][0])[i] = 0u;
 
-    // ---- 1. stage the tile as channel planes --------------------------------
-    if constexpr (sizeof(T) == 1 && C == 3) {
+    // ---- 1. stage the tile as channel planes (done by the caller when STAGED) ----
+    if constexpr (STAGED) {
+    } else if constexpr (sizeof(T) == 1 && C == 3) {
         // full rows: 12-byte groups (4 voxels) -> one word per plane
         const bool fast = (ex == TX) && ((N0 * 3) % 4 == 0) && (((uintptr_t)img & 3) == 0);
         if (fast) {
@@ -481,7 +493,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
         for (int c = 0; c < C; ++c) fs[c] = 0;
         // start a new run at slot sl (flushing the previous one)
         auto next_run = [&](int sl) {
-            flush_run<C>(s.acc, cur, fs, xs, cnt, yl, zl);
+            flush_run<T, C>(s.pk, cur, fs, xs, cnt, yl, zl);
             cur = sl;
             curlab = sl == kNoSlot ? -1 : s.cand[sl];
 #pragma unroll
@@ -553,20 +565,116 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
                 lrow[b] = curlab;
             }
         }
-        flush_run<C>(s.acc, cur, fs, xs, cnt, yl, zl);
+        flush_run<T, C>(s.pk, cur, fs, xs, cnt, yl, zl);
     }
     __syncthreads();
 
     // ---- 5. per-tile sums, shifted to global coordinates ----------------------
     for (int i = tid; i < nc * F; i += kThreads) {
         const int sl = i / F, f = i % F;
-        const unsigned long long cnt = s.acc[sl][C + 3];
+        const unsigned wx = s.pk[sl][C], wyz = s.pk[sl][C + 1];
+        const unsigned long long cnt = wx >> PackedSums::kCnt;
         if (!cnt) continue;
-        unsigned long long v = s.acc[sl][f];
-        if (f == C) v += cnt * (unsigned long long)X0;
-        if (f == C + 1) v += cnt * (unsigned long long)Y0;
-        if (f == C + 2) v += cnt * (unsigned long long)Z0;
+        unsigned long long v;
+        if (f < C) v = s.pk[sl][f];
+        else if (f == C) v = (wx & ((1u << PackedSums::kCnt) - 1)) + cnt * (unsigned long long)X0;
+        else if (f == C + 1) v = (wyz & ((1u << PackedSums::kZ) - 1)) + cnt * (unsigned long long)Y0;
+        else if (f == C + 2) v = (wyz >> PackedSums::kZ) + cnt * (unsigned long long)Z0;
+        else v = cnt;
         atomicAdd(&acc[(int64_t)s.cand[sl] * F + f], v);
+    }
+}
+
+// The tile as the TMA copy leaves it -- bytes [z][y][x * C * sizeof(T)], rows
+// contiguous, out-of-image voxels zero -- rewritten as the channel planes.
+template <typename T, int C, typename SH>
+__device__ __forceinline__ void planes_from_raw(Smem<T, C, SH>& s, const unsigned char* raw)
+{
+    using S = Smem<T, C, SH>;
+    constexpr int TX = SH::TX, TY = SH::TY, TZ = SH::TZ;
+    constexpr int RB = TX * C * (int)sizeof(T);  // raw row bytes
+    const int tid = threadIdx.x;
+    if constexpr (sizeof(T) == 1 && C == 3) {
+        constexpr int GPR = TX / 4;  // 12-byte groups (4 voxels) per row
+        for (int i = tid; i < TY * TZ * GPR; i += kThreads) {
+            const int r = i / GPR, gi = i % GPR, yl = r % TY, zl = r / TY;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(raw + r * RB + gi * 12);
+            const uint32_t a = src[0], b = src[1], cc = src[2];
+            // bytes: a = R0 G0 B0 R1, b = G1 B1 R2 G2, cc = B2 R3 G3 B3
+            unsigned char* row = s.planes + zl * S::PPB + yl * S::RPB + gi * 4;
+            *reinterpret_cast<uint32_t*>(row) = __byte_perm(__byte_perm(a, b, 0x0630), cc, 0x5210);
+            *reinterpret_cast<uint32_t*>(row + S::CPB) = __byte_perm(__byte_perm(a, b, 0x0741), cc, 0x6210);
+            *reinterpret_cast<uint32_t*>(row + 2 * S::CPB) = __byte_perm(__byte_perm(a, b, 0x0052), cc, 0x7410);
+        }
+    } else {
+        static_assert(C == 1, "single-channel raw rows are plane rows");
+        constexpr int WPR = RB / 4;  // words per row
+        for (int i = tid; i < TY * TZ * WPR; i += kThreads) {
+            const int r = i / WPR, wi = i % WPR, yl = r % TY, zl = r / TY;
+            const uint32_t v = reinterpret_cast<const uint32_t*>(raw + r * RB)[wi];
+            *reinterpret_cast<uint32_t*>(s.planes + zl * S::PPB + yl * S::RPB + wi * 4) = v;
+        }
+    }
+}
+
+template <typename T, int C, typename SH>
+struct SmemTma {
+    Smem<T, C, SH> s;
+    alignas(128) unsigned char raw[SH::TX * C * sizeof(T) * SH::TY * SH::TZ];
+    uint64_t mbar;
+};
+
+constexpr long long kTmaWaitLimit = 1LL << 26;  // polls of the copy's mbarrier before giving up
+
+// One image, persistent: each CTA walks tiles blockIdx.x, + gridDim.x, ...
+// and the TMA copy of its next tile's image runs while it computes the
+// current one.  A wait that runs out sets *status and ends the CTA.
+template <typename T, int C, typename SH>
+__global__ void __launch_bounds__(kThreads, 4)
+assign_tile_tma_kernel(TileArgs a, const __grid_constant__ CUtensorMap map, int64_t ntiles,
+                       int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count, unsigned* __restrict__ status)
+{
+    extern __shared__ __align__(128) unsigned char smem_tma[];
+    SmemTma<T, C, SH>& st = *reinterpret_cast<SmemTma<T, C, SH>*>(smem_tma);
+    constexpr uint32_t kBytes = (uint32_t)sizeof(st.raw);
+    constexpr int TX = SH::TX, TY = SH::TY, TZ = SH::TZ;
+    const int tid = threadIdx.x;
+    const int ntx = a.ntx, nty = a.nty;
+    auto issue = [&](int64_t t) {
+        const int X0 = (int)(t % ntx) * TX, Y0 = (int)((t / ntx) % nty) * TY, Z0 = (int)(t / ((int64_t)ntx * nty)) * TZ;
+        tc::mbar_arrive_expect_tx(&st.mbar, kBytes);
+        const int xb = X0 * C * (int)sizeof(T);  // a multiple of 16 bytes
+        if constexpr (SH::NDIM == 3) tc::tma_load_3d(st.raw, &map, xb, Y0, Z0, &st.mbar);
+        else tc::tma_load_2d(st.raw, &map, xb, Y0, &st.mbar);
+    };
+    int64_t t = blockIdx.x;
+    if (tid == 0) {
+        tc::mbar_init(&st.mbar, 1);
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0 && t < ntiles) issue(t);
+    uint32_t parity = 0;
+    for (; t < ntiles; t += gridDim.x) {
+        bool done = false;
+        for (long long it = 0; it < kTmaWaitLimit && !done; ++it) done = tc::mbar_try_wait(&st.mbar, parity);
+        if (!__syncthreads_and(done)) {
+            if (tid == 0) {
+                atomicExch(status, 1u);
+                // give the copy in flight one more bounded wait before leaving
+                for (long long it = 0; it < kTmaWaitLimit && !tc::mbar_try_wait(&st.mbar, parity); ++it) {}
+            }
+            return;
+        }
+        parity ^= 1u;
+        planes_from_raw<T, C, SH>(st.s, st.raw);
+        __syncthreads();  // the raw buffer is free again
+        if (tid == 0 && t + gridDim.x < ntiles) {
+            tc::fence_proxy_async_smem();
+            issue(t + gridDim.x);
+        }
+        tile_body<T, C, SH, true>(a, (int)t, 0, st.s, ovf_tiles, ovf_count);
+        __syncthreads();  // this tile's shared state is no longer read
     }
 }
 
@@ -634,7 +742,7 @@ inline auto with_shape(int shape, F&& f)
 }
 
 template <typename T, int C, typename SH>
-inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st, bool want_tma)
 {
     const Geom& g = c->g;
     Workspace& w = c->ws;
@@ -661,11 +769,36 @@ inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaSt
     a.tx = SH::TX;
     a.ty = SH::TY;
     a.tz = SH::TZ;
-    const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
-    tile::assign_tile_kernel<T, C, SH><<<(unsigned)ntiles, tile::kThreads, smem, st>>>(a, w.ovf_tiles, w.ovf_count);
-    count_launch(c);
-    prof_end(c, pr, st);
-    if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_kernel"))) return rc;
+    alignas(64) CUtensorMap map;
+    const bool tma = want_tma && image_tma_ok(g, img, (int)sizeof(T)) &&
+                     encode_image_map(&map, g, img, (int)sizeof(T), SH::TX, SH::TY, SH::TZ) == SSLIC_OK;
+    if (tma) {
+        // persistent: as many CTAs as fit at once, each walking its share of the tiles
+        const size_t smem_t = sizeof(tile::SmemTma<T, C, SH>);
+        if ((rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_tma_kernel<T, C, SH>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t),
+                             "smem attribute")))
+            return rc;
+        int per_sm = 0;
+        if ((rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &per_sm, tile::assign_tile_tma_kernel<T, C, SH>, tile::kThreads, smem_t),
+                             "occupancy")))
+            return rc;
+        const int64_t grid = imin64(ntiles, (int64_t)c->sms * (per_sm > 0 ? per_sm : 1));
+        const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
+        tile::assign_tile_tma_kernel<T, C, SH><<<(unsigned)grid, tile::kThreads, smem_t, st>>>(
+            a, map, ntiles, w.ovf_tiles, w.ovf_count, w.hc_err);
+        count_launch(c);
+        prof_end(c, pr, st);
+        c->status_pending = 1;
+        if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_tma_kernel"))) return rc;
+    } else {
+        const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
+        tile::assign_tile_kernel<T, C, SH><<<(unsigned)ntiles, tile::kThreads, smem, st>>>(a, w.ovf_tiles, w.ovf_count);
+        count_launch(c);
+        prof_end(c, pr, st);
+        if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_kernel"))) return rc;
+    }
     return launch_voxel_tiles(c, img, labels, SH::TX, SH::TY, SH::TZ, ntx, nty, st);
 }
 
@@ -675,7 +808,10 @@ int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t s
     int shape = c->tile_shape;
     if (shape < 0) shape = tuned_tile_shape(c->g);
     if (shape < 0) shape = default_tile_shape(c->g);
-    return with_shape<NDIM>(shape, [&](auto sh) { return launch_tile_shape<T, C, decltype(sh)>(c, img, labels, st); });
+    const int b = num_base_shapes(NDIM);
+    return with_shape<NDIM>(shape % b, [&](auto sh) {
+        return launch_tile_shape<T, C, decltype(sh)>(c, img, labels, st, shape >= b);
+    });
 }
 
 // batched form: one persistent launch over the (request, tile) queue of all
@@ -698,7 +834,8 @@ template <typename T, int C, int NDIM>
 cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
                               unsigned* ovf_count, int grid, cudaStream_t st)
 {
-    return with_shape<NDIM>(shape, [&](auto sh) {
+    // the batched queue stages with plain loads: a TMA-staged index runs its base shape
+    return with_shape<NDIM>(shape % num_base_shapes(NDIM), [&](auto sh) {
         return launch_queue_shape<T, C, decltype(sh)>(reqs, tpre, nR, ovf, ovf_count, grid, st);
     });
 }

@@ -178,6 +178,7 @@ struct sslic_ctx {
     int sms = 148;
     int busy = 0;
     int tile_shape = -1;   // assignment tile shape index, -1 = chosen from the grid (assign_tile.cu)
+    int status_pending = 0;  // a kernel with bounded waits ran: check the status flag
     char err[512] = {0};
     // tracing
     int prof_on = 0;
@@ -200,6 +201,10 @@ int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t 
 size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
+// TMA tensor map of an image as bytes [N_2][N_1][N_0 * C * esz] (tma.cu);
+// map points at 128 bytes, 64-byte aligned
+bool image_tma_ok(const Geom& g, const void* img, int esz);
+int encode_image_map(void* map, const Geom& g, const void* img, int esz, int tx, int ty, int tz);
 // high-channel float images (hc.cu)
 bool hc_applies(const Geom& g);
 int64_t hc_num_tiles(const Geom& g);
@@ -207,6 +212,7 @@ int launch_hc(sslic_ctx* c, const float* img, int32_t* labels, cudaStream_t st);
 int launch_hc_probe(sslic_ctx* c, const float* img, int32_t* labels, int64_t tile, float* dots, int* cand,
                     float* mu, cudaStream_t st);
 int default_tile_shape(const Geom& g);
+int num_base_shapes(int ndim);
 int num_tile_shapes(int ndim);
 void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz);
 template <typename T, int C, int NDIM>

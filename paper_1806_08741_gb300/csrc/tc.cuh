@@ -1,8 +1,9 @@
-// tc.cuh -- the sm_100-family tensor-core primitives used by the precision
-// form: tensor-memory allocation, tcgen05.mma (BF16 inputs, FP32
-// accumulation in tensor memory), commit to an mbarrier, tensor-memory loads,
-// the fences between them, and shared-memory matrix descriptors for operands
-// in the canonical K-major layout without swizzling.
+// tc.cuh -- the sm_100-family asynchronous primitives: tensor-memory
+// allocation, tcgen05.mma (BF16 inputs, FP32 accumulation in tensor memory),
+// commit to an mbarrier, tensor-memory loads, the fences between them,
+// shared-memory matrix descriptors for operands in the canonical K-major
+// layout without swizzling (precision form), and TMA tiled loads completing
+// on an mbarrier (image staging of the assignment kernel).
 //
 // Operand layout (K-major, no swizzle): the matrix is cut into core matrices
 // of 8 rows x 16 bytes (8 BF16 values along K), each stored as 128
@@ -75,6 +76,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok != 0;
+}
+
+// make an initialised mbarrier visible to the async proxy (TMA, tensor core)
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// this thread's arrival, announcing `bytes` of transactions the barrier must also see
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// ---- TMA: a tiled box of a tensor (map built on the host) into shared memory ----
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* map, int x, int y, int z, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)) : "memory");
 }
 
 // ---- MMA: D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread ----

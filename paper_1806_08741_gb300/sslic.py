@@ -127,7 +127,7 @@ def load(path: str = LIB_PATH):
         getattr(L, f).restype = ctypes.c_int
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.sslic_num_tile_shapes.argtypes = [ctypes.c_int32, i32p]
-    L.sslic_tile_shape_info.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p]
+    L.sslic_tile_shape_info.argtypes = [ctypes.c_int32, ctypes.c_int32, i32p, i32p, i32p]
     L.sslic_set_tile_shape.argtypes = [C, ctypes.c_int32]
     L.sslic_get_tile_shape.argtypes = [C, i32p]
     L.sslic_autotune.argtypes = [C, vp, vp, vp, ctypes.c_int32, i32p, ctypes.POINTER(ctypes.c_float)]
@@ -435,10 +435,11 @@ def num_tile_shapes(ndim: int) -> int:
 def tile_shape_info(ndim: int, shape: int) -> dict:
     dims = (ctypes.c_int32 * 3)()
     vl = ctypes.c_int32(0)
-    rc = load().sslic_tile_shape_info(int(ndim), int(shape), dims, ctypes.byref(vl))
+    tma = ctypes.c_int32(0)
+    rc = load().sslic_tile_shape_info(int(ndim), int(shape), dims, ctypes.byref(vl), ctypes.byref(tma))
     if rc != SSLIC_OK:
         raise SSLICError(rc, "sslic_tile_shape_info")
-    return {"dims": tuple(int(d) for d in dims), "voxels_per_lane": int(vl.value)}
+    return {"dims": tuple(int(d) for d in dims), "voxels_per_lane": int(vl.value), "tma_staged": bool(tma.value)}
 
 
 def tune_forget() -> None:

@@ -87,19 +87,24 @@ def test_create_rejects_bad_sizes(lib):
 
 def test_tile_shape_table_host_only(lib):
     from paper_1806_08741_gb300 import sslic as S
-    assert S.num_tile_shapes(3) == 4 and S.num_tile_shapes(2) == 3 and S.num_tile_shapes(1) == 0
+    assert S.num_tile_shapes(3) == 8 and S.num_tile_shapes(2) == 6 and S.num_tile_shapes(1) == 0
     seen = set()
     for nd in (2, 3):
-        for s in range(S.num_tile_shapes(nd)):
+        n = S.num_tile_shapes(nd)
+        for s in range(n):
             info = S.tile_shape_info(nd, s)
             tx, ty, tz = info["dims"]
             assert info["voxels_per_lane"] in (2, 4)
             assert tx % 16 == 0 and (tz == 1) == (nd == 2)
-            seen.add((nd, info["dims"], info["voxels_per_lane"]))
-    assert len(seen) == 7  # every index names a different configuration
+            assert info["tma_staged"] == (s >= n // 2)
+            if s >= n // 2:   # the TMA-staged twin of a plain shape
+                twin = S.tile_shape_info(nd, s - n // 2)
+                assert (twin["dims"], twin["voxels_per_lane"]) == (info["dims"], info["voxels_per_lane"])
+            seen.add((nd, info["dims"], info["voxels_per_lane"], info["tma_staged"]))
+    assert len(seen) == 14  # every index names a different configuration
     dims = (ctypes.c_int32 * 3)()
-    assert lib.sslic_tile_shape_info(3, 4, dims, None) == -1
-    assert lib.sslic_tile_shape_info(1, 0, dims, None) == -1
+    assert lib.sslic_tile_shape_info(3, 8, dims, None, None) == -1
+    assert lib.sslic_tile_shape_info(1, 0, dims, None, None) == -1
     assert lib.sslic_set_tile_shape(None, 0) == -1
     assert lib.sslic_autotune(None, None, None, None, 1, None, None) == -1
 
@@ -109,11 +114,11 @@ def test_tune_table_host_only(lib):
     S.tune_forget()
     p = S.Params(size=(300, 200, 100), grid=(16, 16, 16))
     assert S.tune_lookup(p) == -1
-    S.tune_record(p, 3)
-    assert S.tune_lookup(p) == 3
+    S.tune_record(p, 7)
+    assert S.tune_lookup(p) == 7
     assert S.tune_lookup(S.Params(size=(300, 200, 100), grid=(8, 8, 8))) == -1   # keyed by grid
-    assert S.tune_lookup(S.Params(size=(50, 60, 70), grid=(16, 16, 16))) == 3    # not by size
-    for bad in (-1, 4):
+    assert S.tune_lookup(S.Params(size=(50, 60, 70), grid=(16, 16, 16))) == 7    # not by size
+    for bad in (-1, 8):
         with pytest.raises(S.SSLICError):
             S.tune_record(p, bad)
     with pytest.raises(S.SSLICError) as e:

@@ -107,6 +107,10 @@ ITER_CASES = [
     ("3d_ragged_S8", lambda: _synth((70, 50, 37)), (8, 8, 8), 10.0),
     ("3d_small_S_overflow", lambda: _synth((40, 30, 20)), (3, 3, 3), 5.0),
     ("3d_aniso", lambda: _synth((80, 48, 30)), (16, 8, 4), 10.0),
+    # rows a multiple of 16 bytes (TMA-staged tiles), ragged along y and z
+    ("3d_tma_ragged", lambda: _synth((45, 37, 64)), (16, 16, 16), 10.0),
+    ("2d_tma_ragged", lambda: _synth((150, 208)), (16, 16), 10.0),
+    ("3d_u16_tma", lambda: _synth((40, 24, 32), 1, "u16", sigma=300), (8, 8, 8), 10.0),
     ("3d_u16", lambda: _synth((64, 40, 30), 1, "u16", sigma=300), (8, 8, 8), 10.0),
     ("2d_gray_u8", lambda: _synth((150, 100), 1), (10, 10), 5.0),
     ("1d", lambda: _synth((1000,), 3), (7,), 10.0),
@@ -152,7 +156,7 @@ def _gpu_iterate_shape(img, grid, centres, m, shape):
 
 SHAPE_CASES = [c for c in ITER_CASES if c[0] in
                ("2d_256", "2d_ragged", "2d_S8", "3d_S16", "3d_ragged_S8", "3d_small_S_overflow", "3d_aniso",
-                "3d_u16", "2d_gray_u8")]
+                "3d_u16", "2d_gray_u8", "3d_tma_ragged", "2d_tma_ragged", "3d_u16_tma")]
 
 
 @pytest.mark.parametrize("name,mk,grid,m", SHAPE_CASES, ids=[c[0] for c in SHAPE_CASES])
@@ -182,7 +186,7 @@ def test_autotune_picks_a_measured_shape_and_keeps_results():
         lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
         t = ctx.autotune(dimg, lab, reps=2)
         assert 0 <= t["best"] < S.num_tile_shapes(3)
-        assert len(t["ms"]) == 4 and all(v > 0 for v in t["ms"])
+        assert len(t["ms"]) == 8 and all(v > 0 for v in t["ms"])
         assert t["ms"][t["best"]] == min(t["ms"])
         assert ctx.tile_shape == t["best"]
         cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")

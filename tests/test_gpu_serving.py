@@ -102,7 +102,7 @@ def test_server_rejects():
         assert e.value.code == -6
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2])
+@pytest.mark.parametrize("shape", [0, 1, 2, 5])
 def test_served_results_equal_alone_for_each_recorded_shape(shape):
     """The tile shape recorded for an image type (as by autotune) is the one
     the batched form uses; no shape changes a result."""

@@ -98,7 +98,12 @@ struct Smem {
     uint8_t blist[NBOX][kCap + 2];       // per warp box: reaching slots, ascending, even length
     uint8_t bcnt[NBOX];
     alignas(16) unsigned char planes[C * CPB];
-    unsigned pk[kCap][C + 2];        // per-tile sums: features, then two packed words (see PackedSums)
+    // per-tile sums: kCopies copies (lane & 7 picks one, so lanes of a warp
+    // adding to the same slot seldom meet on one address), each kCap x (C + 2)
+    // words -- features, then two packed words (see PackedSums) -- with an odd
+    // copy stride so the copies of one word sit in different banks
+    static constexpr int kCopies = 8, kPkStride = kCap * (C + 2) + 1;
+    unsigned pk[kCopies * kPkStride];
     float cpos[kCap][3];
     int cand[kCap];
     int tmp[kCap];
@@ -153,14 +158,15 @@ struct PackedSums {
 };
 
 template <typename T, int C>
-__device__ __forceinline__ void flush_run(unsigned (*pk)[C + 2], int cur, const unsigned* fs, unsigned xs,
-                                          unsigned cnt, int yl, int zl)
+__device__ __forceinline__ void flush_run(unsigned* pk, int cur, const unsigned* fs, unsigned xs, unsigned cnt, int yl,
+                                          int zl)
 {
     if (cur == kNoSlot || cnt == 0) return;
+    unsigned* w = pk + cur * (C + 2);
 #pragma unroll
-    for (int c = 0; c < C; ++c) atomicAdd(&pk[cur][c], fs[c]);
-    atomicAdd(&pk[cur][C], xs | (cnt << PackedSums::kCnt));
-    atomicAdd(&pk[cur][C + 1], (cnt * (unsigned)yl) | ((cnt * (unsigned)zl) << PackedSums::kZ));
+    for (int c = 0; c < C; ++c) atomicAdd(&w[c], fs[c]);
+    atomicAdd(&w[C], xs | (cnt << PackedSums::kCnt));
+    atomicAdd(&w[C + 1], (cnt * (unsigned)yl) | ((cnt * (unsigned)zl) << PackedSums::kZ));
 }
 
 // One tile of one image (request req): everything of steps 1-5 above.  A
@@ -204,7 +210,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     const int ex = min(TX, N0 - X0), ey = min(TY, N1 - Y0), ez = min(TZ, N2 - Z0);
 
     if (tid == 0) { s.nstage = 0; s.ncand = 0; }
-    for (int i = tid; i < kCap * (C + 2); i += kThreads) (&s.pk[0][0])[i] = 0u;
+    for (int i = tid; i < S::kCopies * S::kPkStride; i += kThreads) s.pk[i] = 0u;
 
     // ---- 1. stage the tile as channel planes (done by the caller when STAGED) ----
     if constexpr (STAGED) {
@@ -457,6 +463,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     __syncthreads();
 
     // ---- 4. row segments: labels out, run sums in -------------------------------
+    unsigned* const mypk = s.pk + (lane & (S::kCopies - 1)) * S::kPkStride;
     const bool vec_ok = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
     for (int sg = tid; sg < TY * TZ * SPR; sg += kThreads) {
         // lanes of a warp take segments in different z planes (different
@@ -493,7 +500,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
         for (int c = 0; c < C; ++c) fs[c] = 0;
         // start a new run at slot sl (flushing the previous one)
         auto next_run = [&](int sl) {
-            flush_run<T, C>(s.pk, cur, fs, xs, cnt, yl, zl);
+            flush_run<T, C>(mypk, cur, fs, xs, cnt, yl, zl);
             cur = sl;
             curlab = sl == kNoSlot ? -1 : s.cand[sl];
 #pragma unroll
@@ -565,18 +572,26 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
                 lrow[b] = curlab;
             }
         }
-        flush_run<T, C>(s.pk, cur, fs, xs, cnt, yl, zl);
+        flush_run<T, C>(mypk, cur, fs, xs, cnt, yl, zl);
     }
     __syncthreads();
 
     // ---- 5. per-tile sums, shifted to global coordinates ----------------------
+    // the copies are summed field by field (each field's total fits its width)
     for (int i = tid; i < nc * F; i += kThreads) {
         const int sl = i / F, f = i % F;
-        const unsigned wx = s.pk[sl][C], wyz = s.pk[sl][C + 1];
+        unsigned wx = 0, wyz = 0, wf = 0;
+#pragma unroll
+        for (int k = 0; k < S::kCopies; ++k) {
+            const unsigned* w = s.pk + k * S::kPkStride + sl * (C + 2);
+            wx += w[C];
+            if (f == C + 1 || f == C + 2) wyz += w[C + 1];
+            if (f < C) wf += w[f];
+        }
         const unsigned long long cnt = wx >> PackedSums::kCnt;
         if (!cnt) continue;
         unsigned long long v;
-        if (f < C) v = s.pk[sl][f];
+        if (f < C) v = wf;
         else if (f == C) v = (wx & ((1u << PackedSums::kCnt) - 1)) + cnt * (unsigned long long)X0;
         else if (f == C + 1) v = (wyz & ((1u << PackedSums::kZ) - 1)) + cnt * (unsigned long long)Y0;
         else if (f == C + 2) v = (wyz >> PackedSums::kZ) + cnt * (unsigned long long)Z0;

@@ -52,49 +52,79 @@ constexpr int kCclTV = 2048;
 // invariant through *err instead of spinning.
 constexpr int kWalkLimit = 1 << 26;
 
-__device__ __forceinline__ int uf_find(int* par, int x, unsigned* err)
+// Every walk checks its index against the forest's size n and gives up
+// (flag 2) instead of leaving it.
+__device__ __forceinline__ bool uf_bad(int x, int n, unsigned* err)
+{
+    if (x >= 0 && x < n) return false;
+    atomicExch(err, 2u);
+    return true;
+}
+
+__device__ __forceinline__ int uf_find(int* par, int x, int n, unsigned* err)
 {
     // path halving: every write points a node at one of its ancestors, which
     // is in the same set and has a smaller index, so concurrent finds and
     // links keep the forest acyclic
     volatile int* vp = par;
     for (int i = 0; i < kWalkLimit; ++i) {
+        if (uf_bad(x, n, err)) return -1;
         const int p = vp[x];
         if (p == x) return x;
+        if (uf_bad(p, n, err)) return -1;
         const int gp = vp[p];
         if (gp == p) return p;
         vp[x] = gp;
         x = gp;
     }
     atomicExch(err, 1u);
-    return x;
+    return -1;
 }
 
 // read-only walk to the root, for the compress / flatten passes: those run
 // after every union has finished, and a halving write landing after another
 // thread's final "parent = root" store would leave a non-root parent behind
-__device__ __forceinline__ int uf_root(const int* par, int x, unsigned* err)
+__device__ __forceinline__ int uf_root(const int* par, int x, int n, unsigned* err)
 {
     const volatile int* vp = par;
     for (int i = 0; i < kWalkLimit; ++i) {
+        if (uf_bad(x, n, err)) return -1;
         const int p = vp[x];
         if (p == x) return x;
         x = p;
     }
     atomicExch(err, 1u);
-    return x;
+    return -1;
 }
 
-__device__ __noinline__ void uf_unite(int* par, int a, int b, unsigned* err)
+__device__ __noinline__ void uf_unite(int* par, int a, int b, int n, unsigned* err)
 {
-    a = uf_find(par, a, err);
-    b = uf_find(par, b, err);
+    a = uf_find(par, a, n, err);
+    b = uf_find(par, b, n, err);
     for (int i = 0; i < kWalkLimit && a != b; ++i) {
+        if (a < 0 || b < 0) return;  // flagged
         if (a < b) { int t = a; a = b; b = t; }
         const int old = atomicMin(&par[a], b);
         if (old == a) return;       // a was a root and now hangs under b
-        a = uf_find(par, old, err); // a had been re-linked meanwhile: retry from its root
-        b = uf_find(par, b, err);
+        a = uf_find(par, old, n, err); // a had been re-linked meanwhile: retry from its root
+        b = uf_find(par, b, n, err);
+    }
+    if (a != b) atomicExch(err, 1u);
+}
+
+// The same union for a tile's forest in shared memory, inlined so the walks
+// and the link use shared-memory instructions
+__device__ __forceinline__ void uf_unite_local(int* par, int a, int b, unsigned* err)
+{
+    a = uf_find(par, a, kCclTV, err);
+    b = uf_find(par, b, kCclTV, err);
+    for (int i = 0; i < kWalkLimit && a != b; ++i) {
+        if (a < 0 || b < 0) return;  // flagged
+        if (a < b) { int t = a; a = b; b = t; }
+        const int old = atomicMin(&par[a], b);
+        if (old == a) return;
+        a = uf_find(par, old, kCclTV, err);
+        b = uf_find(par, b, kCclTV, err);
     }
     if (a != b) atomicExch(err, 1u);
 }
@@ -178,7 +208,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
 #pragma unroll 1
         for (int i = 1; i < RPW; ++i) {
             const int e = (warp * RPW + i) * 32 + lane;
-            if (lane == 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite(par, e, e - 1, err);
+            if (lane == 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite_local(par, e, e - 1, err);
         }
     } else {
 #pragma unroll 1
@@ -188,7 +218,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             const int yl = (e / TX) % TY;
             const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
             const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
-            if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite(par, e, e - TX, err);
+            if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite_local(par, e, e - TX, err);
         }
     }
     __syncthreads();
@@ -198,14 +228,14 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     //     labels across the same faces (that path is already united).
     if (NDIM == 1) {
         const int e = warp * RPW * 32;
-        if (lane == 0 && e > 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite(par, e, e - 1, err);
+        if (lane == 0 && e > 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite_local(par, e, e - 1, err);
     } else if (NDIM == 2) {
         const int e = warp * RPW * 32 + lane;
         const int L = lab[e];
         const int yl = (e / TX) % TY;
         const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
         const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
-        if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite(par, e, e - TX, err);
+        if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite_local(par, e, e - TX, err);
     } else {
         constexpr int P = TX * TY;
 #pragma unroll 1
@@ -218,7 +248,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             const bool via_y = zm && yl > 0 && lab[e - TX] == L && lab[e - TX - P] == L;
             const unsigned mz = __ballot_sync(0xffffffffu, zm);
             const unsigned want = mz & (starts | ~(mz << 1)) & ~__ballot_sync(0xffffffffu, via_y);
-            if (want >> lane & 1u) uf_unite(par, e, e - P, err);
+            if (want >> lane & 1u) uf_unite_local(par, e, e - P, err);
         }
     }
     __syncthreads();
@@ -232,8 +262,8 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int e = (warp * RPW + i) * 32 + lane;
         const int L = lab[e];
         if (L != INT_MIN && (lane == 0 || L != lab[e - (lane > 0)])) {
-            const int r = uf_root(par, e, err);
-            for (int x = e, n = 0; x != r && n < kWalkLimit; ++n) {
+            const int r = uf_root(par, e, kCclTV, err);
+            for (int x = e, n = 0; r >= 0 && x != r && n < kWalkLimit; ++n) {  // r < 0: flagged, left alone
                 const int nx = par[x];
                 par[x] = r;
                 x = nx;
@@ -385,7 +415,7 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
             if (old == key) break;
             h = (h + 1) & (kFaceHash - 1);
         }
-        if (fresh) uf_unite(gparent, base_here + (int)la, tile_base[nb] + (int)lb, &counters[3]);
+        if (fresh) uf_unite(gparent, base_here + (int)la, tile_base[nb] + (int)lb, (int)counters[0], &counters[3]);
     }
 }
 
@@ -399,7 +429,8 @@ __global__ void ccl_flatten_kernel(int* gparent, const unsigned* __restrict__ co
 {
     const int64_t M = counters[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = uf_root(gparent, (int)i, &counters[3]);
+        const int r = uf_root(gparent, (int)i, (int)M, &counters[3]);
+        if (r < 0) continue;  // flagged
         gparent[i] = r;
         atomicAdd(&root_size[r], (unsigned long long)comp_size[i]);
         atomicMin(&root_first[r], comp_first[i]);
@@ -610,9 +641,8 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     for (int attempt = 0; attempt < 2; ++attempt) {
         if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
         ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
-                                                              w.comp_label,
-                                                              w.comp_size, w.comp_first, w.gparent, w.counters,
-                                                              w.m_cap, ntx, nty);
+                                                              w.comp_label, w.comp_size, w.comp_first, w.gparent,
+                                                              w.counters, w.m_cap, ntx, nty);
         count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
         if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -699,7 +729,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
         return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
     prof_end(c, pr, st);
-    if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a bounded walk ran out or an internal check failed");
+    if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a bounded walk ran out or an internal check failed (code %u)", hc[3]);
     if (num_labels) *num_labels = g.K + Mn;
     return SSLIC_OK;
 }

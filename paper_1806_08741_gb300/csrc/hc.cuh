@@ -254,13 +254,44 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
         }
         return __fadd_rn(dc, spatial(r));
     };
+    // two covering candidates at a time: their sums are independent chains
+    // (each chain keeps the canonical order)
+    auto exact2 = [&](const float (&xv)[CT], int ra, int rb, float& Da, float& Db) {
+        const float4* ca = reinterpret_cast<const float4*>(cf + ra * CT);
+        const float4* cb = reinterpret_cast<const float4*>(cf + rb * CT);
+        float da = 0.0f, db = 0.0f;
+#pragma unroll
+        for (int j = 0; j < CT / 4; ++j) {
+            const float4 u = ca[j], w = cb[j];
+            const float uv[4] = {u.x, u.y, u.z, u.w}, wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float ea = __fsub_rn(xv[4 * j + t], uv[t]), eb = __fsub_rn(xv[4 * j + t], wv[t]);
+                const float sa = __fmul_rn(ea, ea), sb = __fmul_rn(eb, eb);
+                da = (j == 0 && t == 0) ? sa : __fadd_rn(da, sa);
+                db = (j == 0 && t == 0) ? sb : __fadd_rn(db, sb);
+            }
+        }
+        Da = __fadd_rn(da, spatial(ra));
+        Db = __fadd_rn(db, spatial(rb));
+    };
     auto exact_best = [&](const float (&xv)[CT]) -> int {
         float best = kInfF;
         int bs = kNone;
-        for (uint32_t m = cov; m; m &= m - 1) {
-            const int r = __ffs(m) - 1;
-            const float D = exact(xv, r);
-            if (D < best) { best = D; bs = r; }  // ascending slots = ascending k
+        for (uint32_t m = cov; m; ) {
+            const int ra = __ffs(m) - 1;
+            m &= m - 1;
+            if (m) {
+                const int rb = __ffs(m) - 1;
+                m &= m - 1;
+                float Da, Db;
+                exact2(xv, ra, rb, Da, Db);
+                if (Da < best) { best = Da; bs = ra; }  // ascending slots = ascending k
+                if (Db < best) { best = Db; bs = rb; }
+            } else {
+                const float D = exact(xv, ra);
+                if (D < best) { best = D; bs = ra; }
+            }
         }
         return bs;
     };

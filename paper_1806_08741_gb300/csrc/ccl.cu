@@ -614,13 +614,21 @@ conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __r
     }
     // in place, a tile none of whose components changes label is left alone
     if (!__syncthreads_or(any) && inplace) return;
-    for (int e = threadIdx.x; e < kCclTV; e += kCclThreads) {
-        int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
-        if (x >= g.N[0] || y >= g.N[1] || z >= g.N[2]) continue;
-        const int64_t q = vidx(g, x, y, z);
-        const int l = lid_img[q];
-        if (!inplace || chg[l]) labels_out[q] = tab[l];
+    // the thread's voxels: all local ids in flight first, then the stores
+    constexpr int PT = kCclTV / kCclThreads;
+    int64_t qv[PT];
+    int lv[PT];
+#pragma unroll
+    for (int i = 0; i < PT; ++i) {
+        const int e = threadIdx.x + i * kCclThreads;
+        const int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
+        const bool in = x < g.N[0] && y < g.N[1] && z < g.N[2];
+        qv[i] = in ? vidx(g, x, y, z) : -1;
+        lv[i] = in ? (int)lid_img[qv[i]] : 0;
     }
+#pragma unroll
+    for (int i = 0; i < PT; ++i)
+        if (qv[i] >= 0 && lv[i] < nloc && (!inplace || chg[lv[i]])) labels_out[qv[i]] = tab[lv[i]];
 }
 
 // ---------------------------------------------------------------------------
@@ -663,7 +671,9 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     const int gb = c->sms * 8;
-    ccl_flatten_kernel<<<gb, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
+    // per-record passes: one thread per record, so the walks' latencies overlap
+    const unsigned gm = (unsigned)imax64(1, imin64((M + 255) / 256, (int64_t)1 << 30));
+    ccl_flatten_kernel<<<gm, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
                                            w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
@@ -671,7 +681,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
                                                                  w.gparent, w.root_size, w.fin, ntx, nty);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase1_kernel"))) return rc;
-    conn_phase2_kernel<NDIM><<<gb, 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
+    conn_phase2_kernel<NDIM><<<gm, 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
                                                   w.lid, w.tile_base, w.out_label, w.link, w.new_key, w.new_val,
                                                   w.counters, ntx, nty);
     count_launch(c);
@@ -716,7 +726,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
         count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "assign_new_kernel"))) return rc;
     }
-    conn_resolve_kernel<<<gb, 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
+    conn_resolve_kernel<<<gm, 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
     conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,

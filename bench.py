@@ -45,7 +45,13 @@ UNIT = "Gvoxel-iter/s"
 # of the dominant kernel at the default workload, from the ncu capture
 # summarised in profiles/, keyed by the SHA-256 of the kernel's source file:
 # a changed kernel reports null until it is profiled again.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {
+    # profiles/assign_tile_kernel_rgb3d_512x512x256.md: 202.8 MB read + 215.7 MB
+    # written per launch on the 67.1 M-voxel profiling workload, scaled by the
+    # voxel ratio (69.4x) to the 4.66 G-voxel launch
+    ("rgb3d_2048x1216x1871", "ab5ac041cdc6e732cfc30a1227b46574791dada1d1ad53a62c9eeaf8db58dc48"):
+        (202.845440e6 + 215.713536e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
+}
 
 
 def _sha(path):

@@ -242,8 +242,11 @@ SSLIC_API int sslic_tune_lookup(const sslic_params* p, int32_t* shape);
  * iterations leave after the round and queued requests are admitted, first
  * come first served, as soon as the HBM budget has room for their image,
  * labels, centres, bins and sums.  Each request's labels and centres are the
- * ones sslic_run gives for it alone.  Requests need enforce_connectivity = 0
- * and conv_threshold <= 0 (every request runs its max_iter iterations). */
+ * ones sslic_run gives for it alone.  Requests need enforce_connectivity = 0.  A request with
+ * conv_threshold > 0 stops after the round whose centre residual (computed
+ * as sslic_run computes it) falls below the threshold, as sslic_run would;
+ * while such requests are on the device, each round waits for the previous
+ * one to finish before it is formed. */
 typedef struct sslic_server sslic_server;
 
 typedef struct {
@@ -267,7 +270,7 @@ SSLIC_API int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, 
  * centres_host (K x (C+n) float32, written, may be NULL) must stay valid
  * until sslic_server_wait returns for the ticket; page-locked buffers let the
  * copies overlap the computation.  SSLIC_ENOMEM if the request alone exceeds
- * the budget; SSLIC_EUNSUPPORTED for connectivity or a convergence threshold. */
+ * the budget; SSLIC_EUNSUPPORTED for connectivity. */
 SSLIC_API int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* image_host,
                                   int32_t* labels_host, float* centres_host, int64_t* ticket);
 

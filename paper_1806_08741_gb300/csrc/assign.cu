@@ -137,39 +137,19 @@ __global__ void finalize_kernel(Geom g, float* __restrict__ ctr, unsigned long l
     if (k < g.K) finalize_one(g, ctr, acc, facc, k, rk, ne);
 }
 
-// deterministic residual reduction: fixed-order block sums, then one block
-constexpr int kRedThreads = 256;
-__global__ void resid_partial_kernel(const double* __restrict__ rk, const unsigned* __restrict__ ne,
-                                     int64_t K, double* __restrict__ part, unsigned* __restrict__ cpart)
+// deterministic residual reduction (resid_part / resid_combine)
+__global__ void __launch_bounds__(kRedThreads)
+resid_partial_kernel(const double* __restrict__ rk, const unsigned* __restrict__ ne, int64_t K,
+                     double* __restrict__ part, unsigned* __restrict__ cpart)
 {
-    __shared__ double sd[kRedThreads];
-    __shared__ unsigned sc[kRedThreads];
-    const int64_t per = (K + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = blockIdx.x * per, hi = imin64(K, lo + per);
-    double d = 0.0;
-    unsigned cnt = 0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) { d += rk[i]; cnt += ne[i]; }
-    sd[threadIdx.x] = d;
-    sc[threadIdx.x] = cnt;
-    __syncthreads();
-    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) { sd[threadIdx.x] += sd[threadIdx.x + o]; sc[threadIdx.x] += sc[threadIdx.x + o]; }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) { part[blockIdx.x] = sd[0]; cpart[blockIdx.x] = sc[0]; }
+    resid_part(rk, ne, K, blockIdx.x, &part[blockIdx.x], &cpart[blockIdx.x]);
 }
 
 __global__ void resid_final_kernel(const double* __restrict__ part, const unsigned* __restrict__ cpart,
-                                   int nparts, double* __restrict__ out)
+                                   double* __restrict__ out)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double d = 0.0;
-    unsigned long long cnt = 0;
-    for (int i = 0; i < nparts; ++i) { d += part[i]; cnt += cpart[i]; }
-    out[0] = cnt ? d / (double)cnt : 0.0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = resid_combine(part, cpart);
 }
-
-constexpr int kResidParts = 256;
 
 int launch_finalize(sslic_ctx* c, cudaStream_t st)
 {
@@ -185,7 +165,7 @@ int launch_finalize(sslic_ctx* c, cudaStream_t st)
     resid_partial_kernel<<<kResidParts, kRedThreads, 0, st>>>(w.resid_k, w.nonempty_k, g.K, w.resid_part,
                                                               w.resid_cnt_part);
     if ((rc = cuda_check(c, cudaGetLastError(), "resid_partial_kernel"))) return rc;
-    resid_final_kernel<<<1, 32, 0, st>>>(w.resid_part, w.resid_cnt_part, kResidParts, w.resid_out);
+    resid_final_kernel<<<1, 32, 0, st>>>(w.resid_part, w.resid_cnt_part, w.resid_out);
     prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "resid_final_kernel");
 }

@@ -48,6 +48,12 @@ struct Req {
     unsigned* chunk;        // scan chunk sums
     float* cen_out;         // K x (C + n)
     int perturb;
+    // requests with a convergence threshold: per-cluster residual terms and
+    // the parts of their reduction (null otherwise)
+    double* rk;             // K
+    unsigned* ne;           // K
+    double* rpart;          // kResidParts
+    unsigned* rcnt;         // kResidParts
 };
 
 // ---- kernels -----------------------------------------------------------------
@@ -195,7 +201,7 @@ __global__ void b_finalize(const Req* __restrict__ reqs, const int64_t* __restri
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = prefix_find(kpre, R, i);
         const Req& q = reqs[r];
-        finalize_one(q.a.g, const_cast<float*>(q.a.ctr), q.a.acc, q.a.facc, i - kpre[r], nullptr, nullptr);
+        finalize_one(q.a.g, const_cast<float*>(q.a.ctr), q.a.acc, q.a.facc, i - kpre[r], q.rk, q.ne);
     }
 }
 
@@ -212,6 +218,26 @@ __global__ void b_export(const Req* __restrict__ reqs, const int64_t* __restrict
         const int64_t e = i - epre[r];
         q.cen_out[e] = q.a.ctr[(e / W) * g.CW + (e % W)];
     }
+}
+
+// centre residual of the requests with a convergence threshold, in the same
+// fixed order as the single-image path (so each stops after the same
+// iteration as sslic_run would): part blockIdx.x of request blockIdx.y, ...
+__global__ void __launch_bounds__(kRedThreads)
+b_resid_parts(const Req* __restrict__ reqs, const int* __restrict__ nT)
+{
+    const int T = *nT;
+    for (int r = blockIdx.y; r < T; r += gridDim.y) {
+        const Req& q = reqs[r];
+        resid_part(q.rk, q.ne, q.a.g.K, blockIdx.x, &q.rpart[blockIdx.x], &q.rcnt[blockIdx.x]);
+    }
+}
+
+__global__ void b_resid_final(const Req* __restrict__ reqs, const int* __restrict__ nT, double* __restrict__ out)
+{
+    const int T = *nT;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < T; r += gridDim.x * blockDim.x)
+        out[r] = resid_combine(reqs[r].rpart, reqs[r].rcnt);
 }
 
 // ---- first-fit arena over one device allocation --------------------------------
@@ -287,6 +313,8 @@ struct Slot {
     size_t off = SIZE_MAX, bytes = 0;
     Req d;              // device record (pointers into the arena)
     int iter = 0;
+    bool thr = false;        // a convergence threshold is set
+    bool converged = false;  // its residual fell below it: results final, no more iterations
     int state = kQueued;
     int status = SSLIC_OK;
     cudaEvent_t ev_up = nullptr, ev_done = nullptr;
@@ -310,6 +338,13 @@ static size_t footprint(const Geom& g)
            a256(nch * 4) + a256(K * (g.C + g.n) * 4);
 }
 
+// the residual scratch of a request with a convergence threshold
+static size_t footprint_thr(const Geom& g)
+{
+    const size_t K = (size_t)g.K;
+    return a256(K * 8) + a256(K * 4) + a256(kResidParts * 8) + a256(kResidParts * 4);
+}
+
 // group key: dtype, channels, dims, tile shape (-1 for the per-voxel kernel)
 static int group_key(const Geom& g, int shape) { return ((g.dtype * 512 + g.C) * 8 + g.n) * 8 + (shape + 1); }
 static int key_dtype(int key) { return key / (512 * 64); }
@@ -326,12 +361,13 @@ struct RoundHdr {
     int Rf;                 // requests finishing with it
     int nseed[3];           // joining requests per dtype
     int ngrp[kMaxGroups];   // requests per assignment group
+    int nthr;               // requests with a convergence threshold
 };
 
 // Fixed layout of one round's tables for at most M requests: every table
 // sits at the same device address in every round of the same parity.
 struct TabLayout {
-    size_t hdr, kpre, kpre1, cpre, req, fpre, fin, seed_req[3], seed_pre[3], grp_ta[kMaxGroups],
+    size_t hdr, kpre, kpre1, cpre, req, fpre, fin, thr, res, seed_req[3], seed_pre[3], grp_ta[kMaxGroups],
         grp_pre[kMaxGroups], end;
     void init(int M)
     {
@@ -345,6 +381,8 @@ struct TabLayout {
         req = put((size_t)M * sizeof(Req));
         fpre = put(P);
         fin = put((size_t)M * sizeof(Req));
+        thr = put((size_t)M * sizeof(Req));   // requests with a threshold
+        res = put((size_t)M * sizeof(double));  // their residuals (device -> host)
         for (int t = 0; t < 3; ++t) { seed_req[t] = put((size_t)M * sizeof(Req)); seed_pre[t] = put(P); }
         for (int g = 0; g < kMaxGroups; ++g) { grp_ta[g] = put((size_t)M * sizeof(TileArgs)); grp_pre[g] = put(P); }
         end = (o + 255) / 256 * 256;
@@ -370,7 +408,11 @@ struct sslic_server {
     unsigned char* tab_host[2] = {nullptr, nullptr};
     cudaEvent_t round_ev[2] = {nullptr, nullptr};
     bool round_pending[2] = {false, false};
-    // captured rounds, by (parity, joining dtypes, finishing, groups)
+    // threshold requests of the last round and its parity (their residuals
+    // are read before the next round is formed)
+    std::vector<Slot*> thr_prev;
+    int thr_prev_par = 0;
+    // captured rounds, by (parity, joining dtypes, finishing, thresholds, groups)
     std::map<std::vector<int>, cudaGraphExec_t> graphs;
     int64_t graph_captures = 0, graph_launches = 0;
     // crowded-tile lists, one per group slot in a round
@@ -439,6 +481,12 @@ void place(sslic_server* s, Slot* q)
     d.bin_of = (int*)take(K * 4);
     d.chunk = (unsigned*)take((size_t)q->nchunks * 4);
     d.cen_out = (float*)take(K * (g.C + g.n) * 4);
+    if (q->thr) {
+        d.rk = (double*)take(K * 8);
+        d.ne = (unsigned*)take(K * 4);
+        d.rpart = (double*)take(kResidParts * 8);
+        d.rcnt = (unsigned*)take(kResidParts * 4);
+    }
     a.bin_start = d.bin_start;
     a.bin_items = d.bin_items;
     a.ntx = q->ntx;
@@ -489,7 +537,7 @@ cudaError_t group_launch(sslic_server* s, int key, const TileArgs* ta, const int
 // parity par: seeding of the joining requests (one launch per dtype present),
 // the bin grid, the assignment of each group, the reduction, the export of
 // the finishing requests
-cudaError_t issue_round(sslic_server* s, int par, int seed_mask, bool has_fin, const std::vector<int>& keys)
+cudaError_t issue_round(sslic_server* s, int par, int seed_mask, bool has_fin, bool has_thr, const std::vector<int>& keys)
 {
     const TabLayout& L = s->lay;
     unsigned char* D = s->tab_dev[par];
@@ -520,6 +568,11 @@ cudaError_t issue_round(sslic_server* s, int par, int seed_mask, bool has_fin, c
         if (e != cudaSuccess) return e;
     }
     b_finalize<<<grid, 256, 0, s->cs>>>(dreq, dk, &h->R);
+    if (has_thr) {
+        const Req* dthr = (const Req*)(D + L.thr);
+        b_resid_parts<<<dim3(kResidParts, std::min(s->max_active, 64)), kRedThreads, 0, s->cs>>>(dthr, &h->nthr);
+        b_resid_final<<<1, 64, 0, s->cs>>>(dthr, &h->nthr, (double*)(D + L.res));
+    }
     if (has_fin) b_export<<<grid, 256, 0, s->cs>>>((const Req*)(D + L.fin), (const int64_t*)(D + L.fpre), &h->Rf);
     return cudaGetLastError();
 }
@@ -539,13 +592,33 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
         if ((e = cudaEventSynchronize(s->round_ev[par])) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "round", e);
         s->round_pending[par] = false;
     }
-    std::vector<Slot*> all(act);
+    // residuals of the previous round's threshold requests: that round must
+    // have finished (the next round's form depends on them)
+    if (!s->thr_prev.empty()) {
+        const int pp = s->thr_prev_par;
+        if (s->round_pending[pp]) {
+            if ((e = cudaEventSynchronize(s->round_ev[pp])) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "round", e);
+            s->round_pending[pp] = false;
+        }
+        const double* res = (const double*)(s->tab_host[pp] + s->lay.res);
+        for (size_t i = 0; i < s->thr_prev.size(); ++i) {
+            Slot* q = s->thr_prev[i];
+            if (q->state == kActive && res[i] < q->p.conv_threshold) q->converged = true;
+        }
+        s->thr_prev.clear();
+    }
+    // requests that converged leave without another iteration: their labels
+    // are those of the last assignment and their centres those of the last update
+    std::vector<Slot*> all, fin;
+    for (Slot* q : act) (q->converged ? fin : all).push_back(q);
     all.insert(all.end(), join.begin(), join.end());
     const int R = (int)all.size();
-    std::vector<Slot*> fin;
     for (Slot* q : all)
         if (q->iter + 1 >= q->p.max_iter) fin.push_back(q);
     const int Rf = (int)fin.size();
+    std::vector<Slot*> thr;
+    for (Slot* q : all)
+        if (q->thr && q->iter + 1 < q->p.max_iter) thr.push_back(q);
     std::map<int, std::vector<Slot*>> groups;
     for (Slot* q : all) groups[q->group].push_back(q);
     if ((int)groups.size() > kMaxGroups) return server_fail(s, SSLIC_EUNSUPPORTED, "too many image types");
@@ -570,6 +643,9 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
     int64_t* fpre = (int64_t*)(H + L.fpre);
     fpre[0] = 0;
     for (int i = 0; i < Rf; ++i) { hfin[i] = fin[i]->d; fpre[i + 1] = fpre[i] + fin[i]->g.K * (fin[i]->g.C + fin[i]->g.n); }
+    Req* hthr = (Req*)(H + L.thr);
+    for (size_t i = 0; i < thr.size(); ++i) hthr[i] = thr[i]->d;
+    hdr->nthr = (int)thr.size();
     int seed_mask = 0;
     for (Slot* q : join) {
         const int t = q->g.dtype;
@@ -614,7 +690,7 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
     for (Slot* q : join)
         if ((e = cudaStreamWaitEvent(s->cs, q->ev_up, 0)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "wait", e);
     // the round's kernels: replayed from a captured graph of the same form
-    std::vector<int> sig{par, seed_mask, Rf > 0 ? 1 : 0};
+    std::vector<int> sig{par, seed_mask, Rf > 0 ? 1 : 0, thr.empty() ? 0 : 1};
     sig.insert(sig.end(), keys.begin(), keys.end());
     auto it = s->graphs.find(sig);
     if (it == s->graphs.end()) {
@@ -626,7 +702,7 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
         cudaGraphExec_t ex = nullptr;
         if ((e = cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return server_fail(s, SSLIC_ECUDA, "begin capture", e);
-        const cudaError_t ei = issue_round(s, par, seed_mask, Rf > 0, keys);
+        const cudaError_t ei = issue_round(s, par, seed_mask, Rf > 0, !thr.empty(), keys);
         e = cudaStreamEndCapture(s->cs, &gr);
         if (ei != cudaSuccess || e != cudaSuccess) {
             if (gr) cudaGraphDestroy(gr);
@@ -640,6 +716,13 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
     }
     if ((e = cudaGraphLaunch(it->second, s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "round launch", e);
     s->graph_launches += 1;
+    if (!thr.empty()) {
+        if ((e = cudaMemcpyAsync(H + L.res, s->tab_dev[par] + L.res, thr.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
+            return server_fail(s, SSLIC_ECUDA, "residuals", e);
+        s->thr_prev = thr;
+        s->thr_prev_par = par;
+    }
     for (Slot* q : fin) {
         const Geom& g = q->g;
         if ((e = cudaMemcpyAsync(q->h_lab, q->d.a.labels, (size_t)g.V * 4, cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
@@ -783,7 +866,7 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     Geom g;
     int rc = make_geom(p, &g);
     if (rc) return rc;
-    if (p->enforce_connectivity || p->conv_threshold > 0.0) return SSLIC_EUNSUPPORTED;
+    if (p->enforce_connectivity) return SSLIC_EUNSUPPORTED;
     if (g.K + 1 > (int64_t)kBScanItems * kBScanItems) return SSLIC_EUNSUPPORTED;
     Slot* q = new (std::nothrow) Slot();
     if (!q) return SSLIC_ENOMEM;
@@ -800,7 +883,8 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     }
     q->group = group_key(g, q->shape);
     q->nchunks = (g.K + 1 + kBScanItems - 1) / kBScanItems;
-    q->bytes = footprint(g);
+    q->thr = p->conv_threshold > 0.0;
+    q->bytes = footprint(g) + (q->thr ? footprint_thr(g) : 0);
     q->h_img = image_host;
     q->h_lab = labels_host;
     q->h_cen = centres_host;

@@ -189,6 +189,44 @@ __device__ __forceinline__ void finalize_one(const Geom& g, float* __restrict__ 
         for (int c = 0; c < g.C; ++c) facc[k * g.C + c] = 0.0;
 }
 
+// ---- centre residual (Sec. 3.1: distance between successive centres) ----------
+// The mean over non-empty clusters of the per-cluster terms rk, reduced in a
+// fixed order so every caller gets the same double: kResidParts parts of
+// ceil(K / kResidParts) consecutive clusters, each summed by a block of
+// kRedThreads threads (thread-strided, then a tree), then the parts in order.
+constexpr int kRedThreads = 256;
+constexpr int kResidParts = 256;
+
+// one part; must be called by all kRedThreads threads of the block
+__device__ __forceinline__ void resid_part(const double* __restrict__ rk, const unsigned* __restrict__ ne, int64_t K,
+                                          int part, double* __restrict__ out_d, unsigned* __restrict__ out_c)
+{
+    __shared__ double sd[kRedThreads];
+    __shared__ unsigned sc[kRedThreads];
+    const int64_t per = (K + kResidParts - 1) / kResidParts;
+    const int64_t lo = part * per, hi = imin64(K, lo + per);
+    double d = 0.0;
+    unsigned cnt = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) { d += rk[i]; cnt += ne[i]; }
+    sd[threadIdx.x] = d;
+    sc[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) { sd[threadIdx.x] += sd[threadIdx.x + o]; sc[threadIdx.x] += sc[threadIdx.x + o]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { *out_d = sd[0]; *out_c = sc[0]; }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double resid_combine(const double* __restrict__ part, const unsigned* __restrict__ cpart)
+{
+    double d = 0.0;
+    unsigned long long cnt = 0;
+    for (int i = 0; i < kResidParts; ++i) { d += part[i]; cnt += cpart[i]; }
+    return cnt ? d / (double)cnt : 0.0;
+}
+
 // ---- block-wide exclusive scan of up to 2048 unsigned values -----------------
 // 512 threads x 4 items; in and out may alias; *total (if not null) gets the
 // sum of the n items.  Must be called by all 512 threads of the block.

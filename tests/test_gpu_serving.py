@@ -31,14 +31,16 @@ def _mix(seed=3):
     return reqs
 
 
-def _alone(img, grid, m, iters):
+def _alone(img, grid, m, iters, thr=0.0, info=False):
     import torch
     from paper_1806_08741_gb300 import sslic as S
-    p = S.params_for(img, grid, m=m, max_iter=iters)
+    p = S.params_for(img, grid, m=m, max_iter=iters, conv_threshold=thr)
     with S.Context(p) as ctx:
         lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
         cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
-        ctx.run(torch.from_numpy(img).cuda(), lab, cen)
+        r = ctx.run(torch.from_numpy(img).cuda(), lab, cen)
+        if info:
+            return lab.cpu().numpy(), cen.cpu().numpy(), r
         return lab.cpu().numpy(), cen.cpu().numpy()
 
 
@@ -87,6 +89,47 @@ def test_served_small_requests_equal_oracle():
             srv.wait(t)
             ref = O.slic(O.params_for(img, grid, m=m, max_iter=4), img)
             np.testing.assert_array_equal(lab, ref["labels"])
+
+
+def test_served_requests_with_convergence_thresholds():
+    """Requests with a centre-residual threshold leave after the round in
+    which their residual drops below it -- the iteration at which sslic_run
+    stops -- with the same labels and centres; others in the mix run all
+    their iterations."""
+    from paper_1806_08741_gb300 import sslic as S
+    reqs = _mix(7)[:9]
+    iters = 12
+    # thresholds that stop runs at different iterations (from each run's own residuals)
+    thr = []
+    for i, (img, grid, m) in enumerate(reqs):
+        if i % 3 == 2:
+            thr.append(0.0)
+            continue
+        _, _, r_hi = _alone(img, grid, m, 3, info=True)
+        thr.append(r_hi["residual"] * (1.5 if i % 3 == 0 else 1.01))
+    outs = []
+    with S.Server(1 << 30, max_active=6) as srv:
+        tickets = []
+        for (img, grid, m), t in zip(reqs, thr):
+            p = S.params_for(img, grid, m=m, max_iter=iters, conv_threshold=t)
+            lab = np.empty(img.shape[:-1], np.int32)
+            K = 1
+            for n, g in zip(p.size, p.grid):
+                K *= -(-n // g)
+            cen = np.empty((K, p.channels + p.ndim), np.float32)
+            tickets.append(srv.submit(p, img, lab, cen))
+            outs.append((lab, cen))
+        for t in tickets:
+            srv.wait(t)
+        st = srv.stats()
+    assert st["status"] == 0
+    early = 0
+    for (img, grid, m), t, (lab, cen) in zip(reqs, thr, outs):
+        ref_l, ref_c, info = _alone(img, grid, m, iters, thr=t, info=True)
+        early += info["iterations"] < iters
+        np.testing.assert_array_equal(lab, ref_l)
+        np.testing.assert_array_equal(cen, ref_c)
+    assert early >= 3   # the thresholds did stop runs early
 
 
 def test_server_rejects():

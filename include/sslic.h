@@ -164,6 +164,26 @@ SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const i
 SSLIC_API int sslic_iterate_static(const sslic_params* p, const void* image_dev, const float* centres_in_dev,
                                    int32_t* labels_dev, float* centres_out_dev, void* stream);
 
+/* Colour input: 8-bit sRGB to CIE-Lab float, on the device.  SLIC clusters
+ * colour pixels as [L, a, b, x, y] (Sec. 2, 2.1; its default m = 10 assumes
+ * Lab ranges) and the paper converts its 8-bit RGB volume to CIE-Lab float
+ * before segmenting (Sec. 4.1).  The colour space is sRGB (IEC 61966-2-1
+ * transfer function and matrix) under the D65 white (0.95047, 1, 1.08883),
+ * CIE 1976 L*a*b*: the reading whose extremes over the 8-bit cube match the
+ * L, a, b ranges of Sec. 2.1.  Single precision; within 1e-3 of the exact
+ * value in every component.
+ *   rgb_dev  n interleaved (R, G, B) uint8 triples (device, read only)
+ *   lab_dev  n interleaved (L, a, b) float32 triples (device, written); it
+ *            may not overlap rgb_dev.  The result is an image for the float
+ *            path of sslic_run (C = 3, dtype SSLIC_F32).
+ *   n        voxels (>= 0; 0 is a no-op)
+ *   stream   cudaStream_t, or NULL for the legacy default stream
+ * The fast path wants rgb_dev 4-byte and lab_dev 16-byte aligned; other
+ * pointers take a per-voxel path (same values).  Returns SSLIC_EINVAL for
+ * n < 0, a NULL pointer with n > 0 or overlapping buffers, SSLIC_ECUDA if
+ * the launch fails.  Stream ordered; needs no context. */
+SSLIC_API int sslic_srgb_to_lab(const void* rgb_dev, void* lab_dev, int64_t n, void* stream);
+
 /* Launch configuration of the assignment kernel.  The paper has no
  * counterpart: its multi-threaded filter splits the image into regions per
  * thread (Sec. 3.1), while here a tile shape fixes how voxels map to CUDA

@@ -117,7 +117,8 @@ def lib():
         L.oracle_connectivity.argtypes = [P, dp, ctypes.c_int64, vp, vp, vp]
         L.oracle_slic.argtypes = [P, vp, vp, dp, vp, vp, vp]
         L.oracle_slic_from.argtypes = [P, vp, dp, vp, dp, vp, vp, vp]
-        for f in ("oracle_seed", "oracle_assign", "oracle_update",
+        L.oracle_srgb_to_lab.argtypes = [vp, ctypes.c_int64, dp]
+        for f in ("oracle_seed", "oracle_assign", "oracle_update", "oracle_srgb_to_lab",
                   "oracle_connectivity", "oracle_slic", "oracle_slic_from"):
             getattr(L, f).restype = ctypes.c_int
     return _lib
@@ -171,6 +172,17 @@ def distance(p: Params, feature, pos, centre) -> float:
     x = np.ascontiguousarray(pos, np.int64)
     c = np.ascontiguousarray(centre, np.float64)
     return float(lib().oracle_distance(ctypes.byref(p.to_c()), _ptr(f), _ptr(x), _ptr(c)))
+
+
+def srgb_to_lab(rgb: np.ndarray) -> np.ndarray:
+    """8-bit sRGB [..., 3] -> CIE-Lab float64 [..., 3] (reading R16: sRGB,
+    D65 white, CIE 1976 L*a*b*; the paper's colour space, Sec. 2.1 and 4.1)."""
+    rgb = np.ascontiguousarray(rgb, np.uint8)
+    if rgb.shape[-1] != 3:
+        raise ValueError("srgb_to_lab wants a trailing axis of 3 channels")
+    out = np.empty(rgb.shape, np.float64)
+    _check(lib().oracle_srgb_to_lab(_ptr(rgb), rgb.size // 3, _ptr(out)), "srgb_to_lab")
+    return out
 
 
 def assign(p: Params, image: np.ndarray, centres: np.ndarray) -> np.ndarray:

@@ -42,6 +42,13 @@
  *      with x_d > 0 (x is the raster-first voxel of its component); the
  *      component at the origin gets a new label.
  *  R15 labels are not compacted; centres are not recomputed afterwards.
+ *  R16 colour input: the paper clusters colour in CIE-Lab (Sec. 2, 2.1) and
+ *      converts its 8-bit RGB volume to CIE-Lab float first (Sec. 4.1) but
+ *      names neither the RGB space nor the white point.  Read as sRGB
+ *      (IEC 61966-2-1: its piecewise transfer function and its 4-decimal
+ *      RGB->XYZ matrix), the D65 white (0.95047, 1, 1.08883) and CIE 1976
+ *      L*a*b*: the one combination whose extremes over the 8-bit cube give
+ *      the L, a and b ranges Sec. 2.1 prints, to its three decimals.
  */
 #include "sslic_oracle.h"
 
@@ -574,6 +581,41 @@ int oracle_connectivity(const oracle_params* p, const double* centres, int64_t K
     if (rc != ORACLE_OK) return rc;
     if (!centres || !labels_in || !labels_out || K < 0 || K > 0x7fffffffLL) return ORACLE_EINVAL;
     return connectivity(&g, centres, K, labels_in, labels_out, num_labels);
+}
+
+/* ---- CIE-Lab conversion (R16) -------------------------------------------- */
+
+/* sRGB code value (0..255) -> linear light */
+static double srgb_linear(int code)
+{
+    const double v = code / 255.0;
+    return v <= 0.04045 ? v / 12.92 : pow((v + 0.055) / 1.055, 2.4);
+}
+
+/* CIE 1976 companding: cube root above (6/29)^3, the tangent line below */
+static double lab_f(double t)
+{
+    const double d = 6.0 / 29.0;
+    return t > d * d * d ? cbrt(t) : t / (3.0 * d * d) + 4.0 / 29.0;
+}
+
+int oracle_srgb_to_lab(const uint8_t* rgb, int64_t n, double* lab)
+{
+    static const double M[3][3] = {{0.4124, 0.3576, 0.1805},
+                                   {0.2126, 0.7152, 0.0722},
+                                   {0.0193, 0.1192, 0.9505}};
+    static const double W[3] = {0.95047, 1.0, 1.08883};
+    if (n < 0 || (n > 0 && (!rgb || !lab))) return ORACLE_EINVAL;
+    for (int64_t i = 0; i < n; ++i) {
+        const double r = srgb_linear(rgb[3 * i]), gr = srgb_linear(rgb[3 * i + 1]),
+                     b = srgb_linear(rgb[3 * i + 2]);
+        double f[3];
+        for (int j = 0; j < 3; ++j) f[j] = lab_f((M[j][0] * r + M[j][1] * gr + M[j][2] * b) / W[j]);
+        lab[3 * i] = 116.0 * f[1] - 16.0;
+        lab[3 * i + 1] = 500.0 * (f[0] - f[1]);
+        lab[3 * i + 2] = 200.0 * (f[1] - f[2]);
+    }
+    return ORACLE_OK;
 }
 
 /* ---- whole method -------------------------------------------------------- */

@@ -106,6 +106,10 @@ int oracle_slic_from(const oracle_params* p, const void* image,
                      double* centres_out, int32_t* iters_done,
                      double* residual, int64_t* num_labels);
 
+/* 8-bit sRGB -> CIE-Lab in double precision (reading R16 in the source):
+ * rgb holds n interleaved (R, G, B) triples, lab receives n (L, a, b). */
+int oracle_srgb_to_lab(const uint8_t* rgb, int64_t n, double* lab);
+
 #ifdef __cplusplus
 }
 #endif

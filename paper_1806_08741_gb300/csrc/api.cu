@@ -168,7 +168,7 @@ static void free_all(sslic_ctx* c)
     dfree(w.ctr); dfree(w.acc); dfree(w.facc); dfree(w.resid_k); dfree(w.nonempty_k);
     dfree(w.resid_part); dfree(w.resid_cnt_part); dfree(w.resid_out);
     dfree(w.bin_count); dfree(w.bin_start); dfree(w.bin_cursor); dfree(w.bin_items); dfree(w.bin_of);
-    dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count); dfree(w.hc_err); dfree(w.hc_rechecks);
+    dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count); dfree(w.tile_lists); dfree(w.hc_err); dfree(w.hc_rechecks);
     dfree(w.lid); dfree(w.tile_base); dfree(w.tile_cnt); dfree(w.counters);
     dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
@@ -205,6 +205,9 @@ static int alloc_core(sslic_ctx* c)
     if ((rc = cuda_check(c, cudaMemset(w.hc_rechecks, 0, sizeof(unsigned long long)), "memset"))) return rc;
     if ((rc = dalloc(c, &w.ovf_tiles, (size_t)w.n_assign_tiles, "tiles"))) return rc;
     if ((rc = dalloc(c, &w.ovf_count, 1, "tiles"))) return rc;
+    if (has_tile_kernel(g) &&
+        (rc = dalloc(c, &w.tile_lists, (size_t)assign_num_tiles(g) * tile_list_stride(), "tile lists")))
+        return rc;
     if ((rc = cuda_check(c, cudaMemset(w.acc, 0, K * g.AW * sizeof(unsigned long long)), "memset sums"))) return rc;
     if (w.facc && (rc = cuda_check(c, cudaMemset(w.facc, 0, K * g.C * sizeof(double)), "memset sums"))) return rc;
     if ((rc = cuda_check(c, cudaMemset(w.resid_out, 0, sizeof(double)), "memset"))) return rc;

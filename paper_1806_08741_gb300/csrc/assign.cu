@@ -15,8 +15,8 @@
 // so that integer images give bit-identical labels to a sequential
 // implementation of the same order.
 //
-// The hot case (integer images with 1 or 3 channels, 2-D and 3-D) runs in
-// the tile kernel of assign_tile.cu.  This file holds the per-voxel kernel
+// The hot cases (integer images with 1 or 3 channels and float images with 3,
+// 2-D and 3-D) run in the tile kernel of assign_tile.cu.  This file holds the per-voxel kernel
 // used for every other shape (float images, other channel counts, 1-D) and
 // for tiles that too many centres reach, the reduce step and the centre
 // table conversions.
@@ -116,6 +116,10 @@ int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStr
     if (g.n >= 2 && g.dtype == SSLIC_U16 && g.C == 1) {
         return g.n == 3 ? launch_tile_impl<uint16_t, 1, 3>(c, (const uint16_t*)img, labels, st)
                         : launch_tile_impl<uint16_t, 1, 2>(c, (const uint16_t*)img, labels, st);
+    }
+    if (g.n >= 2 && g.dtype == SSLIC_F32 && g.C == 3) {
+        return g.n == 3 ? launch_tile_impl<float, 3, 3>(c, (const float*)img, labels, st)
+                        : launch_tile_impl<float, 3, 2>(c, (const float*)img, labels, st);
     }
     if (hc_applies(g)) return launch_hc(c, (const float*)img, labels, st);
     switch (g.dtype) {

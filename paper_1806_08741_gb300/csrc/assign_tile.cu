@@ -46,6 +46,8 @@ int default_tile_shape(const Geom& g)
     return reach(g, tile::Shape2L::TX, tile::Shape2L::TY, 1) <= lim ? 0 : 1;
 }
 
+int tile_list_stride() { return tile::kListStride; }
+
 // the most tiles any shape cuts the image into (sizes the crowded-tile list)
 int64_t assign_num_tiles(const Geom& g)
 {

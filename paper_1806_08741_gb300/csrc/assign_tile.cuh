@@ -37,6 +37,8 @@
 #pragma once
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -89,9 +91,11 @@ struct Smem {
     // channel planes: row pitch 4 bytes past the row, plane pitch chosen so a
     // plane advances 4 banks -- the 4x4 (y, z) lanes of a warp box then hit
     // distinct banks
-    static constexpr int RPB = TX * (int)sizeof(T) + 4;
+    // (float planes: pitches kept multiples of 8 bytes for the 64-bit pair loads)
+    static constexpr bool kF = std::is_same<T, float>::value;
+    static constexpr int RPB = TX * (int)sizeof(T) + (kF ? 8 : 4);
     static constexpr int PPB_RAW = TY * RPB;
-    static constexpr int PPB = PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
+    static constexpr int PPB = kF ? (PPB_RAW + 8 + 15) / 16 * 16 : PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
     static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;
     static constexpr int NBOX = (TX / (G::VL * G::WX)) * (TY / G::WY) * (TZ / G::WZ);
     alignas(16) unsigned char cd[(kCap + 1) * CandLayout<C, SH>::CDS];  // [kCap]: a dummy that reaches nothing
@@ -120,6 +124,14 @@ __device__ __forceinline__ unsigned plane_pair(const Smem<T, C, SH>& s, int c, i
     const unsigned char* p = s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * (int)sizeof(T);
     if constexpr (sizeof(T) == 1) return *reinterpret_cast<const uint16_t*>(p);
     else return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// two consecutive voxels of a float plane as one packed pair
+template <typename T, int C, typename SH>
+__device__ __forceinline__ uint64_t plane_pair_f(const Smem<T, C, SH>& s, int c, int xl, int yl, int zl)
+{
+    using S = Smem<T, C, SH>;
+    return *reinterpret_cast<const uint64_t*>(s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * 4);
 }
 
 // typed views of one candidate record
@@ -157,16 +169,130 @@ struct PackedSums {
     static constexpr int kCnt = 17, kZ = 16;
 };
 
+// Float images keep their feature words as FP32 (run partials in FP32, added
+// into the tile's FP32 words; the tile's sums then go to FP64 global sums).
+template <typename T>
+using FeatAcc = typename std::conditional<std::is_same<T, float>::value, float, unsigned>::type;
+
 template <typename T, int C>
-__device__ __forceinline__ void flush_run(unsigned* pk, int cur, const unsigned* fs, unsigned xs, unsigned cnt, int yl,
+__device__ __forceinline__ void flush_run(unsigned* pk, int cur, const FeatAcc<T>* fs, unsigned xs, unsigned cnt, int yl,
                                           int zl)
 {
     if (cur == kNoSlot || cnt == 0) return;
     unsigned* w = pk + cur * (C + 2);
 #pragma unroll
-    for (int c = 0; c < C; ++c) atomicAdd(&w[c], fs[c]);
+    for (int c = 0; c < C; ++c) {
+        if constexpr (std::is_same<T, float>::value) atomicAdd(reinterpret_cast<float*>(&w[c]), fs[c]);
+        else atomicAdd(&w[c], fs[c]);
+    }
     atomicAdd(&w[C], xs | (cnt << PackedSums::kCnt));
     atomicAdd(&w[C + 1], (cnt * (unsigned)yl) | ((cnt * (unsigned)zl) << PackedSums::kZ));
+}
+
+// ---- per-tile candidate lists ------------------------------------------------
+// Step 2 done ahead of the tile kernel, one warp per tile, for a whole image:
+// the warp gathers the centres of the bins that can reach the tile, keeps
+// those whose window meets it and writes them sorted by index into the
+// tile's record: [0] = their count, [1 .. count] = the indices, the rest -1.
+// A tile with more than kStage gathered or kCap kept centres gets count -1
+// and goes to the crowded-tile list here.  The tile kernel then starts from
+// one coalesced load of the record instead of the chain of dependent loads,
+// shared atomics and barriers of the in-kernel gather (kept for the batched
+// queue, which has no lists).
+constexpr int kListStride = kCap + 1;
+constexpr int kListWarps = 8;
+
+template <int NDIM>
+__global__ void __launch_bounds__(kListWarps * 32)
+tile_lists_kernel(Geom g, const float* __restrict__ ctr, const unsigned* __restrict__ bin_start,
+                  const int* __restrict__ bin_items, int* __restrict__ lists, int64_t ntiles, int ntx, int nty,
+                  int TX, int TY, int TZ, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+{
+    __shared__ int stage_all[kListWarps][kStage];
+    __shared__ int kept_all[kListWarps][kCap];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    int* const stage = stage_all[wp];
+    int* const kept = kept_all[wp];
+    const int Tn[3] = {TX, TY, TZ};
+    for (int64_t tile = (int64_t)blockIdx.x * kListWarps + wp; tile < ntiles;
+         tile += (int64_t)gridDim.x * kListWarps) {
+        const int T0[3] = {(int)(tile % ntx) * TX, (int)((tile / ntx) % nty) * TY,
+                           (int)(tile / ((int64_t)ntx * nty)) * TZ};
+        int E[3], blo[3], nbd[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            E[d] = min(Tn[d], (int)g.N[d] - T0[d]);
+            blo[d] = max(0, T0[d] / g.S[d] - 1);
+            nbd[d] = min((int)g.nb[d] - 1, (T0[d] + E[d] - 1) / g.S[d] + 1) - blo[d] + 1;
+        }
+        // gather: bins 32 at a time, items placed by a prefix sum of the counts
+        const int nbins = nbd[0] * nbd[1] * nbd[2];
+        int total = 0;
+        for (int b0 = 0; b0 < nbins; b0 += 32) {
+            const int b = b0 + lane;
+            unsigned first = 0, cnt = 0;
+            if (b < nbins) {
+                const int bx = blo[0] + b % nbd[0], by = blo[1] + (b / nbd[0]) % nbd[1],
+                          bz = blo[2] + b / (nbd[0] * nbd[1]);
+                const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
+                first = bin_start[bin];
+                cnt = bin_start[bin + 1] - first;
+            }
+            unsigned inc = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            const unsigned base = (unsigned)total + inc - cnt;
+            for (unsigned j = 0; j < cnt; ++j)
+                if (base + j < (unsigned)kStage) stage[base + j] = bin_items[first + j];
+            total += (int)__shfl_sync(0xffffffffu, inc, 31);
+        }
+        __syncwarp();
+        // filter: windows that meet the tile, compacted by ballot
+        int nc = 0;
+        if (total <= kStage) {
+            for (int i0 = 0; i0 < total; i0 += 32) {
+                const int i = i0 + lane;
+                bool hit = false;
+                int k = 0;
+                if (i < total) {
+                    k = stage[i];
+                    const float* pos = ctr + (int64_t)k * g.CW + g.C;
+                    hit = true;
+#pragma unroll
+                    for (int d = 0; d < NDIM; ++d) {
+                        const int lo = (int)ceilf(pos[d]) - g.S[d];
+                        hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                const int at = nc + __popc(m & ((1u << lane) - 1u));
+                if (hit && at < kCap) kept[at] = k;
+                nc += __popc(m);
+            }
+        }
+        __syncwarp();
+        int* rec = lists + tile * kListStride;
+        if (total > kStage || nc > kCap) {
+            for (int i = lane; i < kListStride; i += 32) rec[i] = -1;
+            if (lane == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = tile;
+        } else {
+            // rank sort (the indices are distinct: a centre sits in one bin)
+            for (int i = lane; i < kCap; i += 32) {
+                int v = -1, r = i;
+                if (i < nc) {
+                    v = kept[i];
+                    r = 0;
+                    for (int j = 0; j < nc; ++j) r += (kept[j] < v);
+                }
+                rec[1 + r] = v;
+            }
+            if (lane == 0) rec[0] = nc;
+        }
+        __syncwarp();
+    }
 }
 
 // One tile of one image (request req): everything of steps 1-5 above.  A
@@ -208,6 +334,12 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     const int Z0 = (tile / (ntx * nty)) * TZ;
     const int N0 = (int)g.N[0], N1 = (int)g.N[1], N2 = (int)g.N[2];
     const int ex = min(TX, N0 - X0), ey = min(TY, N1 - Y0), ez = min(TZ, N2 - Z0);
+
+    // lists mode: this thread's entry of the tile's candidate record, loaded
+    // before the staging so its latency overlaps it
+    const bool lists = a.lists != nullptr;
+    int lk = -1;
+    if (lists && tid < kListStride) lk = __ldg(a.lists + (int64_t)tile * kListStride + tid);
 
     if (tid == 0) { s.nstage = 0; s.ncand = 0; }
     for (int i = tid; i < S::kCopies * S::kPkStride; i += kThreads) s.pk[i] = 0u;
@@ -269,49 +401,73 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
         bhi[d] = min((int)g.nb[d] - 1, (T0[d] + E[d] - 1) / g.S[d] + 1);
     }
     const int nbx = bhi[0] - blo[0] + 1, nby = bhi[1] - blo[1] + 1, nbz = bhi[2] - blo[2] + 1;
-    __syncthreads();
-    for (int b = tid; b < nbx * nby * nbz; b += kThreads) {
-        const int bx = blo[0] + b % nbx, by = blo[1] + (b / nbx) % nby, bz = blo[2] + b / (nbx * nby);
-        const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
-        const unsigned st = bin_start[bin], en = bin_start[bin + 1];
-        for (unsigned i = st; i < en; ++i) {
-            const int pos = atomicAdd(&s.nstage, 1);
-            if (pos < kStage) s.stage[pos] = bin_items[i];
-        }
-    }
-    __syncthreads();
-    const int nst = s.nstage;
-    for (int i = tid; i < min(nst, kStage); i += kThreads) {
-        const int k = s.stage[i];
-        const float* p = ctr + (int64_t)k * g.CW + C;
-        bool hit = true;
+    // lists mode: the rows of the record's centres, fetched before the barrier
+    float rowv[C + NDIM];
+    if (lists) {
+        if (tid >= 1 && tid < kListStride && lk >= 0 && lk < g.K) {
+            const float* row = ctr + (int64_t)lk * g.CW;
 #pragma unroll
-        for (int d = 0; d < NDIM; ++d) {
-            const int lo = (int)ceilf(p[d]) - g.S[d];
-            hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
+            for (int j = 0; j < C + NDIM; ++j) rowv[j] = row[j];
         }
-        if (hit) {
-            const int pos = atomicAdd(&s.ncand, 1);
-            if (pos < kCap) s.tmp[pos] = k;
-        }
+        if (tid == 0) s.ncand = lk;
     }
     __syncthreads();
-    const int nc = s.ncand;
-    if (nst > kStage || nc > kCap) {
-        if (tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = (req << 40) | (int64_t)tile;
-        return;  // block-uniform: the per-voxel kernel takes this tile
-    }
-    for (int i = tid; i < nc; i += kThreads) {
-        const int k = s.tmp[i];
-        int r = 0;
-        for (int j = 0; j < nc; ++j) r += (s.tmp[j] < k);
-        s.cand[r] = k;
-        const float* row = ctr + (int64_t)k * g.CW;
+    int nc;
+    if (lists) {
+        nc = s.ncand;
+        if (nc < 0) return;  // block-uniform: the list kernel sent the tile to the per-voxel kernel
+        if (tid >= 1 && tid <= nc) {
+            const int r = tid - 1;
+            s.cand[r] = lk;
 #pragma unroll
-        for (int c = 0; c < C; ++c) cand_at<C, SH, float2>(s.cd, r, CL::kOffFe)[c] = make_float2(row[c], row[c]);
-        s.cpos[r][0] = row[C];
-        s.cpos[r][1] = row[C + 1];
-        s.cpos[r][2] = row[C + 2];
+            for (int c = 0; c < C; ++c) cand_at<C, SH, float2>(s.cd, r, CL::kOffFe)[c] = make_float2(rowv[c], rowv[c]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) s.cpos[r][d] = d < NDIM ? rowv[C + d] : 0.0f;
+        }
+    } else {
+        for (int b = tid; b < nbx * nby * nbz; b += kThreads) {
+            const int bx = blo[0] + b % nbx, by = blo[1] + (b / nbx) % nby, bz = blo[2] + b / (nbx * nby);
+            const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
+            const unsigned st = bin_start[bin], en = bin_start[bin + 1];
+            for (unsigned i = st; i < en; ++i) {
+                const int pos = atomicAdd(&s.nstage, 1);
+                if (pos < kStage) s.stage[pos] = bin_items[i];
+            }
+        }
+        __syncthreads();
+        const int nst = s.nstage;
+        for (int i = tid; i < min(nst, kStage); i += kThreads) {
+            const int k = s.stage[i];
+            const float* p = ctr + (int64_t)k * g.CW + C;
+            bool hit = true;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) {
+                const int lo = (int)ceilf(p[d]) - g.S[d];
+                hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
+            }
+            if (hit) {
+                const int pos = atomicAdd(&s.ncand, 1);
+                if (pos < kCap) s.tmp[pos] = k;
+            }
+        }
+        __syncthreads();
+        nc = s.ncand;
+        if (nst > kStage || nc > kCap) {
+            if (tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = (req << 40) | (int64_t)tile;
+            return;  // block-uniform: the per-voxel kernel takes this tile
+        }
+        for (int i = tid; i < nc; i += kThreads) {
+            const int k = s.tmp[i];
+            int r = 0;
+            for (int j = 0; j < nc; ++j) r += (s.tmp[j] < k);
+            s.cand[r] = k;
+            const float* row = ctr + (int64_t)k * g.CW;
+    #pragma unroll
+            for (int c = 0; c < C; ++c) cand_at<C, SH, float2>(s.cd, r, CL::kOffFe)[c] = make_float2(row[c], row[c]);
+            s.cpos[r][0] = row[C];
+            s.cpos[r][1] = row[C + 1];
+            s.cpos[r][2] = row[C + 2];
+        }
     }
     __syncthreads();
 
@@ -395,9 +551,13 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
         for (int c = 0; c < C; ++c)
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                unsigned lo, hi;
-                split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), lo, hi);
-                Fp[c][q] = pk2((float)lo, (float)hi);
+                if constexpr (S::kF) {
+                    Fp[c][q] = plane_pair_f(s, c, xl + 2 * q, yl, zl);
+                } else {
+                    unsigned lo, hi;
+                    split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), lo, hi);
+                    Fp[c][q] = pk2((float)lo, (float)hi);
+                }
             }
         float bd[VL];
         int bs[VL];
@@ -495,7 +655,8 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
             sw[jj] = sp[jj];
         }
         int cur = kNoSlot, curlab = -1;
-        unsigned fs[C], xs = 0, cnt = 0;
+        FeatAcc<T> fs[C];
+        unsigned xs = 0, cnt = 0;
 #pragma unroll
         for (int c = 0; c < C; ++c) fs[c] = 0;
         // start a new run at slot sl (flushing the previous one)
@@ -541,7 +702,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
 #pragma unroll
                             for (int c = 0; c < C; ++c) {
                                 if constexpr (sizeof(T) == 1) fs[c] += (pw[c] >> (8 * b)) & 0xffu;
-                                else fs[c] += (unsigned)*reinterpret_cast<const T*>(
+                                else fs[c] += (FeatAcc<T>)*reinterpret_cast<const T*>(
                                     prow + c * S::CPB + (xq + b) * (int)sizeof(T));
                             }
                             xs += (unsigned)(xq + b);
@@ -565,7 +726,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
                 if (sl != kNoSlot) {
 #pragma unroll
                     for (int c = 0; c < C; ++c)
-                        fs[c] += (unsigned)*reinterpret_cast<const T*>(prow + c * S::CPB + (xs0 + b) * (int)sizeof(T));
+                        fs[c] += (FeatAcc<T>)*reinterpret_cast<const T*>(prow + c * S::CPB + (xs0 + b) * (int)sizeof(T));
                     xs += (unsigned)(xs0 + b);
                     cnt += 1u;
                 }
@@ -580,18 +741,28 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     // the copies are summed field by field (each field's total fits its width)
     for (int i = tid; i < nc * F; i += kThreads) {
         const int sl = i / F, f = i % F;
-        unsigned wx = 0, wyz = 0, wf = 0;
+        unsigned wx = 0, wyz = 0;
+        FeatAcc<T> wf = 0;
 #pragma unroll
         for (int k = 0; k < S::kCopies; ++k) {
             const unsigned* w = s.pk + k * S::kPkStride + sl * (C + 2);
             wx += w[C];
             if (f == C + 1 || f == C + 2) wyz += w[C + 1];
-            if (f < C) wf += w[f];
+            if (f < C) {
+                if constexpr (S::kF) wf += __uint_as_float(w[f]);
+                else wf += w[f];
+            }
         }
         const unsigned long long cnt = wx >> PackedSums::kCnt;
         if (!cnt) continue;
+        if constexpr (S::kF) {
+            if (f < C) {
+                atomicAdd(&a.facc[(int64_t)s.cand[sl] * C + f], (double)wf);
+                continue;
+            }
+        }
         unsigned long long v;
-        if (f < C) v = wf;
+        if (f < C) v = (unsigned long long)wf;
         else if (f == C) v = (wx & ((1u << PackedSums::kCnt) - 1)) + cnt * (unsigned long long)X0;
         else if (f == C + 1) v = (wyz & ((1u << PackedSums::kZ) - 1)) + cnt * (unsigned long long)Y0;
         else if (f == C + 2) v = (wyz >> PackedSums::kZ) + cnt * (unsigned long long)Z0;
@@ -770,6 +941,17 @@ inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaSt
                         "smem attribute");
     if (rc) return rc;
     if ((rc = cuda_check(c, cudaMemsetAsync(w.ovf_count, 0, sizeof(unsigned), st), "memset ovf"))) return rc;
+    if (w.tile_lists) {
+        // step 2 for every tile at once (timed with the bins it reads)
+        const int64_t lgrid = imin64((ntiles + tile::kListWarps - 1) / tile::kListWarps, (int64_t)c->sms * 32);
+        const int pr = prof_begin(c, SSLIC_PHASE_BINS, st);
+        tile::tile_lists_kernel<SH::NDIM><<<(unsigned)lgrid, tile::kListWarps * 32, 0, st>>>(
+            g, w.ctr, w.bin_start, w.bin_items, w.tile_lists, ntiles, ntx, nty, SH::TX, SH::TY, SH::TZ,
+            w.ovf_tiles, w.ovf_count);
+        count_launch(c);
+        prof_end(c, pr, st);
+        if ((rc = cuda_check(c, cudaGetLastError(), "tile_lists_kernel"))) return rc;
+    }
     TileArgs a;
     a.g = g;
     a.img = img;
@@ -784,30 +966,36 @@ inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaSt
     a.tx = SH::TX;
     a.ty = SH::TY;
     a.tz = SH::TZ;
+    a.lists = w.tile_lists;
     alignas(64) CUtensorMap map;
-    const bool tma = want_tma && image_tma_ok(g, img, (int)sizeof(T)) &&
+    const bool tma = sizeof(T) < 4 && want_tma && image_tma_ok(g, img, (int)sizeof(T)) &&
                      encode_image_map(&map, g, img, (int)sizeof(T), SH::TX, SH::TY, SH::TZ) == SSLIC_OK;
-    if (tma) {
-        // persistent: as many CTAs as fit at once, each walking its share of the tiles
-        const size_t smem_t = sizeof(tile::SmemTma<T, C, SH>);
-        if ((rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_tma_kernel<T, C, SH>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t),
-                             "smem attribute")))
-            return rc;
-        int per_sm = 0;
-        if ((rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                    &per_sm, tile::assign_tile_tma_kernel<T, C, SH>, tile::kThreads, smem_t),
-                             "occupancy")))
-            return rc;
-        const int64_t grid = imin64(ntiles, (int64_t)c->sms * (per_sm > 0 ? per_sm : 1));
-        const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
-        tile::assign_tile_tma_kernel<T, C, SH><<<(unsigned)grid, tile::kThreads, smem_t, st>>>(
-            a, map, ntiles, w.ovf_tiles, w.ovf_count, w.hc_err);
-        count_launch(c);
-        prof_end(c, pr, st);
-        c->status_pending = 1;
-        if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_tma_kernel"))) return rc;
-    } else {
+    bool launched = false;
+    if constexpr (sizeof(T) < 4) {  // float planes: a TMA-staged index runs its base shape
+        if (tma) {
+            // persistent: as many CTAs as fit at once, each walking its share of the tiles
+            const size_t smem_t = sizeof(tile::SmemTma<T, C, SH>);
+            if ((rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_tma_kernel<T, C, SH>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_t),
+                                 "smem attribute")))
+                return rc;
+            int per_sm = 0;
+            if ((rc = cuda_check(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                        &per_sm, tile::assign_tile_tma_kernel<T, C, SH>, tile::kThreads, smem_t),
+                                 "occupancy")))
+                return rc;
+            const int64_t grid = imin64(ntiles, (int64_t)c->sms * (per_sm > 0 ? per_sm : 1));
+            const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
+            tile::assign_tile_tma_kernel<T, C, SH><<<(unsigned)grid, tile::kThreads, smem_t, st>>>(
+                a, map, ntiles, w.ovf_tiles, w.ovf_count, w.hc_err);
+            count_launch(c);
+            prof_end(c, pr, st);
+            c->status_pending = 1;
+            if ((rc = cuda_check(c, cudaGetLastError(), "assign_tile_tma_kernel"))) return rc;
+            launched = true;
+        }
+    }
+    if (!launched) {
         const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN, st);
         tile::assign_tile_kernel<T, C, SH><<<(unsigned)ntiles, tile::kThreads, smem, st>>>(a, w.ovf_tiles, w.ovf_count);
         count_launch(c);

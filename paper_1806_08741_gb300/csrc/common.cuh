@@ -106,6 +106,7 @@ struct TileArgs {
     double* facc;
     int ntx, nty;     // tile grid of the tile shape in use
     int tx, ty, tz;   // that shape's tile dimensions
+    const int* lists; // per-tile candidate records of that shape, or nullptr (gathered in the kernel)
 };
 
 // ---- context ---------------------------------------------------------------
@@ -134,6 +135,7 @@ struct Workspace {
     int64_t n_assign_tiles = 0;
     int64_t* ovf_tiles = nullptr;
     unsigned* ovf_count = nullptr;
+    int* tile_lists = nullptr;          // n_assign_tiles records of tile_list_stride() ints (tile kernel images)
     // connectivity
     uint16_t* lid = nullptr;            // V
     int64_t n_ccl_tiles = 0;
@@ -201,6 +203,8 @@ int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t 
 size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
+int tile_list_stride();  // ints per per-tile candidate record
+bool has_tile_kernel(const Geom& g);  // integer images with a tile kernel (2-D, 3-D)
 // TMA tensor map of an image as bytes [N_2][N_1][N_0 * C * esz] (tma.cu);
 // map points at 128 bytes, 64-byte aligned
 bool image_tma_ok(const Geom& g, const void* img, int esz);

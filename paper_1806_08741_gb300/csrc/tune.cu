@@ -23,11 +23,13 @@ std::map<TuneKey, int> g_tuned;
 
 TuneKey key_of(const Geom& g) { return TuneKey(g.dtype, g.C, g.n, g.S[0], g.S[1], g.S[2]); }
 
+}  // namespace
+
 bool has_tile_kernel(const Geom& g)
 {
-    return g.n >= 2 && ((g.dtype == SSLIC_U8 && (g.C == 1 || g.C == 3)) || (g.dtype == SSLIC_U16 && g.C == 1));
+    return g.n >= 2 && ((g.dtype == SSLIC_U8 && (g.C == 1 || g.C == 3)) || (g.dtype == SSLIC_U16 && g.C == 1) ||
+                        (g.dtype == SSLIC_F32 && g.C == 3));
 }
-}  // namespace
 
 int tuned_tile_shape(const Geom& g)
 {

@@ -27,7 +27,7 @@ EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_
            "sslic_server_submit", "sslic_server_wait", "sslic_server_stats_get",
            "sslic_server_destroy", "sslic_num_tile_shapes", "sslic_tile_shape_info",
            "sslic_set_tile_shape", "sslic_get_tile_shape", "sslic_autotune", "sslic_tune_forget",
-           "sslic_tune_record", "sslic_tune_lookup", "sslic_precision_probe",
+           "sslic_tune_record", "sslic_tune_lookup", "sslic_precision_probe", "sslic_srgb_to_lab",
            "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
            "sslic_strerror", "sslic_last_error")
 PHASES = ("seed", "bins", "assign", "assign_voxel", "finalize", "connectivity")
@@ -141,6 +141,8 @@ def load(path: str = LIB_PATH):
               "sslic_tune_lookup"):
         getattr(L, f).restype = ctypes.c_int
     L.sslic_iterate_static.argtypes = [P, vp, vp, vp, vp, vp]
+    L.sslic_srgb_to_lab.argtypes = [vp, vp, ctypes.c_int64, vp]
+    L.sslic_srgb_to_lab.restype = ctypes.c_int
     L.sslic_iterate_static.restype = ctypes.c_int
     L.sslic_profile_enable.argtypes = [C, ctypes.c_int32]
     L.sslic_profile_read.argtypes = [C, ctypes.POINTER(_Profile)]
@@ -484,6 +486,23 @@ def iterate_static(params: Params, image, centres_in, labels, centres_out, strea
                                 _ptr(labels), _ptr(centres_out), _stream(stream))
     if rc != SSLIC_OK:
         raise SSLICError(rc, "sslic_iterate_static")
+
+
+def srgb_to_lab(rgb, out=None, stream=None):
+    """8-bit sRGB [..., 3] device tensor -> CIE-Lab float32 [..., 3] through
+    sslic_srgb_to_lab (sRGB, D65 white, CIE 1976 L*a*b*; the colour space the
+    paper clusters in, Sec. 2.1, 4.1).  ``out`` (optional) receives it."""
+    import torch
+    if rgb.dtype != torch.uint8 or rgb.shape[-1] != 3 or not rgb.is_cuda or not rgb.is_contiguous():
+        raise ValueError("rgb: expected a contiguous uint8 device tensor [..., 3]")
+    if out is None:
+        out = torch.empty(rgb.shape, dtype=torch.float32, device=rgb.device)
+    elif out.dtype != torch.float32 or out.shape != rgb.shape or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out: expected a contiguous float32 device tensor shaped like rgb")
+    rc = load().sslic_srgb_to_lab(_ptr(rgb), _ptr(out), rgb.numel() // 3, _stream(stream))
+    if rc != SSLIC_OK:
+        raise SSLICError(rc, "sslic_srgb_to_lab")
+    return out
 
 
 class Server:

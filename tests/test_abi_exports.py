@@ -124,5 +124,21 @@ def test_tune_table_host_only(lib):
     with pytest.raises(S.SSLICError) as e:
         S.tune_record(S.Params(size=(64, 64), grid=(8, 8), channels=4, dtype=S.F32), 0)
     assert e.value.code == -6
+    lab = S.Params(size=(64, 64), grid=(8, 8), channels=3, dtype=S.F32)   # 3-channel float has tiles
+    S.tune_record(lab, 2)
+    assert S.tune_lookup(lab) == 2
     S.tune_forget()
     assert S.tune_lookup(p) == -1
+
+
+def test_srgb_to_lab_rejects_bad_arguments_without_touching_the_gpu(lib):
+    # argument checks come before any CUDA call
+    f = lib.sslic_srgb_to_lab
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    assert f(None, None, 0, None) == 0                       # nothing to do
+    assert f(None, None, -1, None) == -1                     # negative count
+    assert f(None, 0x20000, 4, None) == -1                   # NULL input
+    assert f(0x10000, None, 4, None) == -1                   # NULL output
+    assert f(0x10000, 0x10000 + 8, 4, None) == -1            # output starts inside the input
+    assert f(0x10000 + 40, 0x10000, 4, None) == -1           # input starts inside the output
+    assert f(0x10000, 0x10000, 1 << 62, None) == -1          # byte count overflows

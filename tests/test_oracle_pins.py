@@ -527,3 +527,59 @@ def test_connectivity_invariants(seed):
         msk = incomp == c
         vals = np.unique(out[msk])
         assert len(vals) == 1       # components are relabelled as a whole
+
+
+# --------------------------------------------------------------------------
+# CIE-Lab conversion (reading R16)
+# --------------------------------------------------------------------------
+
+def _cube():
+    v = np.arange(256)
+    return np.stack(np.meshgrid(v, v, v, indexing="ij"), -1).reshape(-1, 3).astype(np.uint8)
+
+
+def test_lab_ranges_are_the_papers():
+    # The extremes over every 8-bit colour are the ranges Sec. 2.1 prints (to
+    # its three decimals: the last digit may be cut rather than rounded).
+    ref = _load("lab_ranges_paper.json")
+    lab = O.srgb_to_lab(_cube())
+    lo, hi = lab.min(0), lab.max(0)
+    for j, ch in enumerate("Lab"):
+        assert abs(lo[j] - ref[ch][0]) <= 1e-3, (ch, lo[j])
+        assert abs(hi[j] - ref[ch][1]) <= 1e-3, (ch, hi[j])
+    # black and white are the ends of the L axis exactly (the Y row of the
+    # sRGB matrix sums to 1)
+    bw = O.srgb_to_lab(np.array([[0, 0, 0], [255, 255, 255]], np.uint8))
+    assert bw[0].tolist() == [0.0, 0.0, 0.0]
+    assert abs(bw[1, 0] - 100.0) < 1e-12
+
+
+def test_lab_round_trip_through_the_textbook_inverse():
+    # Invert Lab -> XYZ -> linear RGB -> sRGB code with the inverse
+    # definitions (written here independently of the oracle's forward code);
+    # every code must come back to within rounding.
+    rng = np.random.default_rng(7)
+    rgb = rng.integers(0, 256, size=(20000, 3), dtype=np.uint8)
+    lab = O.srgb_to_lab(rgb)
+    d = 6.0 / 29.0
+    fy = (lab[:, 0] + 16.0) / 116.0
+    fx = fy + lab[:, 1] / 500.0
+    fz = fy - lab[:, 2] / 200.0
+
+    def finv(f):
+        return np.where(f > d, f ** 3, 3.0 * d * d * (f - 4.0 / 29.0))
+
+    xyz = np.stack([finv(fx) * 0.95047, finv(fy), finv(fz) * 1.08883], -1)
+    m = np.array([[0.4124, 0.3576, 0.1805], [0.2126, 0.7152, 0.0722], [0.0193, 0.1192, 0.9505]])
+    lin = np.linalg.solve(m, xyz.T).T
+    enc = np.where(lin <= 0.0031308, 12.92 * lin, 1.055 * np.abs(lin) ** (1 / 2.4) - 0.055)
+    np.testing.assert_allclose(enc * 255.0, rgb.astype(np.float64), atol=1e-6)
+
+
+def test_lab_grey_axis():
+    # Greys lie on the L axis (a, b within the 4e-5 gap between the D65 white
+    # and the matrix's row sums) and L rises with the code value.
+    v = np.arange(256, dtype=np.uint8)
+    lab = O.srgb_to_lab(np.stack([v, v, v], -1))
+    assert np.all(np.diff(lab[:, 0]) > 0)
+    assert np.abs(lab[:, 1:]).max() < 0.02

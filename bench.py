@@ -328,6 +328,10 @@ def run_ours(args, w):
                "ms_per_step": dt * 1e3, "labels_equal_device_run": same}
         del h_img, h_lab, h_cen
 
+    lab = None
+    if rank == 0 and world == 1 and not args.no_lab and spec.dtype == "u8" and spec.channels == 3:
+        lab = lab_bench(w, img, labels, steps=max(3, min(args.steps, 5)), warmup=1)
+
     precision = None
     if rank == 0 and world == 1 and not args.no_precision:
         precision = precision_bench(steps=max(3, args.steps))
@@ -353,7 +357,7 @@ def run_ours(args, w):
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
             "tile_shape": tune, "assign_update_loop": loop,
             "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
-            "precision": precision,
+            "precision": precision, "lab": lab,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -361,6 +365,66 @@ def run_ours(args, w):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# colour input: the same volume converted to CIE-Lab float (the paper's data)
+# ---------------------------------------------------------------------------
+def lab_bench(w, rgb, labels, steps=3, warmup=1):
+    """The RGB workload converted on the device to CIE-Lab float (12 B per
+    voxel) and segmented with the same parameters: the conversion's achieved
+    bandwidth (3 B read + 12 B written per voxel), whole runs (iterations +
+    connectivity) on the float image with the autotuned tile shape, and the
+    assignment kernel's bandwidth at 12 + 4 B per voxel."""
+    import torch
+
+    from paper_1806_08741_gb300 import sslic as S
+
+    spec = w.image
+    V = spec.voxels
+    stream = torch.cuda.current_stream()
+    peak, peak_src = _peaks()
+    img = torch.empty(spec.shape, dtype=torch.float32, device=rgb.device)
+    S.srgb_to_lab(rgb, img, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    conv = []
+    for _ in range(3):
+        e0.record(stream)
+        S.srgb_to_lab(rgb, img, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        conv.append(e0.elapsed_time(e1))
+    c_ms = sorted(conv)[1]
+    out = {"workload": "lab" + w.name[3:], "convert": {
+        "ms": c_ms, "GBs": 15 * V / (c_ms / 1e3) / 1e9, "frac_hbm": 15 * V / (c_ms / 1e3) / 1e9 / peak,
+        "bytes_per_voxel": 15, "peak_source": f"of {peak_src}"}}
+    p = S.params_for(img, w.grid, m=w.m, max_iter=w.max_iter, perturb=w.perturb,
+                     enforce_connectivity=w.connectivity)
+    with S.Context(p) as ctx:
+        cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device=rgb.device)
+        t = ctx.autotune(img, labels, reps=2, stream=stream)
+        for _ in range(warmup):
+            ctx.run(img, labels, cen, stream=stream)
+        torch.cuda.synchronize()
+        ctx.profile_enable(True)
+        e0.record(stream)
+        for _ in range(steps):
+            info = ctx.run(img, labels, cen, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ms = e0.elapsed_time(e1) / steps
+        a_ms, a_calls = prof["assign"]
+        achieved = V * 16 / (a_ms / a_calls / 1e3) / 1e9 if a_calls else None
+        out.update({"value": V * info["iterations"] / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_run": ms,
+                    "tile_shape": t["best"], "ms_per_shape": t["ms"],
+                    "assign_ms_per_iter": a_ms / a_calls if a_calls else None, "assign_gbs": achieved,
+                    "assign_frac_hbm": achieved / peak if achieved else None, "bytes_per_voxel": 16,
+                    "connectivity_ms": prof["connectivity"][0] / steps, "num_labels": info["num_labels"]})
+    del img
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -560,6 +624,7 @@ def main():
     ap.add_argument("--tile-shape", type=int, default=None, help="fix the tile shape (no autotuning)")
     ap.add_argument("--no-precision", action="store_true", help="skip the 64-band float workload")
     ap.add_argument("--precision-only", action="store_true", help="only the 64-band float workload")
+    ap.add_argument("--no-lab", action="store_true", help="skip the CIE-Lab float form of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
     ap.add_argument("--reference-edge", type=int, default=128,

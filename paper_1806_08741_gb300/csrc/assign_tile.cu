@@ -1,8 +1,8 @@
 // assign_tile.cu -- the tile shapes of the assignment kernel (host side).
 //
 // Shape indices: 3-D 0 = 32x16x8 / 2 voxels per lane, 1 = 16x8x8 / 2,
-// 2 = 32x16x8 / 4, 3 = 16x8x8 / 4; 2-D 0 = 64x32 / 2, 1 = 32x16 / 2,
-// 2 = 64x32 / 4.  Each base shape comes twice: index b stages the tile with
+// 2 = 32x16x8 / 4, 3 = 16x8x8 / 4, 4 = 32x8x8 / 2, 5 = 32x8x8 / 4; 2-D
+// 0 = 64x32 / 2, 1 = 32x16 / 2, 2 = 64x32 / 4.  Each base shape comes twice: index b stages the tile with
 // plain loads, index b + (number of base shapes) with a TMA copy of the next
 // tile in flight while the current one is computed (used where the image
 // rows are 16-byte multiples; otherwise it is the plain form).  The default
@@ -12,7 +12,7 @@
 
 namespace sslic {
 
-int num_base_shapes(int ndim) { return ndim == 3 ? 4 : (ndim == 2 ? 3 : 0); }
+int num_base_shapes(int ndim) { return ndim == 3 ? 6 : (ndim == 2 ? 3 : 0); }
 int num_tile_shapes(int ndim) { return 2 * num_base_shapes(ndim); }
 
 void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz)
@@ -29,6 +29,13 @@ void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz)
     else with_shape<2>(shape % b, f);
 }
 
+int tile_voxels_per_lane(int ndim, int shape)
+{
+    auto f = [](auto sh) { return decltype(sh)::VL; };
+    const int b = num_base_shapes(ndim);
+    return ndim == 3 ? with_shape<3>(shape % b, f) : with_shape<2>(shape % b, f);
+}
+
 // expected number of centres reaching a tile of shape (tx, ty, tz)
 static double reach(const Geom& g, int tx, int ty, int tz)
 {
@@ -42,7 +49,12 @@ int default_tile_shape(const Geom& g)
 {
     // the large tile while it stays well inside the candidate capacity
     const double lim = 0.75 * tile::kCap;
-    if (g.n == 3) return reach(g, tile::Shape3L::TX, tile::Shape3L::TY, tile::Shape3L::TZ) <= lim ? 0 : 1;
+    if (g.n == 3) {
+        // float channel planes: the 2048-voxel tile keeps four CTAs per SM
+        if (g.dtype == SSLIC_F32)
+            return reach(g, tile::Shape3M::TX, tile::Shape3M::TY, tile::Shape3M::TZ) <= lim ? 4 : 1;
+        return reach(g, tile::Shape3L::TX, tile::Shape3L::TY, tile::Shape3L::TZ) <= lim ? 0 : 1;
+    }
     return reach(g, tile::Shape2L::TX, tile::Shape2L::TY, 1) <= lim ? 0 : 1;
 }
 

@@ -67,6 +67,8 @@ using Shape3L = Shape<3, 32, 16, 8, 2, 4, 4, 2>;   // 4096 voxels, grids S >= 12
 using Shape3S = Shape<3, 16, 8, 8, 2, 4, 4, 2>;    // 1024 voxels, smaller grids
 using Shape3L4 = Shape<3, 32, 16, 8, 2, 4, 4, 4>;  // as 3L, 8x4x4 warp boxes
 using Shape3S4 = Shape<3, 16, 8, 8, 2, 4, 4, 4>;   // as 3S, 8x4x4 warp boxes
+using Shape3M = Shape<3, 32, 8, 8, 2, 4, 4, 2>;    // 2048 voxels: half the staging of 3L (float planes)
+using Shape3M4 = Shape<3, 32, 8, 8, 2, 4, 4, 4>;   // as 3M, 8x4x4 warp boxes
 using Shape2L = Shape<2, 64, 32, 1, 4, 8, 1, 2>;   // 2048 pixels
 using Shape2S = Shape<2, 32, 16, 1, 4, 8, 1, 2>;   // 512 pixels
 using Shape2L4 = Shape<2, 64, 32, 1, 4, 8, 1, 4>;  // as 2L, 16x8 warp boxes
@@ -380,6 +382,33 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
                 }
                 unsigned char* p = s.planes + zl * S::PPB + yl * S::RPB + xl;
                 p[0] = v[0]; p[S::CPB] = v[1]; p[2 * S::CPB] = v[2];
+            }
+        }
+    } else if constexpr (S::kF && C == 3) {
+        // full rows of 16-byte groups (4 floats: voxel x = e / 3, channel e % 3)
+        const bool fast = (ex == TX) && (N0 % 4 == 0) && (((uintptr_t)img & 15) == 0);
+        if (fast) {
+            constexpr int GPR = TX * 3 / 4;  // groups per row
+            for (int i = tid; i < TY * TZ * GPR; i += kThreads) {
+                const int r = i / GPR, gi = i % GPR, yl = r % TY, zl = r / TY;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (yl < ey && zl < ez)
+                    v = __ldg(reinterpret_cast<const float4*>(img + vidx(g, X0, Y0 + yl, Z0 + zl) * 3) + gi);
+                const float f4[4] = {v.x, v.y, v.z, v.w};
+                unsigned char* row = s.planes + zl * S::PPB + yl * S::RPB;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int e = 4 * gi + j;
+                    *reinterpret_cast<float*>(row + (e % 3) * S::CPB + (e / 3) * 4) = f4[j];
+                }
+            }
+        } else {
+            for (int i = tid; i < TV * C; i += kThreads) {
+                const int e = i / C, c = i % C;
+                const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
+                T v = T(0);
+                if (xl < ex && yl < ey && zl < ez) v = img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl) * C + c];
+                *reinterpret_cast<T*>(s.planes + c * S::CPB + zl * S::PPB + yl * S::RPB + xl * (int)sizeof(T)) = v;
             }
         }
     } else {
@@ -916,6 +945,8 @@ inline auto with_shape(int shape, F&& f)
         case 1: return f(tile::Shape3S{});
         case 2: return f(tile::Shape3L4{});
         case 3: return f(tile::Shape3S4{});
+        case 4: return f(tile::Shape3M{});
+        case 5: return f(tile::Shape3M4{});
         default: return f(tile::Shape3L{});
         }
     } else {

@@ -346,11 +346,11 @@ static size_t footprint_thr(const Geom& g)
 }
 
 // group key: dtype, channels, dims, tile shape (-1 for the per-voxel kernel)
-static int group_key(const Geom& g, int shape) { return ((g.dtype * 512 + g.C) * 8 + g.n) * 8 + (shape + 1); }
-static int key_dtype(int key) { return key / (512 * 64); }
-static int key_channels(int key) { return (key / 64) % 512; }
-static int key_ndim(int key) { return (key / 8) % 8; }
-static int key_shape(int key) { return key % 8 - 1; }
+static int group_key(const Geom& g, int shape) { return ((g.dtype * 512 + g.C) * 8 + g.n) * 32 + (shape + 1); }
+static int key_dtype(int key) { return key / (512 * 8 * 32); }
+static int key_channels(int key) { return (key / (8 * 32)) % 512; }
+static int key_ndim(int key) { return (key / 32) % 8; }
+static int key_shape(int key) { return key % 32 - 1; }
 
 constexpr int kMaxGroups = 16;  // assignment groups (image type + tile shape) per round
 

@@ -219,6 +219,7 @@ int default_tile_shape(const Geom& g);
 int num_base_shapes(int ndim);
 int num_tile_shapes(int ndim);
 void tile_dims(int ndim, int shape, int* tx, int* ty, int* tz);
+int tile_voxels_per_lane(int ndim, int shape);
 template <typename T, int C, int NDIM>
 cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
                               unsigned* ovf_count, int grid, cudaStream_t st);

@@ -57,7 +57,7 @@ int sslic_tile_shape_info(int32_t ndim, int32_t shape, int32_t* dims, int32_t* v
     if (!dims || ndim < 2 || ndim > 3 || shape < 0 || shape >= num_tile_shapes(ndim)) return SSLIC_EINVAL;
     tile_dims(ndim, shape, &dims[0], &dims[1], &dims[2]);
     const int b = num_base_shapes(ndim);
-    if (voxels_per_lane) *voxels_per_lane = shape % b >= 2 ? 4 : 2;
+    if (voxels_per_lane) *voxels_per_lane = tile_voxels_per_lane(ndim, shape);
     if (tma_staged) *tma_staged = shape >= b ? 1 : 0;
     return SSLIC_OK;
 }

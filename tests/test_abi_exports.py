@@ -87,7 +87,7 @@ def test_create_rejects_bad_sizes(lib):
 
 def test_tile_shape_table_host_only(lib):
     from paper_1806_08741_gb300 import sslic as S
-    assert S.num_tile_shapes(3) == 8 and S.num_tile_shapes(2) == 6 and S.num_tile_shapes(1) == 0
+    assert S.num_tile_shapes(3) == 12 and S.num_tile_shapes(2) == 6 and S.num_tile_shapes(1) == 0
     seen = set()
     for nd in (2, 3):
         n = S.num_tile_shapes(nd)
@@ -101,9 +101,9 @@ def test_tile_shape_table_host_only(lib):
                 twin = S.tile_shape_info(nd, s - n // 2)
                 assert (twin["dims"], twin["voxels_per_lane"]) == (info["dims"], info["voxels_per_lane"])
             seen.add((nd, info["dims"], info["voxels_per_lane"], info["tma_staged"]))
-    assert len(seen) == 14  # every index names a different configuration
+    assert len(seen) == 18  # every index names a different configuration
     dims = (ctypes.c_int32 * 3)()
-    assert lib.sslic_tile_shape_info(3, 8, dims, None, None) == -1
+    assert lib.sslic_tile_shape_info(3, 12, dims, None, None) == -1
     assert lib.sslic_tile_shape_info(1, 0, dims, None, None) == -1
     assert lib.sslic_set_tile_shape(None, 0) == -1
     assert lib.sslic_autotune(None, None, None, None, 1, None, None) == -1
@@ -118,7 +118,7 @@ def test_tune_table_host_only(lib):
     assert S.tune_lookup(p) == 7
     assert S.tune_lookup(S.Params(size=(300, 200, 100), grid=(8, 8, 8))) == -1   # keyed by grid
     assert S.tune_lookup(S.Params(size=(50, 60, 70), grid=(16, 16, 16))) == 7    # not by size
-    for bad in (-1, 8):
+    for bad in (-1, 12):
         with pytest.raises(S.SSLICError):
             S.tune_record(p, bad)
     with pytest.raises(S.SSLICError) as e:

@@ -143,7 +143,7 @@ def _gpu_iterate_shape(img, grid, centres, m, shape):
         return lab.cpu().numpy(), cout.cpu().numpy().astype(np.float64)
 
 
-SHAPE_CASES = [("3d", (75, 53, 27), (16, 16, 16), 8), ("3d_small_grid", (40, 36, 20), (5, 5, 5), 8),
+SHAPE_CASES = [("3d", (75, 53, 27), (16, 16, 16), 12), ("3d_small_grid", (40, 36, 20), (5, 5, 5), 12),
                ("2d", (203, 150), (16, 16), 6), ("2d_small_grid", (130, 70), (3, 3), 6)]
 
 

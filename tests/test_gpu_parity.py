@@ -186,7 +186,7 @@ def test_autotune_picks_a_measured_shape_and_keeps_results():
         lab = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
         t = ctx.autotune(dimg, lab, reps=2)
         assert 0 <= t["best"] < S.num_tile_shapes(3)
-        assert len(t["ms"]) == 8 and all(v > 0 for v in t["ms"])
+        assert len(t["ms"]) == S.num_tile_shapes(3) and all(v > 0 for v in t["ms"])
         assert t["ms"][t["best"]] == min(t["ms"])
         assert ctx.tile_shape == t["best"]
         cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")

@@ -46,11 +46,11 @@ UNIT = "Gvoxel-iter/s"
 # summarised in profiles/, keyed by the SHA-256 of the kernel's source file:
 # a changed kernel reports null until it is profiled again.
 TRAFFIC_BYTES = {
-    # profiles/assign_tile_kernel_rgb3d_512x512x256.md: 202.8 MB read + 215.7 MB
+    # profiles/assign_tile_kernel_rgb3d_512x512x256.md: 206.3 MB read + 215.6 MB
     # written per launch on the 67.1 M-voxel profiling workload, scaled by the
     # voxel ratio (69.4x) to the 4.66 G-voxel launch
-    ("rgb3d_2048x1216x1871", "ab5ac041cdc6e732cfc30a1227b46574791dada1d1ad53a62c9eeaf8db58dc48"):
-        (202.845440e6 + 215.713536e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
+    ("rgb3d_2048x1216x1871", "605809dd4d6d29cb83a82ee22c90a11e3421be4e35d8d068f1447e465007b76e"):
+        (206.316800e6 + 215.624960e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
 }
 
 
@@ -370,7 +370,7 @@ def run_ours(args, w):
 # ---------------------------------------------------------------------------
 # colour input: the same volume converted to CIE-Lab float (the paper's data)
 # ---------------------------------------------------------------------------
-def lab_bench(w, rgb, labels, steps=3, warmup=1):
+def lab_bench(w, rgb, labels, steps=3, warmup=1, shape=None):
     """The RGB workload converted on the device to CIE-Lab float (12 B per
     voxel) and segmented with the same parameters: the conversion's achieved
     bandwidth (3 B read + 12 B written per voxel), whole runs (iterations +
@@ -403,7 +403,11 @@ def lab_bench(w, rgb, labels, steps=3, warmup=1):
                      enforce_connectivity=w.connectivity)
     with S.Context(p) as ctx:
         cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device=rgb.device)
-        t = ctx.autotune(img, labels, reps=2, stream=stream)
+        if shape is None:
+            t = ctx.autotune(img, labels, reps=2, stream=stream)
+        else:
+            ctx.tile_shape = shape
+            t = {"best": shape, "ms": None}
         for _ in range(warmup):
             ctx.run(img, labels, cen, stream=stream)
         torch.cuda.synchronize()
@@ -625,6 +629,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the 64-band float workload")
     ap.add_argument("--precision-only", action="store_true", help="only the 64-band float workload")
     ap.add_argument("--no-lab", action="store_true", help="skip the CIE-Lab float form of the workload")
+    ap.add_argument("--lab-only", action="store_true",
+                    help="only the CIE-Lab float form of the workload (--tile-shape fixes its shape)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
     ap.add_argument("--reference-edge", type=int, default=128,
@@ -634,6 +640,19 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream benchmark")
     ap.add_argument("--serve-requests", type=int, default=200)
     args = ap.parse_args()
+    if args.lab_only:
+        import torch
+
+        from paper_1806_08741_gb300 import inputs
+        w = inputs.WORKLOADS[args.workload]
+        spec = w.image
+        torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        rgb = torch.empty(spec.shape, dtype=torch.uint8, device="cuda")
+        inputs.make_image_device(spec, rgb.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        labels = torch.empty(spec.shape[:-1], dtype=torch.int32, device="cuda")
+        out = lab_bench(w, rgb, labels, steps=args.steps, warmup=args.warmup, shape=args.tile_shape)
+        print(json.dumps({"lab": out}), flush=True)
+        return 0
     if args.precision_only:
         print(json.dumps({"precision": precision_bench(steps=max(3, args.steps))}), flush=True)
         return 0

@@ -8,7 +8,8 @@
 // the (request, tile) queue of each (image type, tile shape) group; crowded
 // tiles and image types without a tile kernel use the per-voxel kernel.  The
 // arithmetic is the single-image path's, so each request's labels and
-// centres are the ones sslic_run gives for it alone.
+// centres are the ones sslic_run gives for it alone (float images: up to
+// the order of their floating-point sums).
 //
 // Serving.  A worker thread keeps requests on the device and runs rounds of
 // continuous batching: each round advances every admitted request by one
@@ -323,10 +324,7 @@ struct Slot {
 
 static size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 
-static bool tile_type(const Geom& g)
-{
-    return g.n >= 2 && ((g.dtype == SSLIC_U8 && (g.C == 1 || g.C == 3)) || (g.dtype == SSLIC_U16 && g.C == 1));
-}
+static bool tile_type(const Geom& g) { return has_tile_kernel(g); }
 
 static size_t footprint(const Geom& g)
 {
@@ -516,9 +514,12 @@ cudaError_t launch_group(sslic_server* s, int C, int n, int shape, const TileArg
                                : launch_tile_queue<uint8_t, 3, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
         else e = n == 3 ? launch_tile_queue<uint8_t, 1, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
                         : launch_tile_queue<uint8_t, 1, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
-    } else {
+    } else if constexpr (sizeof(T) == 2) {
         e = n == 3 ? launch_tile_queue<uint16_t, 1, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
                    : launch_tile_queue<uint16_t, 1, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
+    } else {
+        e = n == 3 ? launch_tile_queue<float, 3, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
+                   : launch_tile_queue<float, 3, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
     }
     if (e != cudaSuccess || !ta) return e;
     b_voxel_tiles<T><<<grid, 256, 0, s->cs>>>(ta, s->ovf[gi], s->ovf_cnt + gi);

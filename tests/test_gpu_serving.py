@@ -173,3 +173,46 @@ def test_served_results_equal_alone_for_each_recorded_shape(shape):
     for (img, grid, m), lab in zip(reqs, outs):
         ref = O.slic(O.params_for(img, grid, m=m, max_iter=iters), img)
         np.testing.assert_array_equal(lab, ref["labels"])
+
+
+def test_served_lab_requests_match_alone():
+    """3-channel float (CIE-Lab) requests go through the batched tile kernel
+    beside integer ones; each equals its run alone within the float
+    tolerance (labels >= 99.99 % equal, centre table within 1e-5), the
+    integer ones bit for bit."""
+    from paper_1806_08741_gb300 import sslic as S
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i in range(5):
+        size = (int(rng.integers(70, 300)), int(rng.integers(60, 200)))
+        rgb = I.make_image(I.ImageSpec(size, 3, "u8", 400 + i, max(2, size[0] * size[1] // 3000), 6))
+        reqs.append((O.srgb_to_lab(rgb).astype(np.float32), (int(rng.choice([8, 16])),) * 2, 10.0))
+    for i in range(3):
+        side = int(rng.integers(40, 90))
+        rgb = I.make_image(I.ImageSpec((side, side - 7, side - 20), 3, "u8", 500 + i, 20, 6))
+        reqs.append((O.srgb_to_lab(rgb).astype(np.float32), (8, 8, 8), 10.0))
+    reqs += _mix(13)[:3]
+    iters = 5
+    outs = []
+    with S.Server(1 << 30, max_active=6) as srv:
+        tickets = []
+        for img, grid, m in reqs:
+            p = S.params_for(img, grid, m=m, max_iter=iters)
+            lab = np.empty(img.shape[:-1], np.int32)
+            K = 1
+            for n, g in zip(p.size, p.grid):
+                K *= -(-n // g)
+            cen = np.empty((K, p.channels + p.ndim), np.float32)
+            tickets.append(srv.submit(p, img, lab, cen))
+            outs.append((lab, cen))
+        for t in tickets:
+            srv.wait(t)
+        assert srv.stats()["status"] == 0
+    for (img, grid, m), (lab, cen) in zip(reqs, outs):
+        ref_l, ref_c = _alone(img, grid, m, iters)
+        if img.dtype == np.float32:
+            assert (lab == ref_l).mean() >= 0.9999
+            assert np.linalg.norm(cen - ref_c) / np.linalg.norm(ref_c) <= 1e-5
+        else:
+            np.testing.assert_array_equal(lab, ref_l)
+            np.testing.assert_array_equal(cen, ref_c)

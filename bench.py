@@ -46,9 +46,9 @@ UNIT = "Gvoxel-iter/s"
 # summarised in profiles/, keyed by the SHA-256 of the kernel's source file:
 # a changed kernel reports null until it is profiled again.
 TRAFFIC_BYTES = {
-    # profiles/assign_tile_kernel_rgb3d_512x512x256.md: 206.3 MB read + 215.6 MB
-    # written per launch on the 67.1 M-voxel profiling workload, scaled by the
-    # voxel ratio (69.4x) to the 4.66 G-voxel launch
+    # ncu capture of the tile kernel on the 67.1 M-voxel profiling workload
+    # (rgb3d_512x512x256): 206.3 MB read + 215.6 MB written per launch,
+    # scaled by the voxel ratio (69.4x) to the 4.66 G-voxel launch
     ("rgb3d_2048x1216x1871", "605809dd4d6d29cb83a82ee22c90a11e3421be4e35d8d068f1447e465007b76e"):
         (206.316800e6 + 215.624960e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
 }
@@ -317,15 +317,18 @@ def run_ours(args, w):
         if dist:
             dist.barrier()
         n_e2e = max(1, min(args.steps, 3))
+        calls = []
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            ctx.run_host(h_img, h_lab, h_cen, stream=stream)
+            t1 = time.perf_counter()
+            ctx.run_host(h_img, h_lab, h_cen, stream=stream)   # returns after its stream drained
+            calls.append((time.perf_counter() - t1) * 1e3)
         dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, dist, dev)
         same = bool(torch.equal(h_lab, labels.cpu()))
         e2e = {"value": job_throughput(world, V, iters, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(h_img.numel() * h_img.element_size()),
                "d2h_bytes_per_step": int(h_lab.numel() * 4 + h_cen.numel() * 4),
-               "ms_per_step": dt * 1e3, "labels_equal_device_run": same}
+               "ms_per_step": dt * 1e3, "ms_per_call": calls, "labels_equal_device_run": same}
         del h_img, h_lab, h_cen
 
     lab = None

@@ -118,6 +118,8 @@ def lib():
         L.oracle_slic.argtypes = [P, vp, vp, dp, vp, vp, vp]
         L.oracle_slic_from.argtypes = [P, vp, dp, vp, dp, vp, vp, vp]
         L.oracle_srgb_to_lab.argtypes = [vp, ctypes.c_int64, dp]
+        L.oracle_assign_voxels.argtypes = [P, vp, dp, ctypes.c_int64, vp, ctypes.c_int64, vp, vp, vp]
+        L.oracle_assign_voxels.restype = ctypes.c_int
         for f in ("oracle_seed", "oracle_assign", "oracle_update", "oracle_srgb_to_lab",
                   "oracle_connectivity", "oracle_slic", "oracle_slic_from"):
             getattr(L, f).restype = ctypes.c_int
@@ -192,6 +194,24 @@ def assign(p: Params, image: np.ndarray, centres: np.ndarray) -> np.ndarray:
     _check(lib().oracle_assign(ctypes.byref(p.to_c()), _ptr(image), _ptr(c), c.shape[0],
                                _ptr(labels)), "assign")
     return labels
+
+
+def assign_voxels(p: Params, image: np.ndarray, centres: np.ndarray, q, cand_start, cand) -> np.ndarray:
+    """The labels ``assign`` would give at the raster indices ``q`` only (for
+    images too large to assign whole); the candidates of voxel i are
+    ``cand[cand_start[i]:cand_start[i+1]]`` and must include every centre
+    whose window covers it."""
+    image = _img(image)
+    c = np.ascontiguousarray(centres, np.float64)
+    q = np.ascontiguousarray(q, np.int64)
+    cs = np.ascontiguousarray(cand_start, np.int64)
+    cd = np.ascontiguousarray(cand, np.int64)
+    if cs.shape[0] != q.shape[0] + 1:
+        raise ValueError("cand_start needs len(q) + 1 entries")
+    out = np.empty(q.shape[0], np.int32)
+    _check(lib().oracle_assign_voxels(ctypes.byref(p.to_c()), _ptr(image), _ptr(c), c.shape[0], _ptr(q),
+                                      q.shape[0], _ptr(cs), _ptr(cd), _ptr(out)), "assign_voxels")
+    return out
 
 
 def update(p: Params, image: np.ndarray, labels: np.ndarray, centres: np.ndarray):

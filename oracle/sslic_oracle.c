@@ -401,6 +401,57 @@ int oracle_assign(const oracle_params* p, const void* image, const double* centr
     return assign(&g, image, centres, K, labels);
 }
 
+/* The assignment at chosen voxels only, for images too large for
+ * oracle_assign: the same rule as assign() above, evaluated for one voxel at
+ * a time.  The centre loop of assign() visits every centre in ascending k
+ * and keeps a strictly smaller D^2; at one voxel that is the lexicographic
+ * minimum of (D^2, k) over the centres whose window covers it, which does
+ * not depend on the order the candidates are listed in. */
+int oracle_assign_voxels(const oracle_params* p, const void* image, const double* centres, int64_t K,
+                         const int64_t* q, int64_t nq, const int64_t* cand_start, const int64_t* cand,
+                         int32_t* labels_out)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (nq < 0 || (nq > 0 && (!image || !centres || !q || !cand_start || !cand || !labels_out)))
+        return ORACLE_EINVAL;
+    const int width = g.C + g.n;
+    float* f32 = (float*)malloc((size_t)g.C * sizeof(float));
+    double* f64 = (double*)malloc((size_t)g.C * sizeof(double));
+    if (!f32 || !f64) { free(f32); free(f64); return ORACLE_ENOMEM; }
+    for (int64_t i = 0; i < nq; ++i) {
+        if (q[i] < 0 || q[i] >= g.V) { free(f32); free(f64); return ORACLE_EINVAL; }
+        int64_t x[3];
+        coords(&g, q[i], x);
+        for (int c = 0; c < g.C; ++c) {
+            f64[c] = pix(&g, image, q[i], c);
+            f32[c] = (float)f64[c];
+        }
+        int32_t best = -1;
+        double bd64 = INFINITY;
+        float bd32 = INFINITY;
+        for (int64_t j = cand_start[i]; j < cand_start[i + 1]; ++j) {
+            const int64_t k = cand[j];
+            if (k < 0 || k >= K) { free(f32); free(f64); return ORACLE_EINVAL; }
+            const double* ctr = centres + k * width;
+            int inside = 1;
+            for (int d = 0; d < g.n; ++d) inside = inside && in_window(&g, d, x[d], ctr[g.C + d]);
+            if (!inside) continue;
+            if (g.fp64) {
+                double D = dist64(&g, f64, x, ctr);
+                if (D < bd64 || (D == bd64 && k < best)) { bd64 = D; best = (int32_t)k; }
+            } else {
+                float D = dist32(&g, f32, x, ctr);
+                if (D < bd32 || (D == bd32 && k < best)) { bd32 = D; best = (int32_t)k; }
+            }
+        }
+        labels_out[i] = best;
+    }
+    free(f32); free(f64);
+    return ORACLE_OK;
+}
+
 /* ---- update (Sec. 2.2 "Update clusters", Sec. 3.1 map-reduce; R9, R10) --- */
 
 static int update(const geom* g, const void* image, const int32_t* labels, int64_t K,

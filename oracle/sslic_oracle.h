@@ -76,6 +76,15 @@ double oracle_gradient(const oracle_params* p, const void* image, int64_t q);
 int oracle_assign(const oracle_params* p, const void* image,
                   const double* centres, int64_t K, int32_t* labels);
 
+/* The labels oracle_assign would leave at the nq voxels q[i] (raster
+ * indices), for images too large to assign whole.  The candidates of voxel
+ * i are cand[cand_start[i] .. cand_start[i+1]) (cand_start has nq + 1
+ * entries); they must include every centre whose window covers the voxel,
+ * in any order (others fail the window test). */
+int oracle_assign_voxels(const oracle_params* p, const void* image, const double* centres, int64_t K,
+                         const int64_t* q, int64_t nq, const int64_t* cand_start, const int64_t* cand,
+                         int32_t* labels_out);
+
 /* One update: new centres from labels.  centres is read (previous values,
  * kept for empty clusters) and overwritten.  counts (K, may be NULL)
  * receives member counts; residual (may be NULL) receives the residual. */

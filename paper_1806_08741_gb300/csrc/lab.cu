@@ -48,6 +48,8 @@ __device__ __forceinline__ void to_lab(const float* lin, unsigned r, unsigned g,
     o[2] = 200.0f * (fy - fz);
 }
 
+}  // namespace
+
 __global__ void __launch_bounds__(kLabThreads) srgb_to_lab_kernel(const uint8_t* __restrict__ rgb,
                                                                   float* __restrict__ lab, int64_t n, int vec)
 {
@@ -87,7 +89,6 @@ __global__ void __launch_bounds__(kLabThreads) srgb_to_lab_kernel(const uint8_t*
     }
 }
 
-}  // namespace
 }  // namespace sslic
 
 extern "C" int sslic_srgb_to_lab(const void* rgb_dev, void* lab_dev, int64_t n, void* stream)

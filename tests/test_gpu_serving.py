@@ -178,8 +178,12 @@ def test_served_results_equal_alone_for_each_recorded_shape(shape):
 def test_served_lab_requests_match_alone():
     """3-channel float (CIE-Lab) requests go through the batched tile kernel
     beside integer ones; each equals its run alone within the float
-    tolerance (labels >= 99.99 % equal, centre table within 1e-5), the
-    integer ones bit for bit."""
+    tolerance, the integer ones bit for bit.  Both sides are the GPU's FP32
+    path and differ only in the order of their floating-point sums, so a
+    near-tie may flip: labels >= 99.99 % equal, and every cluster whose
+    member set is the same on both sides within 1e-5 per element (reading
+    T1; on these small images one flipped voxel moves its cluster's centre by
+    more than a table-wide 1e-5)."""
     from paper_1806_08741_gb300 import sslic as S
     rng = np.random.default_rng(11)
     reqs = []
@@ -212,7 +216,11 @@ def test_served_lab_requests_match_alone():
         ref_l, ref_c = _alone(img, grid, m, iters)
         if img.dtype == np.float32:
             assert (lab == ref_l).mean() >= 0.9999
-            assert np.linalg.norm(cen - ref_c) / np.linalg.norm(ref_c) <= 1e-5
+            flip = lab != ref_l
+            differ = np.unique(np.concatenate([lab[flip], ref_l[flip]]))
+            same = np.setdiff1d(np.arange(cen.shape[0]), differ)
+            rel = np.abs(cen[same] - ref_c[same]) / np.maximum(np.abs(ref_c[same]), 1e-3)
+            assert rel.max() <= 1e-5, rel.max()
         else:
             np.testing.assert_array_equal(lab, ref_l)
             np.testing.assert_array_equal(cen, ref_c)

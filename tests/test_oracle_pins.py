@@ -583,3 +583,35 @@ def test_lab_grey_axis():
     lab = O.srgb_to_lab(np.stack([v, v, v], -1))
     assert np.all(np.diff(lab[:, 0]) > 0)
     assert np.abs(lab[:, 1:]).max() < 0.02
+
+
+# --------------------------------------------------------------------------
+# assignment at chosen voxels (for sampling images too large to assign whole)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("size,grid,C,mode", [((61,), (4,), 2, O.FP32), ((40, 33), (6, 5), 3, O.FP32),
+                                              ((20, 17, 13), (4, 5, 3), 1, O.FP64),
+                                              ((24, 18, 16), (8, 8, 8), 3, O.FP32)])
+def test_assign_voxels_equals_assign(size, grid, C, mode):
+    import _lattice
+    rng = np.random.default_rng(sum(size))
+    img = rng.integers(0, 256, size=tuple(reversed(size)) + (C,), dtype=np.uint8)
+    p = O.params_for(img, grid, m=7.0, max_iter=2, mode=mode)
+    seeds = O.seed(p, img)
+    K = seeds.shape[0]
+    V = int(np.prod(size))
+    want = O.assign(p, img, seeds).reshape(-1)
+    q = np.arange(V, dtype=np.int64)
+    # every centre as a candidate, listed in a shuffled order
+    start = np.arange(V + 1, dtype=np.int64) * K
+    cand = np.concatenate([rng.permutation(K) for _ in range(V)])
+    np.testing.assert_array_equal(O.assign_voxels(p, img, seeds, q, start, cand), want)
+    # the lattice superset of the seeds that can cover each voxel
+    start, cand = _lattice.seed_candidates(size, grid, q)
+    np.testing.assert_array_equal(O.assign_voxels(p, img, seeds, q, start, cand), want)
+    # and after an update (centres anywhere): with every centre listed
+    cen, _, _ = O.update(p, img, want.reshape(img.shape[:-1]), seeds)
+    start = np.arange(V + 1, dtype=np.int64) * K
+    cand = np.tile(np.arange(K), V)
+    np.testing.assert_array_equal(O.assign_voxels(p, img, cen, q, start, cand),
+                                  O.assign(p, img, cen).reshape(-1))

@@ -30,10 +30,10 @@ _DTYPE_CODE = {np.dtype(np.uint8): U8, np.dtype(np.uint16): U16, np.dtype(np.flo
 class _Params(ctypes.Structure):
     _fields_ = [
         ("ndim", ctypes.c_int32),
-        ("size", ctypes.c_int64 * 3),
+        ("size", ctypes.c_int64 * 4),
         ("channels", ctypes.c_int32),
         ("dtype", ctypes.c_int32),
-        ("grid", ctypes.c_int32 * 3),
+        ("grid", ctypes.c_int32 * 4),
         ("m", ctypes.c_double),
         ("max_iter", ctypes.c_int32),
         ("conv_threshold", ctypes.c_double),
@@ -66,7 +66,7 @@ class Params:
     def to_c(self) -> _Params:
         p = _Params()
         p.ndim = len(self.size)
-        for d in range(3):
+        for d in range(4):
             p.size[d] = int(self.size[d]) if d < len(self.size) else 1
             p.grid[d] = int(self.grid[d]) if d < len(self.grid) else 1
         p.channels = int(self.channels)

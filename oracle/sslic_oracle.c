@@ -60,25 +60,28 @@
 #define ORACLE_EINVAL (-1)
 #define ORACLE_ENOMEM (-2)
 
+/* images of 1 to ND dimensions (the paper's filter is n-dimensional, Sec. 3) */
+#define ND 4
+
 typedef struct {
     int n;              /* spatial dims actually used */
-    int64_t N[3];       /* sizes, padded with 1 */
-    int64_t stride[3];  /* raster strides */
+    int64_t N[ND];      /* sizes, padded with 1 */
+    int64_t stride[ND]; /* raster strides */
     int64_t V;          /* voxel count */
     int C;              /* channels */
     int dt;             /* dtype */
-    int S[3];           /* grid, padded with 1 */
-    int64_t ns[3];      /* seeds per axis, padded with 1 */
+    int S[ND];          /* grid, padded with 1 */
+    int64_t ns[ND];     /* seeds per axis, padded with 1 */
     int64_t K;          /* clusters */
     int fp64;           /* arithmetic mode */
-    float w32[3];       /* fl32(m^2 / S_d^2) */
-    double w64[3];      /* m^2 / S_d^2 */
+    float w32[ND];      /* fl32(m^2 / S_d^2) */
+    double w64[ND];     /* m^2 / S_d^2 */
 } geom;
 
 static int make_geom(const oracle_params* p, geom* g)
 {
     if (!p) return ORACLE_EINVAL;
-    if (p->ndim < 1 || p->ndim > 3) return ORACLE_EINVAL;
+    if (p->ndim < 1 || p->ndim > ND) return ORACLE_EINVAL;
     if (p->channels < 1) return ORACLE_EINVAL;
     if (p->dtype != ORACLE_U8 && p->dtype != ORACLE_U16 && p->dtype != ORACLE_F32) return ORACLE_EINVAL;
     if (p->mode != ORACLE_FP32 && p->mode != ORACLE_FP64) return ORACLE_EINVAL;
@@ -91,7 +94,7 @@ static int make_geom(const oracle_params* p, geom* g)
     g->fp64 = (p->mode == ORACLE_FP64);
     g->V = 1;
     g->K = 1;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < ND; ++d) {
         if (d < g->n) {
             /* positions must be exact in float: N_d <= 2^24 */
             if (p->size[d] < 1 || p->size[d] > (1 << 24)) return ORACLE_EINVAL;
@@ -142,19 +145,46 @@ static int64_t pix_int(const geom* g, const void* image, int64_t q, int c)
 
 static void coords(const geom* g, int64_t q, int64_t* x)
 {
-    for (int d = 0; d < 3; ++d) x[d] = (q / g->stride[d]) % g->N[d];
+    for (int d = 0; d < ND; ++d) x[d] = (q / g->stride[d]) % g->N[d];
 }
 
 static int64_t index_of(const geom* g, const int64_t* x)
 {
-    return x[0] * g->stride[0] + x[1] * g->stride[1] + x[2] * g->stride[2];
+    int64_t q = 0;
+    for (int d = 0; d < ND; ++d) q += x[d] * g->stride[d];
+    return q;
+}
+
+/* The points of the box lo..hi (inclusive on every axis) in raster order,
+ * dimension 0 fastest: box_first sets x to the first point (0: the box is
+ * empty), box_next moves x to the next one (0: x was the last). */
+static int box_first(int64_t* x, const int64_t* lo, const int64_t* hi)
+{
+    int ok = 1;
+    for (int d = 0; d < ND; ++d) {
+        x[d] = lo[d];
+        ok = ok && lo[d] <= hi[d];
+    }
+    return ok;
+}
+
+static int box_next(int64_t* x, const int64_t* lo, const int64_t* hi)
+{
+    for (int d = 0; d < ND; ++d) {
+        if (x[d] < hi[d]) {
+            ++x[d];
+            return 1;
+        }
+        x[d] = lo[d];
+    }
+    return 0;
 }
 
 /* ---- gradient (R2) ------------------------------------------------------ */
 
 static double gradient(const geom* g, const void* image, int64_t q)
 {
-    int64_t x[3];
+    int64_t x[ND];
     coords(g, q, x);
     if (g->dt != ORACLE_F32) {
         /* integer images: exact in int64 */
@@ -209,7 +239,7 @@ double oracle_gradient(const oracle_params* p, const void* image, int64_t q)
 
 static void store_centre(const geom* g, const void* image, int64_t q, double* row)
 {
-    int64_t x[3];
+    int64_t x[ND];
     coords(g, q, x);
     for (int c = 0; c < g->C; ++c) {
         double v = pix(g, image, q, c);
@@ -222,9 +252,9 @@ static int seed(const geom* g, int perturb, const void* image, double* centres)
 {
     const int width = g->C + g->n;
     for (int64_t k = 0; k < g->K; ++k) {
-        int64_t x[3];
+        int64_t x[ND];
         int64_t rem = k;
-        for (int d = 0; d < 3; ++d) {
+        for (int d = 0; d < ND; ++d) {
             int64_t j = rem % g->ns[d];
             rem /= g->ns[d];
             int64_t o = (g->N[d] - 1 - (g->ns[d] - 1) * g->S[d]) / 2;
@@ -234,23 +264,23 @@ static int seed(const geom* g, int perturb, const void* image, double* centres)
         if (perturb) {
             double best_g = gradient(g, image, best);
             /* 3^n offsets in raster order, dimension 0 fastest */
-            int lo2 = g->n >= 3 ? -1 : 0, hi2 = g->n >= 3 ? 1 : 0;
-            int lo1 = g->n >= 2 ? -1 : 0, hi1 = g->n >= 2 ? 1 : 0;
-            for (int o2 = lo2; o2 <= hi2; ++o2)
-                for (int o1 = lo1; o1 <= hi1; ++o1)
-                    for (int o0 = -1; o0 <= 1; ++o0) {
-                        int64_t y[3] = {x[0] + o0, x[1] + o1, x[2] + o2};
-                        int inside = 1;
-                        for (int d = 0; d < 3; ++d)
-                            if (y[d] < 0 || y[d] >= g->N[d]) inside = 0;
-                        if (!inside) continue;
-                        int64_t q = index_of(g, y);
-                        double gq = gradient(g, image, q);
-                        if (gq < best_g) {
-                            best_g = gq;
-                            best = q;
-                        }
-                    }
+            int64_t lo[ND], hi[ND], y[ND];
+            for (int d = 0; d < ND; ++d) {
+                lo[d] = d < g->n ? x[d] - 1 : 0;
+                hi[d] = d < g->n ? x[d] + 1 : 0;
+            }
+            for (int more = box_first(y, lo, hi); more; more = box_next(y, lo, hi)) {
+                int inside = 1;
+                for (int d = 0; d < ND; ++d)
+                    if (y[d] < 0 || y[d] >= g->N[d]) inside = 0;
+                if (!inside) continue;
+                int64_t q = index_of(g, y);
+                double gq = gradient(g, image, q);
+                if (gq < best_g) {
+                    best_g = gq;
+                    best = q;
+                }
+            }
         }
         store_centre(g, image, best, centres + k * width);
     }
@@ -307,7 +337,7 @@ double oracle_distance(const oracle_params* p, const double* feature,
 {
     geom g;
     if (make_geom(p, &g) != ORACLE_OK) return -1.0;
-    int64_t x[3] = {0, 0, 0};
+    int64_t x[ND] = {0};
     for (int d = 0; d < g.n; ++d) x[d] = pos[d];
     if (g.fp64) return dist64(&g, feature, x, centre);
     float f[4096];
@@ -336,16 +366,16 @@ static int assign(const geom* g, const void* image, const double* centres, int64
     else d32 = (float*)malloc((size_t)g->V * sizeof(float));
     float* f32 = (float*)malloc((size_t)g->C * sizeof(float));
     double* f64 = (double*)malloc((size_t)g->C * sizeof(double));
-    int64_t* xs[3] = {NULL, NULL, NULL};
-    int64_t len[3];
+    int64_t* xs[ND] = {NULL};
+    int64_t len[ND];
     int ok = (d32 || d64) && f32 && f64;
-    for (int d = 0; d < 3 && ok; ++d) {
+    for (int d = 0; d < ND && ok; ++d) {
         xs[d] = (int64_t*)malloc((size_t)(2 * g->S[d] + 3) * sizeof(int64_t));
         if (!xs[d]) ok = 0;
     }
     if (!ok) {
         free(d32); free(d64); free(f32); free(f64);
-        for (int d = 0; d < 3; ++d) free(xs[d]);
+        for (int d = 0; d < ND; ++d) free(xs[d]);
         return ORACLE_ENOMEM;
     }
     /* R4: reset l = undefined (-1), d = +inf */
@@ -357,7 +387,7 @@ static int assign(const geom* g, const void* image, const double* centres, int64
     for (int64_t k = 0; k < K; ++k) {
         const double* ctr = centres + k * width;
         /* the window of centre k, axis by axis (R5) */
-        for (int d = 0; d < 3; ++d) {
+        for (int d = 0; d < ND; ++d) {
             len[d] = 0;
             if (d >= g->n) {
                 xs[d][len[d]++] = 0;
@@ -370,24 +400,29 @@ static int assign(const geom* g, const void* image, const double* centres, int64
                 if (in_window(g, d, xd, c)) xs[d][len[d]++] = xd;
             }
         }
-        for (int64_t i2 = 0; i2 < len[2]; ++i2)
-            for (int64_t i1 = 0; i1 < len[1]; ++i1)
-                for (int64_t i0 = 0; i0 < len[0]; ++i0) {
-                    int64_t x[3] = {xs[0][i0], xs[1][i1], xs[2][i2]};
-                    int64_t q = index_of(g, x);
-                    if (g->fp64) {
-                        for (int c = 0; c < g->C; ++c) f64[c] = pix(g, image, q, c);
-                        double D = dist64(g, f64, x, ctr);
-                        if (D < d64[q]) { d64[q] = D; labels[q] = (int32_t)k; }
-                    } else {
-                        for (int c = 0; c < g->C; ++c) f32[c] = (float)pix(g, image, q, c);
-                        float D = dist32(g, f32, x, ctr);
-                        if (D < d32[q]) { d32[q] = D; labels[q] = (int32_t)k; }
-                    }
-                }
+        /* the window's voxels in raster order */
+        int64_t ilo[ND], ihi[ND], ii[ND];
+        for (int d = 0; d < ND; ++d) {
+            ilo[d] = 0;
+            ihi[d] = len[d] - 1;
+        }
+        for (int more = box_first(ii, ilo, ihi); more; more = box_next(ii, ilo, ihi)) {
+            int64_t x[ND];
+            for (int d = 0; d < ND; ++d) x[d] = xs[d][ii[d]];
+            int64_t q = index_of(g, x);
+            if (g->fp64) {
+                for (int c = 0; c < g->C; ++c) f64[c] = pix(g, image, q, c);
+                double D = dist64(g, f64, x, ctr);
+                if (D < d64[q]) { d64[q] = D; labels[q] = (int32_t)k; }
+            } else {
+                for (int c = 0; c < g->C; ++c) f32[c] = (float)pix(g, image, q, c);
+                float D = dist32(g, f32, x, ctr);
+                if (D < d32[q]) { d32[q] = D; labels[q] = (int32_t)k; }
+            }
+        }
     }
     free(d32); free(d64); free(f32); free(f64);
-    for (int d = 0; d < 3; ++d) free(xs[d]);
+    for (int d = 0; d < ND; ++d) free(xs[d]);
     return ORACLE_OK;
 }
 
@@ -422,7 +457,7 @@ int oracle_assign_voxels(const oracle_params* p, const void* image, const double
     if (!f32 || !f64) { free(f32); free(f64); return ORACLE_ENOMEM; }
     for (int64_t i = 0; i < nq; ++i) {
         if (q[i] < 0 || q[i] >= g.V) { free(f32); free(f64); return ORACLE_EINVAL; }
-        int64_t x[3];
+        int64_t x[ND];
         coords(&g, q[i], x);
         for (int c = 0; c < g.C; ++c) {
             f64[c] = pix(&g, image, q[i], c);
@@ -470,7 +505,7 @@ static int update(const geom* g, const void* image, const int32_t* labels, int64
         int32_t k = labels[q];
         if (k < 0) continue; /* R8 */
         if (k >= K) { free(cnt); free(isum); free(fsum); return ORACLE_EINVAL; }
-        int64_t x[3];
+        int64_t x[ND];
         coords(g, q, x);
         cnt[k] += 1;
         for (int c = 0; c < g->C; ++c) {
@@ -528,7 +563,7 @@ static int64_t flood(const geom* g, const int32_t* lab_in, int64_t s, int32_t la
     vis[s] = 1;
     while (head < tail) {
         int64_t q = queue[head++];
-        int64_t x[3];
+        int64_t x[ND];
         coords(g, q, x);
         for (int d = 0; d < g->n; ++d) {
             if (x[d] > 0) {
@@ -562,7 +597,7 @@ static int connectivity(const geom* g, const double* centres, int64_t K,
     /* phase 1: one component per centre, final if large enough (R12) */
     for (int64_t k = 0; k < K; ++k) {
         const double* ctr = centres + k * width;
-        int64_t p[3] = {0, 0, 0};
+        int64_t p[ND] = {0};
         for (int d = 0; d < g->n; ++d) {
             int64_t v = (int64_t)floor(ctr[g->C + d] + 0.5);
             if (v < 0) v = 0;
@@ -574,20 +609,17 @@ static int connectivity(const geom* g, const double* centres, int64_t K,
         if (lab_in[pq] == (int32_t)k) {
             s = pq;
         } else {
-            int64_t lo[3], hi[3];
-            for (int d = 0; d < 3; ++d) {
+            int64_t lo[ND], hi[ND], xx[ND];
+            for (int d = 0; d < ND; ++d) {
                 lo[d] = p[d] - g->S[d] / 2;
                 hi[d] = p[d] + (g->S[d] + 1) / 2 - 1;
                 if (lo[d] < 0) lo[d] = 0;
                 if (hi[d] > g->N[d] - 1) hi[d] = g->N[d] - 1;
             }
-            for (int64_t z = lo[2]; z <= hi[2] && s < 0; ++z)
-                for (int64_t y = lo[1]; y <= hi[1] && s < 0; ++y)
-                    for (int64_t x = lo[0]; x <= hi[0] && s < 0; ++x) {
-                        int64_t xx[3] = {x, y, z};
-                        int64_t q = index_of(g, xx);
-                        if (lab_in[q] == (int32_t)k) s = q;
-                    }
+            for (int more = box_first(xx, lo, hi); more && s < 0; more = box_next(xx, lo, hi)) {
+                int64_t q = index_of(g, xx);
+                if (lab_in[q] == (int32_t)k) s = q;
+            }
         }
         if (s < 0) continue;
         int64_t size = flood(g, lab_in, s, (int32_t)k, vis, queue);
@@ -607,7 +639,7 @@ static int connectivity(const geom* g, const double* centres, int64_t K,
         if (4 * size > sprod || q == 0) {
             newlab = (int32_t)next++;
         } else {
-            int64_t x[3];
+            int64_t x[ND];
             coords(g, q, x);
             int d = 0;
             while (x[d] == 0) ++d;

@@ -48,11 +48,11 @@ enum { ORACLE_U8 = 0, ORACLE_U16 = 1, ORACLE_F32 = 2 };
 enum { ORACLE_FP32 = 0, ORACLE_FP64 = 1 };
 
 typedef struct {
-    int32_t ndim;           /* 1..3 */
-    int64_t size[3];        /* N_d, d = 0 fastest; unused dims ignored */
+    int32_t ndim;           /* 1..4 */
+    int64_t size[4];        /* N_d, d = 0 fastest; unused dims ignored */
     int32_t channels;       /* C >= 1 */
     int32_t dtype;          /* ORACLE_U8 / ORACLE_U16 / ORACLE_F32 */
-    int32_t grid[3];        /* S_d >= 1 */
+    int32_t grid[4];        /* S_d >= 1 */
     double  m;              /* proximity weight */
     int32_t max_iter;       /* >= 0 */
     double  conv_threshold; /* <= 0: always run max_iter iterations */

@@ -151,7 +151,8 @@ def brute_assign_fp32(img, centres, grid, m):
 
 
 CASES = [((37,), (5,), 1), ((37,), (4,), 3), ((13, 11), (3, 4), 1), ((13, 11), (4, 4), 3),
-         ((9, 7, 5), (3, 3, 2), 1), ((9, 7, 5), (2, 3, 4), 3)]
+         ((9, 7, 5), (3, 3, 2), 1), ((9, 7, 5), (2, 3, 4), 3),
+         ((5, 4, 4, 3), (2, 2, 2, 2), 1), ((6, 4, 3, 4), (3, 2, 2, 2), 3)]
 
 
 @pytest.mark.parametrize("size,grid,C", CASES)
@@ -265,7 +266,8 @@ def brute_perturbed_seeds(img, grid):
     return np.array(seeds)
 
 
-@pytest.mark.parametrize("size,grid", [((37,), (4,)), ((17, 12), (4, 3)), ((9, 8, 7), (3, 3, 2))])
+@pytest.mark.parametrize("size,grid", [((37,), (4,)), ((17, 12), (4, 3)), ((9, 8, 7), (3, 3, 2)),
+                                       ((6, 5, 4, 5), (3, 2, 2, 3))])
 def test_perturbation_brute_force(size, grid):
     rng = np.random.default_rng(7)
     img = rng.integers(0, 256, size=tuple(reversed(size)) + (3,)).astype(np.uint8)
@@ -286,13 +288,15 @@ def test_seed_lattice_counts():
 # closed form: constant image
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n", [1, 2, 3])
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
 @pytest.mark.parametrize("S", [1, 2, 3, 16])
 @pytest.mark.parametrize("C", [1, 3])
 def test_constant_image_fixed_point(n, S, C):
-    cells = {1: (5,), 2: (4, 3), 3: (3, 2, 2)}[n]
+    cells = {1: (5,), 2: (4, 3), 3: (3, 2, 2), 4: (2, 2, 1, 2)}[n]
     if S == 16 and n == 3:
         cells = (2, 2, 1)
+    if S == 16 and n == 4:
+        cells = (1, 2, 1, 1)
     size = tuple(c * S for c in cells)
     img = np.full(tuple(reversed(size)) + (C,), 77, np.uint8)
     p = O.params_for(img, (S,), m=10.0, max_iter=3, perturb=True, enforce_connectivity=True)
@@ -497,12 +501,12 @@ def _ccl(labels):
     return comp, total
 
 
-@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("seed", range(6))
 def test_connectivity_invariants(seed):
     rng = np.random.default_rng(100 + seed)
-    n = 2 if seed % 2 == 0 else 3
-    size = (30, 26) if n == 2 else (14, 12, 10)
-    grid = (6, 6) if n == 2 else (4, 4, 3)
+    n = (2, 3, 4)[seed % 3]
+    size = {2: (30, 26), 3: (14, 12, 10), 4: (9, 8, 7, 6)}[n]
+    grid = {2: (6, 6), 3: (4, 4, 3), 4: (3, 3, 3, 2)}[n]
     img = rng.integers(0, 256, size=tuple(reversed(size)) + (3,)).astype(np.uint8)
     p = O.params_for(img, grid, m=2.0, max_iter=3, enforce_connectivity=False)
     r = O.slic(p, img)
@@ -591,7 +595,8 @@ def test_lab_grey_axis():
 
 @pytest.mark.parametrize("size,grid,C,mode", [((61,), (4,), 2, O.FP32), ((40, 33), (6, 5), 3, O.FP32),
                                               ((20, 17, 13), (4, 5, 3), 1, O.FP64),
-                                              ((24, 18, 16), (8, 8, 8), 3, O.FP32)])
+                                              ((24, 18, 16), (8, 8, 8), 3, O.FP32),
+                                              ((9, 8, 7, 6), (3, 3, 2, 3), 2, O.FP32)])
 def test_assign_voxels_equals_assign(size, grid, C, mode):
     import _lattice
     rng = np.random.default_rng(sum(size))

@@ -55,7 +55,8 @@ typedef enum { SSLIC_U8 = 0, SSLIC_U16 = 1, SSLIC_F32 = 2 } sslic_dtype;
  * weight m, iteration cap, monitored residual, connectivity on/off, plus
  * seed perturbation on/off (Sec. 3.1 step 1). */
 typedef struct {
-    int32_t ndim;           /* n: 1, 2 or 3 */
+    int32_t ndim;           /* n: 1 to 4 (2-D and 3-D integer and 3-channel float images run
+                             * the tile kernels; the rest the per-voxel kernel) */
     int64_t size[4];        /* N_d (d = 0 fastest); entries >= ndim ignored; 1 <= N_d <= 2^24 */
     int32_t channels;       /* C: 1 .. 256 */
     int32_t dtype;          /* sslic_dtype */

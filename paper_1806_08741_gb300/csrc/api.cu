@@ -77,7 +77,7 @@ static void dfree(P*& p)
 static int validate(const sslic_params* p, Geom* g)
 {
     if (!p) return SSLIC_EINVAL;
-    if (p->ndim < 1 || p->ndim > 3) return SSLIC_EINVAL;
+    if (p->ndim < 1 || p->ndim > kMaxDims) return SSLIC_EINVAL;
     if (p->channels < 1 || p->channels > kMaxChannels) return SSLIC_EINVAL;
     if (p->dtype != SSLIC_U8 && p->dtype != SSLIC_U16 && p->dtype != SSLIC_F32) return SSLIC_EINVAL;
     if (!(p->m > 0.0f) || !std::isfinite(p->m)) return SSLIC_EINVAL;
@@ -95,13 +95,13 @@ static int validate(const sslic_params* p, Geom* g)
     G.n = p->ndim;
     G.C = p->channels;
     G.dtype = p->dtype;
-    G.CW = G.C + 3;
-    G.AW = G.C + 4;
+    G.CW = G.C + (G.n > 3 ? G.n : 3);
+    G.AW = G.CW + 1;
     G.V = 1;
     G.K = 1;
     G.sprod = 1;
     const double m = (double)p->m;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < kMaxDims; ++d) {
         if (d < G.n) {
             if (p->size[d] < 1 || p->size[d] > (1 << 24)) return SSLIC_EINVAL;
             if (p->grid[d] < 1 || p->grid[d] > (1 << 24)) return SSLIC_EINVAL;
@@ -285,7 +285,7 @@ extern "C" {
 
 int sslic_default_params(int32_t ndim, sslic_params* p)
 {
-    if (!p || ndim < 1 || ndim > 3) return SSLIC_EINVAL;
+    if (!p || ndim < 1 || ndim > kMaxDims) return SSLIC_EINVAL;
     memset(p, 0, sizeof(*p));
     p->ndim = ndim;
     for (int d = 0; d < 4; ++d) {

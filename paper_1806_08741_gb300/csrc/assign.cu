@@ -48,7 +48,7 @@ __global__ void assign_voxel_kernel(Geom g, const T* __restrict__ img, const flo
     else nwork = g.V;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwork;
          w += (int64_t)gridDim.x * blockDim.x) {
-        int64_t x, y, z;
+        int64_t x, y, z, u = 0;
         if (tiles) {
             const int64_t t = tiles[w / tv] & ((1LL << 40) - 1);  // low bits: tile, high bits: request
             int e = (int)(w % tv);
@@ -59,9 +59,10 @@ __global__ void assign_voxel_kernel(Geom g, const T* __restrict__ img, const flo
         } else {
             x = w % g.N[0];
             y = (w / g.N[0]) % g.N[1];
-            z = w / (g.N[0] * g.N[1]);
+            z = (w / (g.N[0] * g.N[1])) % g.N[2];
+            u = w / (g.N[0] * g.N[1] * g.N[2]);
         }
-        voxel_assign<T>(g, img, ctr, bin_start, bin_items, labels, acc, facc, x, y, z);
+        voxel_assign<T>(g, img, ctr, bin_start, bin_items, labels, acc, facc, x, y, z, u);
     }
 }
 
@@ -105,19 +106,20 @@ static int launch_voxel(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_
 int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st)
 {
     const Geom& g = c->g;
-    if (g.n >= 2 && g.dtype == SSLIC_U8 && g.C == 3) {
+    const bool tiled = g.n == 2 || g.n == 3;
+    if (tiled && g.dtype == SSLIC_U8 && g.C == 3) {
         return g.n == 3 ? launch_tile_impl<uint8_t, 3, 3>(c, (const uint8_t*)img, labels, st)
                         : launch_tile_impl<uint8_t, 3, 2>(c, (const uint8_t*)img, labels, st);
     }
-    if (g.n >= 2 && g.dtype == SSLIC_U8 && g.C == 1) {
+    if (tiled && g.dtype == SSLIC_U8 && g.C == 1) {
         return g.n == 3 ? launch_tile_impl<uint8_t, 1, 3>(c, (const uint8_t*)img, labels, st)
                         : launch_tile_impl<uint8_t, 1, 2>(c, (const uint8_t*)img, labels, st);
     }
-    if (g.n >= 2 && g.dtype == SSLIC_U16 && g.C == 1) {
+    if (tiled && g.dtype == SSLIC_U16 && g.C == 1) {
         return g.n == 3 ? launch_tile_impl<uint16_t, 1, 3>(c, (const uint16_t*)img, labels, st)
                         : launch_tile_impl<uint16_t, 1, 2>(c, (const uint16_t*)img, labels, st);
     }
-    if (g.n >= 2 && g.dtype == SSLIC_F32 && g.C == 3) {
+    if (tiled && g.dtype == SSLIC_F32 && g.C == 3) {
         return g.n == 3 ? launch_tile_impl<float, 3, 3>(c, (const float*)img, labels, st)
                         : launch_tile_impl<float, 3, 2>(c, (const float*)img, labels, st);
     }

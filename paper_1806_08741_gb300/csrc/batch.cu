@@ -868,6 +868,7 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     int rc = make_geom(p, &g);
     if (rc) return rc;
     if (p->enforce_connectivity) return SSLIC_EUNSUPPORTED;
+    if (g.n > 3) return SSLIC_EUNSUPPORTED;  // the batched tables are laid out for up to three axes
     if (g.K + 1 > (int64_t)kBScanItems * kBScanItems) return SSLIC_EUNSUPPORTED;
     Slot* q = new (std::nothrow) Slot();
     if (!q) return SSLIC_ENOMEM;

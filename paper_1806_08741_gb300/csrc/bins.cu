@@ -112,7 +112,8 @@ __global__ void bin_count_kernel(Geom g, const float* __restrict__ ctr, int* __r
     int64_t b0 = bin_of_coord(p[0], g.S[0], g.nb[0]);
     int64_t b1 = bin_of_coord(p[1], g.S[1], g.nb[1]);
     int64_t b2 = bin_of_coord(p[2], g.S[2], g.nb[2]);
-    int64_t b = b0 + g.nb[0] * (b1 + g.nb[1] * b2);
+    int64_t b3 = g.n >= 4 ? bin_of_coord(p[3], g.S[3], g.nb[3]) : 0;
+    int64_t b = b0 + g.nb[0] * (b1 + g.nb[1] * (b2 + g.nb[2] * b3));
     bin_of[k] = (int)b;
     atomicAdd(&count[b], 1u);
 }

@@ -42,6 +42,10 @@ template <>
 struct CclCfg<2> { static constexpr int TX = 32, TY = 64, TZ = 1; };
 template <>
 struct CclCfg<1> { static constexpr int TX = 2048, TY = 1, TZ = 1; };
+// 4-D: a tile is a 32x8x8 block of one slice along the fourth axis; the
+// tile-local pass is the 3-D one and the slice below adds a fourth face
+template <>
+struct CclCfg<4> { static constexpr int TX = 32, TY = 8, TZ = 8; };
 
 constexpr int kCclThreads = 256;
 constexpr int kCclTV = 2048;
@@ -130,11 +134,23 @@ __device__ __forceinline__ void uf_unite_local(int* par, int a, int b, unsigned*
 }
 
 template <int NDIM>
-__device__ __forceinline__ int64_t ccl_tile_of(const Geom& g, int64_t x, int64_t y, int64_t z, int64_t ntx,
-                                               int64_t nty)
+__device__ __forceinline__ int64_t ccl_tile_of(const Geom& g, int64_t x, int64_t y, int64_t z, int64_t w, int64_t ntx,
+                                               int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
-    return x / Cfg::TX + ntx * (y / Cfg::TY + nty * (z / Cfg::TZ));
+    return x / Cfg::TX + ntx * (y / Cfg::TY + nty * (z / Cfg::TZ + ntz * w));
+}
+
+// origin of tile t (the fourth coordinate is 0 below 4-D)
+template <int NDIM>
+__device__ __forceinline__ void ccl_tile_origin(int64_t t, int64_t ntx, int64_t nty, int64_t ntz, int64_t& X0,
+                                                int64_t& Y0, int64_t& Z0, int64_t& W0)
+{
+    using Cfg = CclCfg<NDIM>;
+    X0 = (t % ntx) * Cfg::TX;
+    Y0 = ((t / ntx) % nty) * Cfg::TY;
+    Z0 = ((t / (ntx * nty)) % ntz) * Cfg::TZ;
+    W0 = t / (ntx * nty * ntz);
 }
 
 // Tile-local components.  The tile is handled as 64 rows of 32 voxels (one
@@ -154,7 +170,7 @@ __global__ void __launch_bounds__(kCclThreads)
 ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restrict__ lid_img,
                  int* __restrict__ tile_base, int* __restrict__ tile_cnt, int* __restrict__ comp_label, unsigned* __restrict__ comp_size,
                  unsigned long long* __restrict__ comp_first, int* __restrict__ gparent,
-                 unsigned* __restrict__ counters, int64_t m_cap, int64_t ntx, int64_t nty)
+                 unsigned* __restrict__ counters, int64_t m_cap, int64_t ntx, int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
@@ -171,7 +187,8 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t tile = blockIdx.x;
-    const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * TZ;
+    int64_t X0, Y0, Z0, W0;
+    ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     const int ex = (int)imin64(TX, g.N[0] - X0);
     const int ey = (int)imin64(TY, g.N[1] - Y0);
     const int ez = (int)imin64(TZ, g.N[2] - Z0);
@@ -185,7 +202,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int e = (warp * RPW + i) * 32 + lane;
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         const bool v = xl < ex && yl < ey && zl < ez;
-        Lr[i] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] : INT_MIN;
+        Lr[i] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl, W0)] : INT_MIN;
     }
 #pragma unroll
     for (int i = 0; i < RPW; ++i) {
@@ -329,7 +346,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const unsigned hm = __ballot_sync(0xffffffffu, head);
         if (r >= 0) {
             const uint16_t l = lidv[r];
-            lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl)] = l;
+            lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl, W0)] = l;
             if (head) {
                 const unsigned later = hm & ~(lt | (1u << lane));
                 const int len = (later ? __ffs(later) - 1 : 32) - lane;
@@ -344,7 +361,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         comp_label[r] = lab[e];
         comp_size[r] = sz[lidv[e]];
-        comp_first[r] = (unsigned long long)vidx(g, X0 + xl, Y0 + yl, Z0 + zl);
+        comp_first[r] = (unsigned long long)vidx(g, X0 + xl, Y0 + yl, Z0 + zl, W0);
         gparent[r] = r;
     }
     if (tid == 0) {
@@ -355,9 +372,9 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
 
 template <int NDIM>
 __device__ __forceinline__ int gid_of(const Geom& g, const uint16_t* lid_img, const int* tile_base, int64_t x,
-                                      int64_t y, int64_t z, int64_t ntx, int64_t nty)
+                                      int64_t y, int64_t z, int64_t w, int64_t ntx, int64_t nty, int64_t ntz)
 {
-    return tile_base[ccl_tile_of<NDIM>(g, x, y, z, ntx, nty)] + (int)lid_img[vidx(g, x, y, z)];
+    return tile_base[ccl_tile_of<NDIM>(g, x, y, z, w, ntx, nty, ntz)] + (int)lid_img[vidx(g, x, y, z, w)];
 }
 
 // Union across the low faces of every tile.  Each face pixel whose label
@@ -366,54 +383,64 @@ __device__ __forceinline__ int gid_of(const Geom& g, const uint16_t* lid_img, co
 // same two labels names the same pair and is skipped, and the remaining
 // pairs are deduplicated in a shared hash set, so each distinct pair of
 // records is united once per tile.
-constexpr int kFaceHash = 2048;  // > 3 faces x 576 pixels / 2: load factor < 1
+// The set holds every key a tile can produce: at most 576 face pixels in
+// 2-D / 3-D; in 4-D another 2048 for the slice below.
+template <int NDIM>
+struct FaceHash {
+    static constexpr int kSize = NDIM == 4 ? 4096 : 2048;
+    static constexpr int kShift = NDIM == 4 ? 20 : 21;  // 32 - log2(kSize)
+};
 
 template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __restrict__ lid_img,
                  const int* __restrict__ tile_base, int* gparent, unsigned* counters, int64_t ntx,
-                 int64_t nty)
+                 int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
-    __shared__ unsigned hset[kFaceHash];
+    constexpr int HS = FaceHash<NDIM>::kSize;
+    __shared__ unsigned hset[HS];
     const int64_t tile = blockIdx.x;
-    const int64_t tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
-    const int64_t X0 = tx * TX, Y0 = ty * TY, Z0 = tz * TZ;
+    int64_t X0, Y0, Z0, W0;
+    ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     const int EX = (int)imin64(TX, g.N[0] - X0), EY = (int)imin64(TY, g.N[1] - Y0), EZ = (int)imin64(TZ, g.N[2] - Z0);
-    for (int i = threadIdx.x; i < kFaceHash; i += kCclThreads) hset[i] = 0u;
+    for (int i = threadIdx.x; i < HS; i += kCclThreads) hset[i] = 0u;
     __syncthreads();
     const int base_here = tile_base[tile];
-    const int64_t sy = g.N[0], sz = g.N[0] * g.N[1];
+    const int64_t sy = g.N[0], sz = g.N[0] * g.N[1], sw4 = sz * g.N[2];
     // the faces that exist (the tile is not on the image's low border there)
-    const bool has[3] = {X0 > 0, NDIM >= 2 && Y0 > 0, NDIM >= 3 && Z0 > 0};
-    const int nf[3] = {has[0] ? EY * EZ : 0, has[1] ? EX * EZ : 0, has[2] ? EX * EY : 0};
-    const int n_all = nf[0] + nf[1] + nf[2];
-    const int64_t p0 = vidx(g, X0, Y0, Z0);
+    const bool has[4] = {X0 > 0, NDIM >= 2 && Y0 > 0, NDIM >= 3 && Z0 > 0, NDIM >= 4 && W0 > 0};
+    const int nf[4] = {has[0] ? EY * EZ : 0, has[1] ? EX * EZ : 0, has[2] ? EX * EY : 0, has[3] ? EX * EY * EZ : 0};
+    const int n_all = nf[0] + nf[1] + nf[2] + nf[3];
+    const int64_t p0 = vidx(g, X0, Y0, Z0, W0);
     // one pixel of one face per thread and step; its loads are issued together
     for (int idx = threadIdx.x; idx < n_all; idx += kCclThreads) {
-        const int d = idx < nf[0] ? 0 : (idx < nf[0] + nf[1] ? 1 : 2);
-        const int i = idx - (d == 0 ? 0 : (d == 1 ? nf[0] : nf[0] + nf[1]));
-        // in-face axes: u (the longer one) and w
+        const int d = idx < nf[0] ? 0 : (idx < nf[0] + nf[1] ? 1 : (idx < nf[0] + nf[1] + nf[2] ? 2 : 3));
+        const int i = idx - (d == 0 ? 0 : (d == 1 ? nf[0] : (d == 2 ? nf[0] + nf[1] : nf[0] + nf[1] + nf[2])));
+        // in-face axes: u (the longer one, x except on the x face) and the rest
         const int nu = d == 0 ? EY : EX;
-        const int64_t su = d == 0 ? sy : 1, sw = d == 2 ? sy : sz;
-        const int64_t st = d == 0 ? 1 : (d == 1 ? sy : sz);
+        const int64_t su = d == 0 ? sy : 1;
+        const int64_t st = d == 0 ? 1 : (d == 1 ? sy : (d == 2 ? sz : sw4));
         const int iu = i % nu, iw = i / nu;
-        const int64_t ia = p0 + iu * su + iw * sw, ib = ia - st;
+        int64_t rest;
+        if (d == 3) rest = (iw % EY) * sy + (iw / EY) * sz;  // the slice face: (y, z) beyond u = x
+        else rest = iw * (d == 2 ? sy : sz);
+        const int64_t ia = p0 + iu * su + rest, ib = ia - st;
         const int64_t ja = iu > 0 ? ia - su : ia, jb = iu > 0 ? ib - su : ib;
         const int L = labels[ia], Lb = labels[ib], La1 = labels[ja], Lb1 = labels[jb];
         const unsigned la = lid_img[ia], lb = lid_img[ib];
         if (L != Lb) continue;
         if (iu > 0 && La1 == L && Lb1 == L) continue;  // same pair as the predecessor along u
-        const int64_t nb = d == 0 ? tile - 1 : (d == 1 ? tile - ntx : tile - ntx * nty);
+        const int64_t nb = d == 0 ? tile - 1 : (d == 1 ? tile - ntx : (d == 2 ? tile - ntx * nty : tile - ntx * nty * ntz));
         const unsigned key = 1u + ((unsigned)d << 22 | la << 11 | lb);
-        unsigned h = (key * 2654435761u) >> 21;  // 11 bits
+        unsigned h = (key * 2654435761u) >> FaceHash<NDIM>::kShift;
         bool fresh = false;
-        for (int probe = 0; probe < kFaceHash; ++probe) {
+        for (int probe = 0; probe < HS; ++probe) {
             const unsigned old = atomicCAS(&hset[h], 0u, key);
             if (old == 0u) { fresh = true; break; }
             if (old == key) break;
-            h = (h + 1) & (kFaceHash - 1);
+            h = (h + 1) & (HS - 1);
         }
         if (fresh) uf_unite(gparent, base_here + (int)la, tile_base[nb] + (int)lb, (int)counters[0], &counters[3]);
     }
@@ -442,32 +469,34 @@ template <int NDIM>
 __global__ void conn_phase1_kernel(Geom g, const float* __restrict__ ctr, const int32_t* __restrict__ labels,
                                    const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
                                    const int* __restrict__ gparent, const unsigned long long* __restrict__ root_size,
-                                   uint8_t* __restrict__ fin, int64_t ntx, int64_t nty)
+                                   uint8_t* __restrict__ fin, int64_t ntx, int64_t nty, int64_t ntz)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= g.K) return;
     const float* pc = ctr + k * g.CW + g.C;
-    int64_t p[3] = {0, 0, 0};
+    int64_t p[kMaxDims] = {0, 0, 0, 0};
     for (int d = 0; d < g.n; ++d) {
         int64_t v = (int64_t)floor((double)pc[d] + 0.5);
         p[d] = v < 0 ? 0 : (v > g.N[d] - 1 ? g.N[d] - 1 : v);
     }
-    int64_t s[3] = {-1, -1, -1};
-    if (labels[vidx(g, p[0], p[1], p[2])] == (int32_t)k) {
-        s[0] = p[0]; s[1] = p[1]; s[2] = p[2];
+    int64_t s[kMaxDims] = {-1, -1, -1, -1};
+    if (labels[vidx(g, p[0], p[1], p[2], p[3])] == (int32_t)k) {
+        for (int d = 0; d < kMaxDims; ++d) s[d] = p[d];
     } else {
-        int64_t lo[3], hi[3];
-        for (int d = 0; d < 3; ++d) {
+        // the S-box around p in raster order, dimension 0 fastest
+        int64_t lo[kMaxDims], hi[kMaxDims];
+        for (int d = 0; d < kMaxDims; ++d) {
             lo[d] = imax64(0, p[d] - g.S[d] / 2);
             hi[d] = imin64(g.N[d] - 1, p[d] + (g.S[d] + 1) / 2 - 1);
         }
-        for (int64_t z = lo[2]; z <= hi[2] && s[0] < 0; ++z)
-            for (int64_t y = lo[1]; y <= hi[1] && s[0] < 0; ++y)
-                for (int64_t x = lo[0]; x <= hi[0]; ++x)
-                    if (labels[vidx(g, x, y, z)] == (int32_t)k) { s[0] = x; s[1] = y; s[2] = z; break; }
+        for (int64_t w = lo[3]; w <= hi[3] && s[0] < 0; ++w)
+            for (int64_t z = lo[2]; z <= hi[2] && s[0] < 0; ++z)
+                for (int64_t y = lo[1]; y <= hi[1] && s[0] < 0; ++y)
+                    for (int64_t x = lo[0]; x <= hi[0]; ++x)
+                        if (labels[vidx(g, x, y, z, w)] == (int32_t)k) { s[0] = x; s[1] = y; s[2] = z; s[3] = w; break; }
     }
     if (s[0] < 0) return;
-    const int G = gparent[gid_of<NDIM>(g, lid_img, tile_base, s[0], s[1], s[2], ntx, nty)];
+    const int G = gparent[gid_of<NDIM>(g, lid_img, tile_base, s[0], s[1], s[2], s[3], ntx, nty, ntz)];
     if (4ull * root_size[G] > (unsigned long long)g.sprod) fin[G] = 1;
 }
 
@@ -482,7 +511,7 @@ __global__ void conn_phase2_kernel(Geom g, const int* __restrict__ gparent, cons
                                    const int* __restrict__ tile_base, int* __restrict__ out_label,
                                    int* __restrict__ link, unsigned long long* __restrict__ new_key,
                                    int* __restrict__ new_val, unsigned* __restrict__ counters, int64_t ntx,
-                                   int64_t nty)
+                                   int64_t nty, int64_t ntz)
 {
     const int64_t M = counters[0];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
@@ -496,13 +525,16 @@ __global__ void conn_phase2_kernel(Geom g, const int* __restrict__ gparent, cons
             out_label[i] = kPendingNew;
             continue;
         }
-        int64_t x[3] = {(int64_t)(f % (unsigned long long)g.N[0]),
-                        (int64_t)((f / (unsigned long long)g.N[0]) % (unsigned long long)g.N[1]),
-                        (int64_t)(f / ((unsigned long long)g.N[0] * (unsigned long long)g.N[1]))};
+        int64_t x[kMaxDims];
+        unsigned long long r = f;
+        for (int d = 0; d < kMaxDims; ++d) {
+            x[d] = (int64_t)(r % (unsigned long long)g.N[d]);
+            r /= (unsigned long long)g.N[d];
+        }
         int d = 0;
         while (x[d] == 0) ++d;
         x[d] -= 1;
-        link[i] = gparent[gid_of<NDIM>(g, lid_img, tile_base, x[0], x[1], x[2], ntx, nty)];
+        link[i] = gparent[gid_of<NDIM>(g, lid_img, tile_base, x[0], x[1], x[2], x[3], ntx, nty, ntz)];
         out_label[i] = kPendingMerge;
     }
 }
@@ -593,14 +625,15 @@ __global__ void __launch_bounds__(kCclThreads)
 conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
                     const int* __restrict__ tile_cnt, const int* __restrict__ gparent,
                     const int* __restrict__ out_label, const int* __restrict__ comp_label,
-                    int32_t* __restrict__ labels_out, int inplace, int64_t ntx, int64_t nty)
+                    int32_t* __restrict__ labels_out, int inplace, int64_t ntx, int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY;
     __shared__ int tab[kCclTV];       // local component -> output label
     __shared__ uint8_t chg[kCclTV];   // ... and whether it differs from the input label
     const int64_t tile = blockIdx.x;
-    const int64_t X0 = (tile % ntx) * TX, Y0 = ((tile / ntx) % nty) * TY, Z0 = (tile / (ntx * nty)) * Cfg::TZ;
+    int64_t X0, Y0, Z0, W0;
+    ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     const int base = tile_base[tile];
     const int nloc = tile_cnt[tile];
     int any = 0;
@@ -623,7 +656,7 @@ conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __r
         const int e = threadIdx.x + i * kCclThreads;
         const int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
         const bool in = x < g.N[0] && y < g.N[1] && z < g.N[2];
-        qv[i] = in ? vidx(g, x, y, z) : -1;
+        qv[i] = in ? vidx(g, x, y, z, W0) : -1;
         lv[i] = in ? (int)lid_img[qv[i]] : 0;
     }
 #pragma unroll
@@ -642,7 +675,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     const int64_t ntx = (g.N[0] + Cfg::TX - 1) / Cfg::TX;
     const int64_t nty = (g.N[1] + Cfg::TY - 1) / Cfg::TY;
     const int64_t ntz = (g.N[2] + Cfg::TZ - 1) / Cfg::TZ;
-    const int64_t ntiles = ntx * nty * ntz;
+    const int64_t ntiles = ntx * nty * ntz * g.N[3];  // one slice of tiles per index along a fourth axis
     int rc;
     unsigned hc[4];
     const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
@@ -650,7 +683,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
         if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
         ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
                                                               w.comp_label, w.comp_size, w.comp_first, w.gparent,
-                                                              w.counters, w.m_cap, ntx, nty);
+                                                              w.counters, w.m_cap, ntx, nty, ntz);
         count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
         if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -667,7 +700,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     if ((rc = cuda_check(c, cudaMemsetAsync(w.root_first, 0xff, M * sizeof(unsigned long long), st), "memset"))) return rc;
     if ((rc = cuda_check(c, cudaMemsetAsync(w.fin, 0, M, st), "memset"))) return rc;
     ccl_faces_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.gparent,
-                                                           w.counters, ntx, nty);
+                                                           w.counters, ntx, nty, ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     const int gb = c->sms * 8;
@@ -678,12 +711,12 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
     conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,
-                                                                 w.gparent, w.root_size, w.fin, ntx, nty);
+                                                                 w.gparent, w.root_size, w.fin, ntx, nty, ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase1_kernel"))) return rc;
     conn_phase2_kernel<NDIM><<<gm, 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
                                                   w.lid, w.tile_base, w.out_label, w.link, w.new_key, w.new_val,
-                                                  w.counters, ntx, nty);
+                                                  w.counters, ntx, nty, ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase2_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -731,7 +764,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
     conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,
                                                               w.out_label, w.comp_label, labels_out,
-                                                              labels_in == labels_out ? 1 : 0, ntx, nty);
+                                                              labels_in == labels_out ? 1 : 0, ntx, nty, ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -746,6 +779,11 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
 
 int64_t ccl_num_tiles(const Geom& g)
 {
+    if (g.n == 4) {
+        using C4 = CclCfg<4>;
+        return ((g.N[0] + C4::TX - 1) / C4::TX) * ((g.N[1] + C4::TY - 1) / C4::TY) * ((g.N[2] + C4::TZ - 1) / C4::TZ) *
+               g.N[3];
+    }
     if (g.n == 3) {
         using C3 = CclCfg<3>;
         return ((g.N[0] + C3::TX - 1) / C3::TX) * ((g.N[1] + C3::TY - 1) / C3::TY) * ((g.N[2] + C3::TZ - 1) / C3::TZ);
@@ -761,6 +799,7 @@ int run_connectivity(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out
                      int64_t* num_labels)
 {
     switch (c->g.n) {
+    case 4: return connectivity_impl<4>(c, labels_in, labels_out, st, num_labels);
     case 3: return connectivity_impl<3>(c, labels_in, labels_out, st, num_labels);
     case 2: return connectivity_impl<2>(c, labels_in, labels_out, st, num_labels);
     default: return connectivity_impl<1>(c, labels_in, labels_out, st, num_labels);

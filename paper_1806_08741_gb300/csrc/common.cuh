@@ -21,20 +21,22 @@ namespace sslic {
 constexpr int kMaxChannels = 256;
 constexpr uint8_t kNoSlot = 255;
 
+constexpr int kMaxDims = 4;  // images of 1 to 4 dimensions (the paper's filter is n-dimensional, Sec. 3)
+
 struct Geom {
-    int n;            // real spatial dims (1..3)
-    int64_t N[3];     // sizes, padded with 1
-    int S[3];         // grid, padded with 1
-    int64_t nb[3];    // seeds (= bins) per axis: ceil(N_d / S_d)
-    int64_t off[3];   // lattice offset o_d = floor((N_d - 1 - (nb_d - 1) S_d) / 2)
+    int n;                // real spatial dims (1..4)
+    int64_t N[kMaxDims];  // sizes, padded with 1
+    int S[kMaxDims];      // grid, padded with 1
+    int64_t nb[kMaxDims]; // seeds (= bins) per axis: ceil(N_d / S_d)
+    int64_t off[kMaxDims];// lattice offset o_d = floor((N_d - 1 - (nb_d - 1) S_d) / 2)
     int64_t V, K;
-    int C;            // channels
-    int dtype;        // SSLIC_U8 / SSLIC_U16 / SSLIC_F32
-    int CW;           // internal centre row width C + 3
-    int AW;           // accumulator row width C + 4 (features, x, y, z, count)
-    float w[3];       // fl32(m^2 / S_d^2)
-    double w64[3];    // m^2 / S_d^2
-    int64_t sprod;    // prod S_d over the real axes
+    int C;                // channels
+    int dtype;            // SSLIC_U8 / SSLIC_U16 / SSLIC_F32
+    int CW;               // internal centre row width C + P, P = max(3, n) position slots
+    int AW;               // accumulator row width C + P + 1 (features, positions, count last)
+    float w[kMaxDims];    // fl32(m^2 / S_d^2)
+    double w64[kMaxDims]; // m^2 / S_d^2
+    int64_t sprod;        // prod S_d over the real axes
 };
 
 // ---- packed FP32 pairs (sm_100 family .f32x2 arithmetic, round to nearest) --
@@ -71,9 +73,9 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
-__host__ __device__ __forceinline__ int64_t vidx(const Geom& g, int64_t x, int64_t y, int64_t z)
+__host__ __device__ __forceinline__ int64_t vidx(const Geom& g, int64_t x, int64_t y, int64_t z, int64_t w = 0)
 {
-    return x + g.N[0] * (y + g.N[1] * z);
+    return x + g.N[0] * (y + g.N[1] * (z + g.N[2] * w));
 }
 
 // Covered range of a centre coordinate c along an axis of grid S: the voxels

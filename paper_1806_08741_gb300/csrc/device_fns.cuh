@@ -7,35 +7,36 @@ namespace sslic {
 
 constexpr float kInfF = __builtin_huge_valf();
 
-// Assignment + map-update of one voxel (x, y, z) by direct search: the 3^n
+// Assignment + map-update of one voxel (x, y, z, w) by direct search: the 3^n
 // bins around it, the exact window test, the canonical single-precision D^2
 // (Sec. 2.1, one rounding per operation, no FMA) and a lexicographic (D^2, k)
 // comparison, so the bin visiting order does not matter.  Sums go to the
-// cluster's row of acc (uint64: features of integer images, x, y, z, count)
-// and facc (double features of float images).
+// cluster's row of acc (uint64: features of integer images, positions,
+// count last) and facc (double features of float images).
 template <typename T>
 __device__ __forceinline__ void voxel_assign(const Geom& g, const T* __restrict__ img,
                                              const float* __restrict__ ctr,
                                              const unsigned* __restrict__ bin_start,
                                              const int* __restrict__ bin_items, int32_t* __restrict__ labels,
                                              unsigned long long* __restrict__ acc, double* __restrict__ facc,
-                                             int64_t x, int64_t y, int64_t z)
+                                             int64_t x, int64_t y, int64_t z, int64_t w = 0)
 {
     const int C = g.C;
     constexpr float kInf = kInfF;
-    const int64_t q = vidx(g, x, y, z);
-    const int64_t X[3] = {x, y, z};
-    int64_t blo[3], bhi[3];
-    for (int d = 0; d < 3; ++d) {
+    const int64_t q = vidx(g, x, y, z, w);
+    const int64_t X[kMaxDims] = {x, y, z, w};
+    int64_t blo[kMaxDims], bhi[kMaxDims];
+    for (int d = 0; d < kMaxDims; ++d) {
         blo[d] = imax64(0, X[d] / g.S[d] - 1);
         bhi[d] = imin64(g.nb[d] - 1, X[d] / g.S[d] + 1);
     }
     float best = kInf;
     int bestk = -1;
+    for (int64_t bw = blo[3]; bw <= bhi[3]; ++bw)
     for (int64_t bz = blo[2]; bz <= bhi[2]; ++bz)
         for (int64_t by = blo[1]; by <= bhi[1]; ++by)
             for (int64_t bx = blo[0]; bx <= bhi[0]; ++bx) {
-                int64_t bin = bx + g.nb[0] * (by + g.nb[1] * bz);
+                int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (bz + g.nb[2] * bw));
                 for (unsigned i = bin_start[bin]; i < bin_start[bin + 1]; ++i) {
                     const int k = bin_items[i];
                     const float* row = ctr + (int64_t)k * g.CW;
@@ -68,10 +69,8 @@ __device__ __forceinline__ void voxel_assign(const Geom& g, const T* __restrict_
             if (sizeof(T) == 4) atomicAdd(&facc[(int64_t)bestk * C + c], (double)img[q * C + c]);
             else atomicAdd(&a[c], (unsigned long long)img[q * C + c]);
         }
-        atomicAdd(&a[C], (unsigned long long)x);
-        atomicAdd(&a[C + 1], (unsigned long long)y);
-        atomicAdd(&a[C + 2], (unsigned long long)z);
-        atomicAdd(&a[C + 3], 1ull);
+        for (int d = 0; d < g.CW - C; ++d) atomicAdd(&a[C + d], (unsigned long long)X[d]);
+        atomicAdd(&a[g.AW - 1], 1ull);
     }
 }
 
@@ -83,7 +82,7 @@ __device__ __forceinline__ int64_t grad_int(const Geom& g, const T* img, const i
     int64_t acc = 0;
     for (int c = 0; c < g.C; ++c) {
         for (int d = 0; d < g.n; ++d) {
-            int64_t st = d == 0 ? 1 : (d == 1 ? g.N[0] : g.N[0] * g.N[1]);
+            int64_t st = d == 0 ? 1 : (d == 1 ? g.N[0] : (d == 2 ? g.N[0] * g.N[1] : g.N[0] * g.N[1] * g.N[2]));
             int64_t hi = x[d] + 1 < g.N[d] ? q + st : q;
             int64_t lo = x[d] > 0 ? q - st : q;
             int64_t diff = (int64_t)img[hi * g.C + c] - (int64_t)img[lo * g.C + c];
@@ -99,7 +98,7 @@ __device__ __forceinline__ float grad_f32(const Geom& g, const float* img, const
     bool first = true;
     for (int c = 0; c < g.C; ++c) {
         for (int d = 0; d < g.n; ++d) {
-            int64_t st = d == 0 ? 1 : (d == 1 ? g.N[0] : g.N[0] * g.N[1]);
+            int64_t st = d == 0 ? 1 : (d == 1 ? g.N[0] : (d == 2 ? g.N[0] * g.N[1] : g.N[0] * g.N[1] * g.N[2]));
             int64_t hi = x[d] + 1 < g.N[d] ? q + st : q;
             int64_t lo = x[d] > 0 ? q - st : q;
             float diff = __fsub_rn(img[hi * g.C + c], img[lo * g.C + c]);
@@ -115,30 +114,32 @@ template <typename T>
 __device__ __forceinline__ void seed_one(const Geom& g, const T* __restrict__ img, float* __restrict__ ctr,
                                          int perturb, int64_t k)
 {
-    int64_t x[3];
+    int64_t x[kMaxDims];
     int64_t rem = k;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < kMaxDims; ++d) {
         int64_t j = rem % g.nb[d];
         rem /= g.nb[d];
         x[d] = g.off[d] + j * g.S[d];
     }
-    int64_t best[3] = {x[0], x[1], x[2]};
+    int64_t best[kMaxDims] = {x[0], x[1], x[2], x[3]};
     if (perturb) {
-        int64_t q0 = vidx(g, x[0], x[1], x[2]);
+        int64_t q0 = vidx(g, x[0], x[1], x[2], x[3]);
         constexpr bool kFloat = sizeof(T) == 4;
         int64_t bi = 0;
         float bf = 0.0f;
         if constexpr (kFloat) bf = grad_f32(g, (const float*)img, x, q0);
         else bi = grad_int(g, img, x, q0);
-        const int lo2 = g.n >= 3 ? -1 : 0, lo1 = g.n >= 2 ? -1 : 0;
+        // the 3^n offsets in raster order, dimension 0 fastest
+        const int lo3 = g.n >= 4 ? -1 : 0, lo2 = g.n >= 3 ? -1 : 0, lo1 = g.n >= 2 ? -1 : 0;
+        for (int o3 = lo3; o3 <= -lo3; ++o3)
         for (int o2 = lo2; o2 <= -lo2; ++o2)
             for (int o1 = lo1; o1 <= -lo1; ++o1)
                 for (int o0 = -1; o0 <= 1; ++o0) {
-                    int64_t y[3] = {x[0] + o0, x[1] + o1, x[2] + o2};
-                    if (y[0] < 0 || y[0] >= g.N[0] || y[1] < 0 || y[1] >= g.N[1] || y[2] < 0 ||
-                        y[2] >= g.N[2])
-                        continue;
-                    int64_t q = vidx(g, y[0], y[1], y[2]);
+                    int64_t y[kMaxDims] = {x[0] + o0, x[1] + o1, x[2] + o2, x[3] + o3};
+                    bool inside = true;
+                    for (int d = 0; d < kMaxDims; ++d) inside = inside && y[d] >= 0 && y[d] < g.N[d];
+                    if (!inside) continue;
+                    int64_t q = vidx(g, y[0], y[1], y[2], y[3]);
                     bool better;
                     if constexpr (kFloat) {
                         float gq = grad_f32(g, (const float*)img, y, q);
@@ -149,13 +150,14 @@ __device__ __forceinline__ void seed_one(const Geom& g, const T* __restrict__ im
                         better = gq < bi;
                         if (better) bi = gq;
                     }
-                    if (better) { best[0] = y[0]; best[1] = y[1]; best[2] = y[2]; }
+                    if (better)
+                        for (int d = 0; d < kMaxDims; ++d) best[d] = y[d];
                 }
     }
-    int64_t qb = vidx(g, best[0], best[1], best[2]);
+    int64_t qb = vidx(g, best[0], best[1], best[2], best[3]);
     float* row = ctr + k * g.CW;
     for (int c = 0; c < g.C; ++c) row[c] = (float)img[qb * g.C + c];
-    for (int d = 0; d < 3; ++d) row[g.C + d] = (float)best[d];
+    for (int d = 0; d < g.CW - g.C; ++d) row[g.C + d] = (float)best[d];
 }
 
 // ---- reduce step of the update (Sec. 3.1): centre k = sum / count, divided in
@@ -167,7 +169,7 @@ __device__ __forceinline__ void finalize_one(const Geom& g, float* __restrict__ 
                                              int64_t k, double* __restrict__ rk, unsigned* __restrict__ ne)
 {
     unsigned long long* a = acc + k * g.AW;
-    const unsigned long long cnt = a[g.C + 3];
+    const unsigned long long cnt = a[g.AW - 1];
     float* row = ctr + k * g.CW;
     double r = 0.0;
     if (cnt) {

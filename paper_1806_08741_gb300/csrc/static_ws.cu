@@ -89,6 +89,7 @@ extern "C" int sslic_iterate_static(const sslic_params* p, const void* image_dev
     Geom g;
     int rc = make_geom(p, &g);
     if (rc) return rc;
+    if (g.n > 3) return SSLIC_EUNSUPPORTED;  // the array's centre rows hold three positions
     if (g.K > stat::kMaxK || g.C > stat::kMaxC || assign_num_tiles(g) > stat::kMaxTiles ||
         scan_tmp_needed(g.K + 1) > stat::kScanTmp)
         return SSLIC_EINVAL;  // beyond the array's stated maximum sizes

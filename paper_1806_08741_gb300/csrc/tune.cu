@@ -27,8 +27,8 @@ TuneKey key_of(const Geom& g) { return TuneKey(g.dtype, g.C, g.n, g.S[0], g.S[1]
 
 bool has_tile_kernel(const Geom& g)
 {
-    return g.n >= 2 && ((g.dtype == SSLIC_U8 && (g.C == 1 || g.C == 3)) || (g.dtype == SSLIC_U16 && g.C == 1) ||
-                        (g.dtype == SSLIC_F32 && g.C == 3));
+    return (g.n == 2 || g.n == 3) && ((g.dtype == SSLIC_U8 && (g.C == 1 || g.C == 3)) ||
+                                      (g.dtype == SSLIC_U16 && g.C == 1) || (g.dtype == SSLIC_F32 && g.C == 3));
 }
 
 int tuned_tile_shape(const Geom& g)

@@ -56,7 +56,7 @@ def test_host_only_calls(lib):
     assert lib.sslic_last_error(None) == b""
 
 
-@pytest.mark.parametrize("field,value", [("ndim", 0), ("ndim", 4), ("channels", 0),
+@pytest.mark.parametrize("field,value", [("ndim", 0), ("ndim", 5), ("channels", 0),
                                          ("channels", 300), ("dtype", 5), ("m", 0.0),
                                          ("m", float("nan")), ("max_iter", 0), ("perturb", 2),
                                          ("precision", 7)])

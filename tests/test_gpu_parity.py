@@ -469,3 +469,57 @@ def test_invalid_calls_raise():
         with pytest.raises(ValueError):
             ctx.run(_dev(img), torch.empty(5, dtype=torch.int32, device="cuda"))
         assert ctx.lib.sslic_run(ctx._c, None, None, None, None, None) == -1
+
+
+# ---------------------------------------------------------------------------
+# 4-D images (the paper's filter is n-dimensional, Sec. 3): per-voxel kernel,
+# 4-D bins, 3^4 perturbation, 4-D connectivity
+# ---------------------------------------------------------------------------
+def _blocky4d(size, C, dtype, seed):
+    """Piecewise-constant blocks (a few voxels per axis) plus noise."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(reversed(size))
+    hi = 256 if dtype == np.uint8 else (65536 if dtype == np.uint16 else 1.0)
+    blocks = [max(1, s // 5) for s in shape]
+    base = rng.uniform(0, hi, size=tuple(blocks) + (C,))
+    idx = np.ix_(*[np.minimum(np.arange(s) * b // s, b - 1) for s, b in zip(shape, blocks)])
+    img = base[idx] + rng.normal(0, 0.04 * hi, size=shape + (C,))
+    if dtype == np.float32:
+        return img.astype(np.float32)
+    return np.clip(np.rint(img), 0, hi - 1).astype(dtype)
+
+
+CASES_4D = [("u8_rgb", (20, 18, 14, 12), (6, 6, 5, 4), 3, np.uint8),
+            ("u16_ragged_aniso", (17, 13, 11, 9), (5, 4, 3, 4), 1, np.uint16),
+            ("u8_small_grid", (12, 10, 9, 8), (2, 3, 2, 2), 2, np.uint8)]
+
+
+@pytest.mark.parametrize("name,size,grid,C,dtype", CASES_4D, ids=[c[0] for c in CASES_4D])
+def test_4d_parity(name, size, grid, C, dtype):
+    img = _blocky4d(size, C, dtype, sum(size))
+    # seeds (3^4 perturbation)
+    np.testing.assert_array_equal(_gpu_seed(img, grid, perturb=True), O.seed(O.params_for(img, grid), img))
+    # one iteration from the oracle's centres after two iterations
+    p = O.params_for(img, grid, m=10.0, max_iter=2)
+    cen = O.slic(p, img)["centres"]
+    lab, cout, _ = _gpu_iterate(img, grid, cen)
+    np.testing.assert_array_equal(lab, O.assign(p, img, cen))
+    ref_c, _, _ = O.update(p, img, lab, cen)
+    np.testing.assert_array_equal(cout, ref_c)
+    # whole runs, with and without connectivity
+    for conn in (False, True):
+        kw = dict(m=10.0, max_iter=5, perturb=True, enforce_connectivity=conn)
+        ref = O.slic(O.params_for(img, grid, **kw), img)
+        lab, cen, info = _gpu_run(img, grid, **kw)
+        np.testing.assert_array_equal(lab, ref["labels"])
+        np.testing.assert_array_equal(cen, ref["centres"])
+        assert info["num_labels"] == ref["num_labels"]
+
+
+def test_4d_float_assignment_is_fp32_canonical():
+    img = _blocky4d((16, 14, 12, 10), 2, np.float32, 4)
+    grid = (5, 5, 4, 4)
+    p = O.params_for(img, grid, m=0.5, max_iter=2)
+    cen = O.slic(p, img)["centres"]
+    lab, _, _ = _gpu_iterate(img, grid, cen, m=0.5)
+    np.testing.assert_array_equal(lab, O.assign(p, img, cen))

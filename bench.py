@@ -331,6 +331,10 @@ def run_ours(args, w):
                "ms_per_step": dt * 1e3, "ms_per_call": calls, "labels_equal_device_run": same}
         del h_img, h_lab, h_cen
 
+    streamed = None
+    if rank == 0 and world == 1 and not args.no_streamed:
+        streamed = streamed_bench(w, img, args.slab_planes)
+
     lab = None
     if rank == 0 and world == 1 and not args.no_lab and spec.dtype == "u8" and spec.channels == 3:
         lab = lab_bench(w, img, labels, steps=max(3, min(args.steps, 5)), warmup=1)
@@ -360,7 +364,7 @@ def run_ours(args, w):
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
             "tile_shape": tune, "assign_update_loop": loop,
             "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
-            "precision": precision, "lab": lab,
+            "precision": precision, "lab": lab, "streamed": streamed,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -368,6 +372,47 @@ def run_ours(args, w):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# streamed form: the image in host memory, streamed through the GPU in slabs
+# ---------------------------------------------------------------------------
+def streamed_bench(w, img, slab_planes, runs=2):
+    """The workload through sslic_run_streamed (the out-of-device-memory form;
+    no connectivity enforcement): the image stays in page-locked host memory
+    and every iteration uploads it slab by slab; the last iteration's labels
+    come back.  Whole runs timed on the host clock (the call is synchronous),
+    with the labels checked against a resident run of the same parameters."""
+    import torch
+
+    from paper_1806_08741_gb300 import sslic as S
+
+    spec = w.image
+    V = spec.voxels
+    h_img = torch.empty(spec.shape, dtype=img.dtype, pin_memory=True)
+    h_img.copy_(img)
+    h_lab = torch.empty(spec.shape[:-1], dtype=torch.int32, pin_memory=True)
+    p = S.params_for(img, w.grid, m=w.m, max_iter=w.max_iter, perturb=w.perturb, enforce_connectivity=False)
+    out = {"slab_planes": slab_planes, "connectivity": False}
+    with S.Context(p) as ctx:
+        h_cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, pin_memory=True)
+        ctx.run_streamed(h_img, h_lab, h_cen, slab_planes=slab_planes)   # warm-up (allocates the slabs)
+        ts = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            info = ctx.run_streamed(h_img, h_lab, h_cen, slab_planes=slab_planes)
+            ts.append(time.perf_counter() - t0)
+        dt = sorted(ts)[len(ts) // 2]
+        lab = torch.empty(spec.shape[:-1], dtype=torch.int32, device=img.device)
+        ctx.run(img, lab, torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device=img.device))
+        same = bool(torch.equal(h_lab, lab.cpu()))
+    it = info["iterations"]
+    out.update({"value": V * it / dt / 1e9, "unit": UNIT, "ms_per_run": dt * 1e3, "iterations": it,
+                "h2d_bytes_per_run": int(h_img.numel() * h_img.element_size()) * it,
+                "d2h_bytes_per_run": int(h_lab.numel() * 4), "labels_equal_resident_run": same})
+    del h_img, h_lab
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -632,6 +677,8 @@ def main():
     ap.add_argument("--no-precision", action="store_true", help="skip the 64-band float workload")
     ap.add_argument("--precision-only", action="store_true", help="only the 64-band float workload")
     ap.add_argument("--no-lab", action="store_true", help="skip the CIE-Lab float form of the workload")
+    ap.add_argument("--no-streamed", action="store_true", help="skip the streamed (host-resident image) form")
+    ap.add_argument("--slab-planes", type=int, default=128, help="planes per slab of the streamed form")
     ap.add_argument("--lab-only", action="store_true",
                     help="only the CIE-Lab float form of the workload (--tile-shape fixes its shape)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

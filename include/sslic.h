@@ -122,6 +122,32 @@ SSLIC_API int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labe
 /* Step entry points (the rows of the method, for parity tests and callers
  * that drive the loop themselves).  All device pointers, stream ordered. */
 
+/* Streamed form, for volumes larger than device memory (the paper's
+ * motivating several-GB images, Sec. 1; its 53 GB Lab volume, Sec. 4.1):
+ * the image stays in host memory and every iteration streams it through the
+ * GPU in slabs of slab_planes planes along its last axis (z in 3-D, y in
+ * 2-D), two slab buffers deep, so the upload of one slab overlaps the
+ * assignment of the other.  Assignment is voxel-centric and needs only the
+ * centres and their bins, which stay on the device, so slabs need no halo
+ * (seeding reads two planes on either side); each slab adds its exact sums
+ * to the centres' sums, so integer images give the labels and centres of
+ * sslic_run bit for bit.  Device memory: the context's centres, sums and
+ * bins plus two slabs (image planes + int32 labels).
+ *   image_host   the whole image (layout as sslic_run), host memory;
+ *                page-locked memory overlaps best
+ *   labels_host  receives the final labels (host, V int32)
+ *   centres_host receives the final centres (host, K x (C+n) float, may be NULL)
+ *   slab_planes  planes per slab: a positive multiple of 32
+ *   stream       cudaStream_t for the kernels (a copy stream of the context
+ *                carries the transfers), or NULL for the legacy default stream
+ * 2-D and 3-D images without connectivity enforcement or the precision form
+ * (else SSLIC_EUNSUPPORTED); float images with 16 or more channels take the
+ * per-voxel kernel here.  Synchronous: returns when the labels are in
+ * labels_host.  Errors: SSLIC_EINVAL (pointers, slab_planes), SSLIC_ENOMEM,
+ * SSLIC_ECUDA, SSLIC_EBUSY. */
+SSLIC_API int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_host, float* centres_host,
+                                 int64_t slab_planes, void* stream, sslic_result* out);
+
 /* Seeding on the lattice plus optional perturbation (Sec. 2.2 / 3.1 step 1).
  * centres_dev: K x (C+n) float32, written. */
 SSLIC_API int sslic_seed(sslic_ctx* c, const void* image_dev, float* centres_dev, void* stream);

@@ -174,6 +174,10 @@ static void free_all(sslic_ctx* c)
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
     dfree(w.new_key); dfree(w.new_val); dfree(w.sort_key); dfree(w.sort_val);
     dfree(w.img_dev); dfree(w.lab_dev); dfree(w.cen_dev);
+    for (int i = 0; i < 2; ++i) { dfree(w.slab_img[i]); dfree(w.slab_lab[i]); }
+    for (int i = 0; i < 8; ++i)
+        if (w.slab_ev[i]) { cudaEventDestroy(w.slab_ev[i]); w.slab_ev[i] = nullptr; }
+    if (w.copy_stream) { cudaStreamDestroy(w.copy_stream); w.copy_stream = nullptr; }
 }
 
 static int alloc_core(sslic_ctx* c)
@@ -391,6 +395,127 @@ int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host, f
         return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
     if (out) *out = r;
+    return SSLIC_OK;
+}
+
+int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_host, float* centres_host,
+                       int64_t slab_planes, void* stream, sslic_result* out)
+{
+    if (!c || !image_host || !labels_host) return SSLIC_EINVAL;
+    const Geom& g = c->g;
+    if (g.n != 2 && g.n != 3) return set_error(c, SSLIC_EUNSUPPORTED, "streamed form: 2-D and 3-D images");
+    if (c->p.enforce_connectivity || c->p.precision)
+        return set_error(c, SSLIC_EUNSUPPORTED, "streamed form: no connectivity enforcement or precision form");
+    if (slab_planes < 32 || slab_planes % 32 != 0)
+        return set_error(c, SSLIC_EINVAL, "slab depth must be a positive multiple of 32 planes");
+    Busy b(c);
+    if (!b.ok) return SSLIC_EBUSY;
+    Workspace& w = c->ws;
+    const int ax = g.n - 1;                      // the last axis: slabs are ranges of its planes
+    const int64_t NL = g.N[ax];
+    int64_t plane = 1;
+    for (int d = 0; d < ax; ++d) plane *= g.N[d];
+    const size_t esz = g.dtype == SSLIC_U8 ? 1 : (g.dtype == SSLIC_U16 ? 2 : 4);
+    const size_t pbytes = (size_t)plane * g.C * esz;  // image bytes per plane
+    const int64_t depth = imin64(slab_planes, NL);
+    int rc;
+    if (w.slab_planes < depth + 4) {
+        for (int i = 0; i < 2; ++i) { dfree(w.slab_img[i]); dfree(w.slab_lab[i]); }
+        w.slab_planes = 0;
+        for (int i = 0; i < 2; ++i) {
+            if ((rc = dalloc(c, &w.slab_img[i], (size_t)(depth + 4) * pbytes, "slab buffers"))) return rc;
+            if ((rc = dalloc(c, &w.slab_lab[i], (size_t)depth * plane, "slab buffers"))) return rc;
+        }
+        w.slab_planes = depth + 4;
+    }
+    if (!w.copy_stream &&
+        (rc = cuda_check(c, cudaStreamCreateWithFlags(&w.copy_stream, cudaStreamNonBlocking), "copy stream")))
+        return rc;
+    for (int i = 0; i < 8; ++i)
+        if (!w.slab_ev[i] &&
+            (rc = cuda_check(c, cudaEventCreateWithFlags(&w.slab_ev[i], cudaEventDisableTiming), "events")))
+            return rc;
+    cudaStream_t st = (cudaStream_t)stream, cs = w.copy_stream;
+    cudaEvent_t* img_ready = w.slab_ev;      // [2]: recorded on cs after a buffer's upload
+    cudaEvent_t* img_free = w.slab_ev + 2;   // [2]: recorded on st after the kernels that read it
+    cudaEvent_t* lab_done = w.slab_ev + 4;   // [2]: recorded on st after the kernels that write it
+    cudaEvent_t* lab_free = w.slab_ev + 6;   // [2]: recorded on cs after its download
+    for (int i = 0; i < 2; ++i) {
+        if ((rc = cuda_check(c, cudaEventRecord(img_free[i], st), "event"))) return rc;
+        if ((rc = cuda_check(c, cudaEventRecord(lab_free[i], st), "event"))) return rc;
+    }
+    const int64_t nslab = (NL + depth - 1) / depth;
+    // upload planes [a, b) of the image into buffer i, after its previous readers
+    auto upload = [&](int i, int64_t a, int64_t bnd) -> int {
+        int r;
+        if ((r = cuda_check(c, cudaStreamWaitEvent(cs, img_free[i], 0), "wait"))) return r;
+        if ((r = cuda_check(c, cudaMemcpyAsync(w.slab_img[i], (const unsigned char*)image_host + a * pbytes,
+                                               (size_t)(bnd - a) * pbytes, cudaMemcpyHostToDevice, cs),
+                            "slab upload")))
+            return r;
+        if ((r = cuda_check(c, cudaEventRecord(img_ready[i], cs), "event"))) return r;
+        return cuda_check(c, cudaStreamWaitEvent(st, img_ready[i], 0), "wait");
+    };
+    // seeding: each slab with the two planes on either side its gradients reach
+    for (int64_t s = 0; s < nslab; ++s) {
+        const int i = (int)(s & 1);
+        const int64_t lo = s * depth, hi = imin64(NL, lo + depth);
+        const int64_t a = imax64(0, lo - 2), bnd = imin64(NL, hi + 2);
+        if ((rc = upload(i, a, bnd))) return rc;
+        const Slab sl{lo, hi};
+        if ((rc = launch_seed(c, w.slab_img[i] - a * pbytes, st, &sl))) return rc;
+        if ((rc = cuda_check(c, cudaEventRecord(img_free[i], st), "event"))) return rc;
+    }
+    // iterations: every slab's assignment adds its exact sums to the centres' sums
+    int it = 0;
+    double res = 0.0;
+    const bool thr = c->p.conv_threshold > 0.0;
+    for (it = 0; it < c->p.max_iter; ++it) {
+        const bool keep = thr || it == c->p.max_iter - 1;  // labels that may be the result go back
+        if ((rc = build_bins(c, st))) return rc;
+        for (int64_t s = 0; s < nslab; ++s) {
+            const int i = (int)(s & 1);
+            const int64_t lo = s * depth, hi = imin64(NL, lo + depth);
+            if ((rc = upload(i, lo, hi))) return rc;
+            if ((rc = cuda_check(c, cudaStreamWaitEvent(st, lab_free[i], 0), "wait"))) return rc;
+            const Slab sl{lo, hi};
+            if ((rc = launch_assign_update(c, w.slab_img[i] - lo * pbytes, w.slab_lab[i] - lo * plane, st, &sl)))
+                return rc;
+            if ((rc = cuda_check(c, cudaEventRecord(img_free[i], st), "event"))) return rc;
+            if ((rc = cuda_check(c, cudaEventRecord(lab_done[i], st), "event"))) return rc;
+            if (keep) {
+                if ((rc = cuda_check(c, cudaStreamWaitEvent(cs, lab_done[i], 0), "wait"))) return rc;
+                if ((rc = cuda_check(c, cudaMemcpyAsync(labels_host + lo * plane, w.slab_lab[i],
+                                                        (size_t)(hi - lo) * plane * sizeof(int32_t),
+                                                        cudaMemcpyDeviceToHost, cs),
+                                     "slab labels")))
+                    return rc;
+                if ((rc = cuda_check(c, cudaEventRecord(lab_free[i], cs), "event"))) return rc;
+            }
+        }
+        if ((rc = launch_finalize(c, st))) return rc;
+        if (thr) {
+            if ((rc = read_residual(c, st, &res))) return rc;
+            if (res < c->p.conv_threshold) { ++it; break; }
+        }
+    }
+    if (centres_host) {
+        if (!w.cen_dev && (rc = dalloc(c, &w.cen_dev, (size_t)g.K * (g.C + g.n), "centres"))) return rc;
+        if ((rc = launch_export_centres(c, w.cen_dev, st))) return rc;
+        if ((rc = cuda_check(c, cudaMemcpyAsync(centres_host, w.cen_dev, (size_t)g.K * (g.C + g.n) * sizeof(float),
+                                                cudaMemcpyDeviceToHost, st),
+                             "D2H")))
+            return rc;
+    }
+    if ((rc = read_residual(c, st, &res))) return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(cs), "sync"))) return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    if (out) {
+        out->num_clusters = g.K;
+        out->num_labels = g.K;
+        out->iterations = it;
+        out->residual = res;
+    }
     return SSLIC_OK;
 }
 

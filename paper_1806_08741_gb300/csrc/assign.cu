@@ -39,14 +39,14 @@ __global__ void assign_voxel_kernel(Geom g, const T* __restrict__ img, const flo
                                     const int* __restrict__ bin_items, int32_t* __restrict__ labels,
                                     unsigned long long* __restrict__ acc, double* __restrict__ facc,
                                     const int64_t* __restrict__ tiles, const unsigned* __restrict__ ntiles,
-                                    int64_t ntx, int64_t nty, int tx_, int ty_, int tz_)
+                                    int64_t ntx, int64_t nty, int tx_, int ty_, int tz_, int64_t v0, int64_t v1)
 {
-    // tiles == nullptr: block b covers voxels [b * blockDim, ...) in raster order
+    // tiles == nullptr: the voxels [v0, v1) in raster order
     const int tv = tx_ * ty_ * tz_;
     int64_t nwork;
     if (tiles) nwork = (int64_t)(*ntiles) * tv;
-    else nwork = g.V;
-    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwork;
+    else nwork = v1;
+    for (int64_t w = (tiles ? 0 : v0) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwork;
          w += (int64_t)gridDim.x * blockDim.x) {
         int64_t x, y, z, u = 0;
         if (tiles) {
@@ -77,7 +77,7 @@ int launch_voxel_tiles(sslic_ctx* c, const T* img, int32_t* labels, int tx, int 
     Workspace& w = c->ws;
     const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN_VOXEL, st);
     assign_voxel_kernel<T><<<c->sms * 4, 256, 0, st>>>(g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc,
-                                                        w.facc, w.ovf_tiles, w.ovf_count, ntx, nty, tx, ty, tz);
+                                                        w.facc, w.ovf_tiles, w.ovf_count, ntx, nty, tx, ty, tz, 0, 0);
     count_launch(c);
     prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "assign_voxel_kernel(crowded tiles)");
@@ -90,44 +90,47 @@ template int launch_voxel_tiles<uint16_t>(sslic_ctx*, const uint16_t*, int32_t*,
 template int launch_voxel_tiles<float>(sslic_ctx*, const float*, int32_t*, int, int, int, int, int, cudaStream_t);
 
 template <typename T>
-static int launch_voxel(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+static int launch_voxel(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st, const Slab* slab)
 {
     const Geom& g = c->g;
     Workspace& w = c->ws;
-    int64_t blocks = imin64((g.V + 255) / 256, (int64_t)c->sms * 16);
+    int64_t plane = 1;
+    for (int d = 0; d < g.n - 1; ++d) plane *= g.N[d];
+    const int64_t v0 = slab ? slab->lo * plane : 0, v1 = slab ? slab->hi * plane : g.V;
+    int64_t blocks = imax64(1, imin64((v1 - v0 + 255) / 256, (int64_t)c->sms * 16));
     const int pr = prof_begin(c, SSLIC_PHASE_ASSIGN_VOXEL, st);
     assign_voxel_kernel<T><<<blocks, 256, 0, st>>>(g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc,
-                                                    w.facc, nullptr, nullptr, 1, 1, 1, 1, 1);
+                                                    w.facc, nullptr, nullptr, 1, 1, 1, 1, 1, v0, v1);
     count_launch(c);
     prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "assign_voxel_kernel");
 }
 
-int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st)
+int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st, const Slab* slab)
 {
     const Geom& g = c->g;
     const bool tiled = g.n == 2 || g.n == 3;
     if (tiled && g.dtype == SSLIC_U8 && g.C == 3) {
-        return g.n == 3 ? launch_tile_impl<uint8_t, 3, 3>(c, (const uint8_t*)img, labels, st)
-                        : launch_tile_impl<uint8_t, 3, 2>(c, (const uint8_t*)img, labels, st);
+        return g.n == 3 ? launch_tile_impl<uint8_t, 3, 3>(c, (const uint8_t*)img, labels, st, slab)
+                        : launch_tile_impl<uint8_t, 3, 2>(c, (const uint8_t*)img, labels, st, slab);
     }
     if (tiled && g.dtype == SSLIC_U8 && g.C == 1) {
-        return g.n == 3 ? launch_tile_impl<uint8_t, 1, 3>(c, (const uint8_t*)img, labels, st)
-                        : launch_tile_impl<uint8_t, 1, 2>(c, (const uint8_t*)img, labels, st);
+        return g.n == 3 ? launch_tile_impl<uint8_t, 1, 3>(c, (const uint8_t*)img, labels, st, slab)
+                        : launch_tile_impl<uint8_t, 1, 2>(c, (const uint8_t*)img, labels, st, slab);
     }
     if (tiled && g.dtype == SSLIC_U16 && g.C == 1) {
-        return g.n == 3 ? launch_tile_impl<uint16_t, 1, 3>(c, (const uint16_t*)img, labels, st)
-                        : launch_tile_impl<uint16_t, 1, 2>(c, (const uint16_t*)img, labels, st);
+        return g.n == 3 ? launch_tile_impl<uint16_t, 1, 3>(c, (const uint16_t*)img, labels, st, slab)
+                        : launch_tile_impl<uint16_t, 1, 2>(c, (const uint16_t*)img, labels, st, slab);
     }
     if (tiled && g.dtype == SSLIC_F32 && g.C == 3) {
-        return g.n == 3 ? launch_tile_impl<float, 3, 3>(c, (const float*)img, labels, st)
-                        : launch_tile_impl<float, 3, 2>(c, (const float*)img, labels, st);
+        return g.n == 3 ? launch_tile_impl<float, 3, 3>(c, (const float*)img, labels, st, slab)
+                        : launch_tile_impl<float, 3, 2>(c, (const float*)img, labels, st, slab);
     }
-    if (hc_applies(g)) return launch_hc(c, (const float*)img, labels, st);
+    if (hc_applies(g) && !slab) return launch_hc(c, (const float*)img, labels, st);  // slabs: per-voxel kernel
     switch (g.dtype) {
-    case SSLIC_U8: return launch_voxel<uint8_t>(c, (const uint8_t*)img, labels, st);
-    case SSLIC_U16: return launch_voxel<uint16_t>(c, (const uint16_t*)img, labels, st);
-    default: return launch_voxel<float>(c, (const float*)img, labels, st);
+    case SSLIC_U8: return launch_voxel<uint8_t>(c, (const uint8_t*)img, labels, st, slab);
+    case SSLIC_U16: return launch_voxel<uint16_t>(c, (const uint16_t*)img, labels, st, slab);
+    default: return launch_voxel<float>(c, (const float*)img, labels, st, slab);
     }
 }
 

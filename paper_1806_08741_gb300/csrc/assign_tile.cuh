@@ -207,8 +207,8 @@ constexpr int kListWarps = 8;
 template <int NDIM>
 __global__ void __launch_bounds__(kListWarps * 32)
 tile_lists_kernel(Geom g, const float* __restrict__ ctr, const unsigned* __restrict__ bin_start,
-                  const int* __restrict__ bin_items, int* __restrict__ lists, int64_t ntiles, int ntx, int nty,
-                  int TX, int TY, int TZ, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+                  const int* __restrict__ bin_items, int* __restrict__ lists, int64_t tile0, int64_t ntiles, int ntx,
+                  int nty, int TX, int TY, int TZ, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
 {
     __shared__ int stage_all[kListWarps][kStage];
     __shared__ int kept_all[kListWarps][kCap];
@@ -216,7 +216,7 @@ tile_lists_kernel(Geom g, const float* __restrict__ ctr, const unsigned* __restr
     int* const stage = stage_all[wp];
     int* const kept = kept_all[wp];
     const int Tn[3] = {TX, TY, TZ};
-    for (int64_t tile = (int64_t)blockIdx.x * kListWarps + wp; tile < ntiles;
+    for (int64_t tile = tile0 + (int64_t)blockIdx.x * kListWarps + wp; tile < tile0 + ntiles;
          tile += (int64_t)gridDim.x * kListWarps) {
         const int T0[3] = {(int)(tile % ntx) * TX, (int)((tile / ntx) % nty) * TY,
                            (int)(tile / ((int64_t)ntx * nty)) * TZ};
@@ -899,7 +899,8 @@ __global__ void __launch_bounds__(kThreads, 4)
 assign_tile_kernel(TileArgs a, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_body<T, C, SH>(a, blockIdx.x, 0, *reinterpret_cast<Smem<T, C, SH>*>(smem_raw), ovf_tiles, ovf_count);
+    tile_body<T, C, SH>(a, (int)(a.tile0 + blockIdx.x), 0, *reinterpret_cast<Smem<T, C, SH>*>(smem_raw), ovf_tiles,
+                        ovf_count);
 }
 
 // many images: a persistent grid walks one queue of (request, tile) work
@@ -959,13 +960,25 @@ inline auto with_shape(int shape, F&& f)
 }
 
 template <typename T, int C, typename SH>
-inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st, bool want_tma)
+inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st, bool want_tma,
+                             const Slab* slab)
 {
     const Geom& g = c->g;
     Workspace& w = c->ws;
     int ntx, nty, ntz;
     tile_grid<SH>(g, ntx, nty, ntz);
-    const int64_t ntiles = (int64_t)ntx * nty * ntz;
+    // the tiles of the launch: all, or the slab's rows of tiles along the last
+    // axis (tiles are numbered with that axis slowest; slab bounds are tile-aligned)
+    int64_t tile0 = 0, ntiles = (int64_t)ntx * nty * ntz;
+    if (slab) {
+        const int64_t ext = SH::NDIM == 3 ? SH::TZ : SH::TY;
+        const int64_t row = SH::NDIM == 3 ? (int64_t)ntx * nty : (int64_t)ntx;
+        if (slab->lo % ext != 0 || (slab->hi % ext != 0 && slab->hi != g.N[SH::NDIM - 1]))
+            return set_error(c, SSLIC_EINVAL, "slab bounds are not multiples of the tile extent");
+        tile0 = slab->lo / ext * row;
+        ntiles = (slab->hi + ext - 1) / ext * row - tile0;
+        want_tma = false;
+    }
     const size_t smem = sizeof(tile::Smem<T, C, SH>);
     int rc = cuda_check(c, cudaFuncSetAttribute(tile::assign_tile_kernel<T, C, SH>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -977,7 +990,7 @@ inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaSt
         const int64_t lgrid = imin64((ntiles + tile::kListWarps - 1) / tile::kListWarps, (int64_t)c->sms * 32);
         const int pr = prof_begin(c, SSLIC_PHASE_BINS, st);
         tile::tile_lists_kernel<SH::NDIM><<<(unsigned)lgrid, tile::kListWarps * 32, 0, st>>>(
-            g, w.ctr, w.bin_start, w.bin_items, w.tile_lists, ntiles, ntx, nty, SH::TX, SH::TY, SH::TZ,
+            g, w.ctr, w.bin_start, w.bin_items, w.tile_lists, tile0, ntiles, ntx, nty, SH::TX, SH::TY, SH::TZ,
             w.ovf_tiles, w.ovf_count);
         count_launch(c);
         prof_end(c, pr, st);
@@ -998,6 +1011,7 @@ inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaSt
     a.ty = SH::TY;
     a.tz = SH::TZ;
     a.lists = w.tile_lists;
+    a.tile0 = tile0;
     alignas(64) CUtensorMap map;
     const bool tma = sizeof(T) < 4 && want_tma && image_tma_ok(g, img, (int)sizeof(T)) &&
                      encode_image_map(&map, g, img, (int)sizeof(T), SH::TX, SH::TY, SH::TZ) == SSLIC_OK;
@@ -1037,14 +1051,14 @@ inline int launch_tile_shape(sslic_ctx* c, const T* img, int32_t* labels, cudaSt
 }
 
 template <typename T, int C, int NDIM>
-int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st)
+int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st, const Slab* slab)
 {
     int shape = c->tile_shape;
     if (shape < 0) shape = tuned_tile_shape(c->g);
     if (shape < 0) shape = default_tile_shape(c->g);
     const int b = num_base_shapes(NDIM);
     return with_shape<NDIM>(shape % b, [&](auto sh) {
-        return launch_tile_shape<T, C, decltype(sh)>(c, img, labels, st, shape >= b);
+        return launch_tile_shape<T, C, decltype(sh)>(c, img, labels, st, shape >= b, slab);
     });
 }
 
@@ -1078,6 +1092,7 @@ cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tp
 
 // explicit instantiation of both launchers for one image type
 #define SSLIC_TILE_INSTANTIATE(T, C, NDIM)                                                                  \
-    template int sslic::launch_tile_impl<T, C, NDIM>(sslic_ctx*, const T*, int32_t*, cudaStream_t);         \
+    template int sslic::launch_tile_impl<T, C, NDIM>(sslic_ctx*, const T*, int32_t*, cudaStream_t,         \
+                                                     const sslic::Slab*);                                   \
     template cudaError_t sslic::launch_tile_queue<T, C, NDIM>(int, const sslic::TileArgs*, const int64_t*, \
                                                               const int*, int64_t*, unsigned*, int, cudaStream_t);

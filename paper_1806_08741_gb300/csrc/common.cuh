@@ -109,6 +109,14 @@ struct TileArgs {
     int ntx, nty;     // tile grid of the tile shape in use
     int tx, ty, tz;   // that shape's tile dimensions
     const int* lists; // per-tile candidate records of that shape, or nullptr (gathered in the kernel)
+    int64_t tile0;    // first tile of the launch (a slab of the streamed form), else 0
+};
+
+// Part of an image along its last axis (z in 3-D, y in 2-D) for the streamed
+// form: the kernels read and write only the planes [lo, hi), through buffers
+// whose pointers are set back by lo planes so that voxel indices stay global.
+struct Slab {
+    int64_t lo, hi;
 };
 
 // ---- context ---------------------------------------------------------------
@@ -163,6 +171,13 @@ struct Workspace {
     void* img_dev = nullptr;
     int32_t* lab_dev = nullptr;
     float* cen_dev = nullptr;
+    // streamed form (sslic_run_streamed): two slab buffers of image planes and
+    // of labels, a copy stream and the events that order the two streams
+    unsigned char* slab_img[2] = {nullptr, nullptr};
+    int32_t* slab_lab[2] = {nullptr, nullptr};
+    int64_t slab_planes = 0;            // planes each buffer holds (image: + 4 halo planes)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t slab_ev[8] = {};        // img ready / img free / labels done / labels free, per buffer
 };
 
 }  // namespace sslic
@@ -193,9 +208,9 @@ struct sslic_ctx {
 
 namespace sslic {
 // kernels / launchers implemented in the .cu files
-int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st);
+int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st, const Slab* slab = nullptr);
 int build_bins(sslic_ctx* c, cudaStream_t st);
-int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st);
+int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st, const Slab* slab = nullptr);
 int launch_finalize(sslic_ctx* c, cudaStream_t st);
 int launch_export_centres(sslic_ctx* c, float* out, cudaStream_t st);
 int launch_import_centres(sslic_ctx* c, const float* in, cudaStream_t st);
@@ -226,7 +241,7 @@ template <typename T, int C, int NDIM>
 cudaError_t launch_tile_queue(int shape, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
                               unsigned* ovf_count, int grid, cudaStream_t st);
 template <typename T, int C, int NDIM>
-int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st);
+int launch_tile_impl(sslic_ctx* c, const T* img, int32_t* labels, cudaStream_t st, const Slab* slab = nullptr);
 template <typename T>
 int launch_voxel_tiles(sslic_ctx* c, const T* img, int32_t* labels, int tx, int ty, int tz, int ntx, int nty,
                        cudaStream_t st);

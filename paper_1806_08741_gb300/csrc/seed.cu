@@ -15,28 +15,45 @@
 namespace sslic {
 
 template <typename T>
-__global__ void seed_kernel(Geom g, const T* __restrict__ img, float* __restrict__ ctr, int perturb)
+__global__ void seed_kernel(Geom g, const T* __restrict__ img, float* __restrict__ ctr, int perturb, int64_t k0,
+                            int64_t k1)
 {
-    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < g.K) seed_one<T>(g, img, ctr, perturb, k);
+    const int64_t k = k0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < k1) seed_one<T>(g, img, ctr, perturb, k);
 }
 
-int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st)
+// With a slab: the seeds whose lattice coordinate along the last axis lies in
+// [lo, hi); the buffer must hold the planes [lo - 2, hi + 2) (clamped to the
+// image), which the perturbation's gradients reach.
+int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st, const Slab* slab)
 {
     const Geom& g = c->g;
+    int64_t k0 = 0, k1 = g.K;
+    if (slab) {
+        const int a = g.n - 1;  // the last axis
+        int64_t per = 1;
+        for (int d = 0; d < a; ++d) per *= g.nb[d];
+        auto first_at_or_after = [&](int64_t v) {  // smallest j with off + j S >= v
+            const int64_t t = v - g.off[a];
+            return t <= 0 ? 0 : imin64(g.nb[a], (t + g.S[a] - 1) / g.S[a]);
+        };
+        k0 = first_at_or_after(slab->lo) * per;
+        k1 = first_at_or_after(slab->hi) * per;
+        if (k1 <= k0) return SSLIC_OK;
+    }
     int threads = 128;
-    int64_t blocks = (g.K + threads - 1) / threads;
+    int64_t blocks = (k1 - k0 + threads - 1) / threads;
     const int pr = prof_begin(c, SSLIC_PHASE_SEED, st);
     count_launch(c);
     switch (g.dtype) {
     case SSLIC_U8:
-        seed_kernel<uint8_t><<<blocks, threads, 0, st>>>(g, (const uint8_t*)img, c->ws.ctr, c->p.perturb);
+        seed_kernel<uint8_t><<<blocks, threads, 0, st>>>(g, (const uint8_t*)img, c->ws.ctr, c->p.perturb, k0, k1);
         break;
     case SSLIC_U16:
-        seed_kernel<uint16_t><<<blocks, threads, 0, st>>>(g, (const uint16_t*)img, c->ws.ctr, c->p.perturb);
+        seed_kernel<uint16_t><<<blocks, threads, 0, st>>>(g, (const uint16_t*)img, c->ws.ctr, c->p.perturb, k0, k1);
         break;
     default:
-        seed_kernel<float><<<blocks, threads, 0, st>>>(g, (const float*)img, c->ws.ctr, c->p.perturb);
+        seed_kernel<float><<<blocks, threads, 0, st>>>(g, (const float*)img, c->ws.ctr, c->p.perturb, k0, k1);
     }
     prof_end(c, pr, st);
     return cuda_check(c, cudaGetLastError(), "seed_kernel");

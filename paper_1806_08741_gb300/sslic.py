@@ -22,7 +22,7 @@ U8, U16, F32 = 0, 1, 2
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUSY", -6: "EUNSUPPORTED"}
 
 EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_run",
-           "sslic_run_from", "sslic_run_host", "sslic_seed", "sslic_iterate",
+           "sslic_run_from", "sslic_run_host", "sslic_run_streamed", "sslic_seed", "sslic_iterate",
            "sslic_connectivity", "sslic_iterate_static", "sslic_server_create",
            "sslic_server_submit", "sslic_server_wait", "sslic_server_stats_get",
            "sslic_server_destroy", "sslic_num_tile_shapes", "sslic_tile_shape_info",
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH):
     L.sslic_run.argtypes = [C, vp, vp, vp, vp, R]
     L.sslic_run_from.argtypes = [C, vp, vp, vp, vp, vp, R]
     L.sslic_run_host.argtypes = [C, vp, vp, vp, vp, R]
+    L.sslic_run_streamed.argtypes = [C, vp, vp, vp, ctypes.c_int64, vp, R]
     L.sslic_seed.argtypes = [C, vp, vp, vp]
     L.sslic_iterate.argtypes = [C, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sslic_connectivity.argtypes = [C, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
@@ -323,6 +324,21 @@ class Context:
         r = _Result()
         self._check(self.lib.sslic_run_host(self._c, _ptr(image), _ptr(labels), _ptr(centres),
                                             _stream(stream), ctypes.byref(r)), "sslic_run_host")
+        return {"num_clusters": r.num_clusters, "num_labels": r.num_labels,
+                "iterations": r.iterations, "residual": r.residual}
+
+    def run_streamed(self, image, labels, centres=None, slab_planes: int = 64, stream=None) -> dict:
+        """The whole method with the image in host memory, streamed through
+        the GPU in slabs of slab_planes planes along the last axis every
+        iteration (sslic_run_streamed; host buffers, ideally pinned)."""
+        V = self._voxels()
+        self._need(image, V * self.params.channels, "image", device=False)
+        self._need(labels, V, "labels", device=False)
+        self._need(centres, self.K * self.centre_width, "centres", device=False)
+        r = _Result()
+        self._check(self.lib.sslic_run_streamed(self._c, _ptr(image), _ptr(labels), _ptr(centres),
+                                                int(slab_planes), _stream(stream), ctypes.byref(r)),
+                    "sslic_run_streamed")
         return {"num_clusters": r.num_clusters, "num_labels": r.num_labels,
                 "iterations": r.iterations, "residual": r.residual}
 

@@ -348,7 +348,7 @@ def run_ours(args, w):
         ctx.close()
         del img, labels, centres
         torch.cuda.empty_cache()
-        serving = serving_bench(n_req=args.serve_requests)
+        serving = serving_bench(n_req=args.serve_requests, max_active=args.serve_max_active)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -540,7 +540,7 @@ def precision_bench(steps=3, warmup=2):
 # ---------------------------------------------------------------------------
 # serving: request stream, continuous batching vs one image per launch
 # ---------------------------------------------------------------------------
-def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12):
+def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=256):
     """Poisson arrivals (rate per second) of requests mixing 2-D RGB uint8
     tiles (side ~ U[256, 4096]) and 3-D uint16 blocks (side ~ U[128, 512]),
     S in {8, 16, 32}, m in {5, 10, 20}, 10 iterations.  Inputs come from a
@@ -610,7 +610,7 @@ def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12):
 
     # served form: a submitter at the arrival times, a waiter recycling outputs
     res = {}
-    with S.Server(int(budget_gb * (1 << 30)), max_active=256) as srv:
+    with S.Server(int(budget_gb * (1 << 30)), max_active=max_active) as srv:
         import queue as _q
         handed = _q.Queue()
         lats = []
@@ -639,7 +639,8 @@ def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12):
         st = srv.stats()
     res["served"] = {"p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
                      "mean_ms": float(np.mean(lats)), "throughput": vox_iters / wall / 1e9,
-                     "wall_s": wall, "max_active": st["max_active"], "rounds": st["rounds"],
+                     "wall_s": wall, "max_active": st["max_active"], "max_active_limit": max_active,
+                     "rounds": st["rounds"],
                      "peak_gb": st["peak_bytes"] / 2 ** 30}
 
     # plain form: one request at a time, in arrival order
@@ -689,6 +690,7 @@ def main():
                     help="only the request-stream benchmark (served vs plain form)")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream benchmark")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-max-active", type=int, default=256, help="requests the server advances at once")
     args = ap.parse_args()
     if args.lab_only:
         import torch
@@ -709,7 +711,7 @@ def main():
     if args.serve:
         import torch
         torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
-        print(json.dumps({"serving": serving_bench(n_req=args.serve_requests)}), flush=True)
+        print(json.dumps({"serving": serving_bench(n_req=args.serve_requests, max_active=args.serve_max_active)}), flush=True)
         return 0
     from paper_1806_08741_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]

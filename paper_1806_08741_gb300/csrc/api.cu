@@ -178,6 +178,7 @@ static void free_all(sslic_ctx* c)
     for (int i = 0; i < 8; ++i)
         if (w.slab_ev[i]) { cudaEventDestroy(w.slab_ev[i]); w.slab_ev[i] = nullptr; }
     if (w.copy_stream) { cudaStreamDestroy(w.copy_stream); w.copy_stream = nullptr; }
+    if (w.down_stream) { cudaStreamDestroy(w.down_stream); w.down_stream = nullptr; }
 }
 
 static int alloc_core(sslic_ctx* c)
@@ -431,11 +432,14 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
     if (!w.copy_stream &&
         (rc = cuda_check(c, cudaStreamCreateWithFlags(&w.copy_stream, cudaStreamNonBlocking), "copy stream")))
         return rc;
+    if (!w.down_stream &&
+        (rc = cuda_check(c, cudaStreamCreateWithFlags(&w.down_stream, cudaStreamNonBlocking), "copy stream")))
+        return rc;
     for (int i = 0; i < 8; ++i)
         if (!w.slab_ev[i] &&
             (rc = cuda_check(c, cudaEventCreateWithFlags(&w.slab_ev[i], cudaEventDisableTiming), "events")))
             return rc;
-    cudaStream_t st = (cudaStream_t)stream, cs = w.copy_stream;
+    cudaStream_t st = (cudaStream_t)stream, cs = w.copy_stream, ds = w.down_stream;
     cudaEvent_t* img_ready = w.slab_ev;      // [2]: recorded on cs after a buffer's upload
     cudaEvent_t* img_free = w.slab_ev + 2;   // [2]: recorded on st after the kernels that read it
     cudaEvent_t* lab_done = w.slab_ev + 4;   // [2]: recorded on st after the kernels that write it
@@ -456,10 +460,21 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
         if ((r = cuda_check(c, cudaEventRecord(img_ready[i], cs), "event"))) return r;
         return cuda_check(c, cudaStreamWaitEvent(st, img_ready[i], 0), "wait");
     };
-    // seeding: each slab with the two planes on either side its gradients reach
-    for (int64_t s = 0; s < nslab; ++s) {
+    // seeding reads the planes within two of a seed plane (the perturbation's
+    // gradients): with S >= 8 along the last axis, only those five planes per
+    // lattice row go up; with finer grids, whole slabs with a two-plane halo
+    const int64_t S_l = g.S[ax];
+    const int64_t nrow = S_l >= 8 ? g.nb[ax] : nslab;
+    for (int64_t s = 0; s < nrow; ++s) {
         const int i = (int)(s & 1);
-        const int64_t lo = s * depth, hi = imin64(NL, lo + depth);
+        int64_t lo, hi;
+        if (S_l >= 8) {
+            lo = g.off[ax] + s * S_l;  // the lattice row's plane
+            hi = lo + 1;
+        } else {
+            lo = s * depth;
+            hi = imin64(NL, lo + depth);
+        }
         const int64_t a = imax64(0, lo - 2), bnd = imin64(NL, hi + 2);
         if ((rc = upload(i, a, bnd))) return rc;
         const Slab sl{lo, hi};
@@ -484,13 +499,13 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
             if ((rc = cuda_check(c, cudaEventRecord(img_free[i], st), "event"))) return rc;
             if ((rc = cuda_check(c, cudaEventRecord(lab_done[i], st), "event"))) return rc;
             if (keep) {
-                if ((rc = cuda_check(c, cudaStreamWaitEvent(cs, lab_done[i], 0), "wait"))) return rc;
+                if ((rc = cuda_check(c, cudaStreamWaitEvent(ds, lab_done[i], 0), "wait"))) return rc;
                 if ((rc = cuda_check(c, cudaMemcpyAsync(labels_host + lo * plane, w.slab_lab[i],
                                                         (size_t)(hi - lo) * plane * sizeof(int32_t),
-                                                        cudaMemcpyDeviceToHost, cs),
+                                                        cudaMemcpyDeviceToHost, ds),
                                      "slab labels")))
                     return rc;
-                if ((rc = cuda_check(c, cudaEventRecord(lab_free[i], cs), "event"))) return rc;
+                if ((rc = cuda_check(c, cudaEventRecord(lab_free[i], ds), "event"))) return rc;
             }
         }
         if ((rc = launch_finalize(c, st))) return rc;
@@ -508,6 +523,7 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
             return rc;
     }
     if ((rc = read_residual(c, st, &res))) return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(ds), "sync"))) return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(cs), "sync"))) return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
     if (out) {

@@ -176,7 +176,8 @@ struct Workspace {
     unsigned char* slab_img[2] = {nullptr, nullptr};
     int32_t* slab_lab[2] = {nullptr, nullptr};
     int64_t slab_planes = 0;            // planes each buffer holds (image: + 4 halo planes)
-    cudaStream_t copy_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // uploads
+    cudaStream_t down_stream = nullptr;  // label downloads (the other direction, concurrently)
     cudaEvent_t slab_ev[8] = {};        // img ready / img free / labels done / labels free, per buffer
 };
 

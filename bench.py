@@ -540,7 +540,7 @@ def precision_bench(steps=3, warmup=2):
 # ---------------------------------------------------------------------------
 # serving: request stream, continuous batching vs one image per launch
 # ---------------------------------------------------------------------------
-def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=256):
+def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=16):
     """Poisson arrivals (rate per second) of requests mixing 2-D RGB uint8
     tiles (side ~ U[256, 4096]) and 3-D uint16 blocks (side ~ U[128, 512]),
     S in {8, 16, 32}, m in {5, 10, 20}, 10 iterations.  Inputs come from a
@@ -690,7 +690,7 @@ def main():
                     help="only the request-stream benchmark (served vs plain form)")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream benchmark")
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-max-active", type=int, default=256, help="requests the server advances at once")
+    ap.add_argument("--serve-max-active", type=int, default=16, help="requests the server advances at once")
     args = ap.parse_args()
     if args.lab_only:
         import torch

@@ -218,8 +218,10 @@ tile_lists_kernel(Geom g, const float* __restrict__ ctr, const unsigned* __restr
     const int Tn[3] = {TX, TY, TZ};
     for (int64_t tile = tile0 + (int64_t)blockIdx.x * kListWarps + wp; tile < tile0 + ntiles;
          tile += (int64_t)gridDim.x * kListWarps) {
-        const int T0[3] = {(int)(tile % ntx) * TX, (int)((tile / ntx) % nty) * TY,
-                           (int)(tile / ((int64_t)ntx * nty)) * TZ};
+        const unsigned t32 = (unsigned)tile;  // tile counts stay below 2^31: 32-bit division
+        const unsigned txy = t32 / (unsigned)ntx;
+        const int T0[3] = {(int)(t32 - txy * (unsigned)ntx) * TX, (int)(txy % (unsigned)nty) * TY,
+                           (int)(txy / (unsigned)nty) * TZ};
         int E[3], blo[3], nbd[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -234,8 +236,9 @@ tile_lists_kernel(Geom g, const float* __restrict__ ctr, const unsigned* __restr
             const int b = b0 + lane;
             unsigned first = 0, cnt = 0;
             if (b < nbins) {
-                const int bx = blo[0] + b % nbd[0], by = blo[1] + (b / nbd[0]) % nbd[1],
-                          bz = blo[2] + b / (nbd[0] * nbd[1]);
+                const unsigned bq = (unsigned)b / (unsigned)nbd[0];
+                const int bx = blo[0] + (int)((unsigned)b - bq * (unsigned)nbd[0]),
+                          by = blo[1] + (int)(bq % (unsigned)nbd[1]), bz = blo[2] + (int)(bq / (unsigned)nbd[1]);
                 const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
                 first = bin_start[bin];
                 cnt = bin_start[bin + 1] - first;

@@ -297,6 +297,20 @@ def run_ours(args, w):
                 "peak_source": f"of {peak_src}", "bytes_per_launch": algo,
                 "bytes_per_voxel": bytes_per_vox, "avg_launch_ms": a_ms / a_calls,
                 "traffic": TRAFFIC_BYTES.get((w.name, src))}
+    # the same kernel against the SM's FP32 lanes, the unit that bounds it:
+    # per (voxel, covering centre) pair the canonical D^2 costs C subtractions,
+    # C products and C - 1 + n sums once the per-axis terms are tabulated per
+    # tile, plus one comparison; a voxel is covered by prod_d (2 S_d) K / V
+    # windows on average; peak = 152 SMs x 128 FP32 lanes x the SM clock
+    roof_alu = None
+    if a_calls:
+        cover = float(np.prod([2 * s_ for s_ in w.grid])) * ctx.K / V
+        ops_pair = 2 * spec.channels + (spec.channels - 1) + spec.ndim + 1
+        alu_peak = 152 * 128 * 2.07e9 / 1e12
+        ach = V * cover * ops_pair / (a_ms / a_calls / 1e3) / 1e12
+        roof_alu = {"kernel": roof["kernel"], "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": ach / alu_peak, "ops_per_voxel": cover * ops_pair, "covering_centres_per_voxel": cover,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
     phases = {k: {"ms_per_step": v[0] / args.steps, "calls_per_step": v[1] / args.steps}
               for k, v in prof.items() if k in S.PHASES}
     # the iterated assign/update loop alone (bins + assignment + reduction),
@@ -363,7 +377,7 @@ def run_ours(args, w):
             "config": {**_config(w), "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
             "tile_shape": tune, "assign_update_loop": loop,
-            "roofline": roof, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
+            "roofline": roof, "roofline_alu": roof_alu, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
             "precision": precision, "lab": lab, "streamed": streamed,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }

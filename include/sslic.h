@@ -47,7 +47,7 @@ extern "C" {
 #define SSLIC_ECUDA (-3)    /* a CUDA launch or runtime call failed */
 #define SSLIC_ETIMEOUT (-4) /* a bounded device-side wait expired */
 #define SSLIC_EBUSY (-5)    /* the context is in use by another call */
-#define SSLIC_EUNSUPPORTED (-6) /* valid request this build does not implement */
+#define SSLIC_EUNSUPPORTED (-6) /* valid request the library does not implement */
 
 typedef enum { SSLIC_U8 = 0, SSLIC_U16 = 1, SSLIC_F32 = 2 } sslic_dtype;
 

@@ -28,9 +28,10 @@
 // voxels), one voxel per thread, its features in registers (the channel
 // count is a template parameter, C zero-padded to it).  Tiles reached by
 // more than 32 centres go to the per-voxel kernel.  The map step sums the
-// features per (channel, part of the tile) in FP32 along runs of equal
-// labels and adds each run to the double-precision sums with one FP64
-// atomic; positions and counts are exact integers.
+// features, staged in shared memory, per (channel, part of the tile) in FP32
+// along runs of equal labels, adds the runs in double per slot and the
+// slots to the double-precision sums with one FP64 atomic per (slot,
+// channel); positions and counts are exact integers.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -64,12 +65,18 @@ __host__ __device__ inline int ct_of(int C) { return C <= 16 ? 16 : C <= 32 ? 32
 // dynamic shared memory for CT channels: the two BF16 planes (high and low
 // parts) of the voxel operand A and the centre operand B, then the FP32
 // candidate features
+// then, for the map step, the tile's features in FP32, channel-major with a
+// row pitch of kTV + 1 floats (the tensor-core form reuses its operand region
+// once its MMAs are done)
+constexpr int kXP = kTV + 1;
 template <int CT, bool MMA>
 struct Lay {
     static constexpr size_t A = (size_t)kTV * CT * 2, B = (size_t)kNC * CT * 2;
     static constexpr size_t a_hi = 0, a_lo = MMA ? A : 0, b_hi = MMA ? 2 * A : 0, b_lo = MMA ? 2 * A + B : 0;
     static constexpr size_t cf = MMA ? 2 * A + 2 * B : 0;
-    static constexpr size_t end = cf + (size_t)kNC * CT * 4;
+    static constexpr size_t xs = MMA ? 0 : cf + (size_t)kNC * CT * 4;
+    static constexpr size_t end = MMA ? cf + (size_t)kNC * CT * 4 : xs + (size_t)CT * kXP * 4;
+    static_assert(!MMA || (size_t)CT * kXP * 4 <= 2 * A + 2 * B, "features fit the operand region");
 };
 
 struct Fixed {
@@ -299,6 +306,10 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
     int bs = kNone;
     if constexpr (!MMA) {
         bs = exact_best(x);
+        // the features for the map step, channel-major (the registers are free after this)
+        float* xs = reinterpret_cast<float*>(smem + LY::xs);
+#pragma unroll
+        for (int c = 0; c < CT; ++c) xs[c * kXP + v] = x[c];
     } else {
         // shift: the mean of the candidates' features
         for (int c = tid; c < CT; c += kThreads) {
@@ -422,6 +433,15 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
     }
     f.slot[v] = (uint8_t)bs;
     if (valid && !dbg_dots) labels[q] = bs == kNone ? -1 : f.cand[bs];
+    if constexpr (MMA) {
+        // the features for the map step, into the operand region: every thread
+        // has seen the MMAs complete, so nothing reads it any more
+        float xr2[CT];
+        load_x(xr2);
+        float* xs = reinterpret_cast<float*>(smem + LY::xs);
+#pragma unroll
+        for (int c = 0; c < CT; ++c) xs[c * kXP + v] = xr2[c];
+    }
     for (int i = tid; i < nc * 4; i += kThreads) (&f.pacc[0][0])[i] = 0u;
     __syncthreads();
     if (MMA && warp == 0) {
@@ -431,36 +451,52 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
     if (dbg_dots) return;
 
     // ---- map step: positions and counts per slot in shared memory; features
-    //      per (channel, part of the tile) as FP32 sums along runs of equal
-    //      slots, each run leaving through one FP64 atomic ----
+    //      staged channel-major, summed in FP32 along runs of equal slots,
+    //      the runs added in double per slot and leaving through one FP64
+    //      atomic per (slot, channel) ----
     if (bs != kNone) {
         atomicAdd(&f.pacc[bs][0], (unsigned)xl);
         atomicAdd(&f.pacc[bs][1], (unsigned)yl);
         atomicAdd(&f.pacc[bs][2], (unsigned)zl);
         atomicAdd(&f.pacc[bs][3], 1u);
     }
+    // per-slot sums in double in the candidate-feature region (no longer
+    // read) when they fit it; else every run goes straight to the FP64 sums
+    double* dsum = reinterpret_cast<double*>(cf);
+    const bool tile_sums = 2 * nc <= kNC;
+    if (tile_sums)
+        for (int i = tid; i < nc * CT; i += kThreads) dsum[i] = 0.0;
+    __syncthreads();
     {
         const int parts = kThreads / C;
         if (tid < parts * C) {
             const int c = tid % C, part = tid / C;
             const int v0 = part * kTV / parts, v1 = (part + 1) * kTV / parts;
+            const float* xr = reinterpret_cast<const float*>(smem + LY::xs) + c * kXP;
+            auto flush = [&](int r, float sum) {
+                if (tile_sums) atomicAdd(&dsum[r * CT + c], (double)sum);
+                else atomicAdd(&facc[(int64_t)f.cand[r] * C + c], (double)sum);
+            };
             int cur = kNone;
-            float s = 0.0f;
+            float sum = 0.0f;
             for (int w = v0; w < v1; ++w) {
                 const int sl = f.slot[w];
                 if (sl != cur) {
-                    if (cur != kNone) atomicAdd(&facc[(int64_t)f.cand[cur] * C + c], (double)s);
+                    if (cur != kNone) flush(cur, sum);
                     cur = sl;
-                    s = 0.0f;
+                    sum = 0.0f;
                 }
-                if (sl != kNone) {
-                    const int wx = w % TX, wy = (w / TX) % TY, wz = w / (TX * TY);
-                    s = __fadd_rn(s, __ldg(img + vidx(g, X0 + wx, Y0 + wy, Z0 + wz) * C + c));
-                }
+                if (sl != kNone) sum = __fadd_rn(sum, xr[w]);
             }
-            if (cur != kNone) atomicAdd(&facc[(int64_t)f.cand[cur] * C + c], (double)s);
+            if (cur != kNone) flush(cur, sum);
         }
     }
+    __syncthreads();
+    if (tile_sums)
+        for (int i = tid; i < nc * C; i += kThreads) {
+            const int r = i / C, c = i % C;
+            if (f.pacc[r][3]) atomicAdd(&facc[(int64_t)f.cand[r] * C + c], dsum[r * CT + c]);
+        }
     __syncthreads();
     for (int i = tid; i < nc * 4; i += kThreads) {
         const int r = i / 4, j = i % 4;

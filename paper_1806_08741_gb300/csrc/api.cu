@@ -210,9 +210,12 @@ static int alloc_core(sslic_ctx* c)
     if ((rc = cuda_check(c, cudaMemset(w.hc_rechecks, 0, sizeof(unsigned long long)), "memset"))) return rc;
     if ((rc = dalloc(c, &w.ovf_tiles, (size_t)w.n_assign_tiles, "tiles"))) return rc;
     if ((rc = dalloc(c, &w.ovf_count, 1, "tiles"))) return rc;
-    if (has_tile_kernel(g) &&
-        (rc = dalloc(c, &w.tile_lists, (size_t)assign_num_tiles(g) * tile_list_stride(), "tile lists")))
-        return rc;
+    {
+        // candidate records for the tile kernels (the largest tiling any shape makes)
+        int64_t nrec = has_tile_kernel(g) ? assign_num_tiles(g) : 0;
+        if (hc_applies(g)) nrec = imax64(nrec, hc_num_tiles(g));
+        if (nrec > 0 && (rc = dalloc(c, &w.tile_lists, (size_t)nrec * tile_list_stride(), "tile lists"))) return rc;
+    }
     if ((rc = cuda_check(c, cudaMemset(w.acc, 0, K * g.AW * sizeof(unsigned long long)), "memset sums"))) return rc;
     if (w.facc && (rc = cuda_check(c, cudaMemset(w.facc, 0, K * g.C * sizeof(double)), "memset sums"))) return rc;
     if ((rc = cuda_check(c, cudaMemset(w.resid_out, 0, sizeof(double)), "memset"))) return rc;

@@ -59,6 +59,26 @@ int default_tile_shape(const Geom& g)
 }
 
 int tile_list_stride() { return tile::kListStride; }
+static_assert(tile::kListStride == kTileListStride, "record layout");
+
+int launch_tile_lists(sslic_ctx* c, int ndim, int tx, int ty, int tz, int ntx, int nty, int64_t tile0,
+                      int64_t ntiles, cudaStream_t st)
+{
+    const Workspace& w = c->ws;
+    const int64_t lgrid = imax64(1, imin64((ntiles + tile::kListWarps - 1) / tile::kListWarps, (int64_t)c->sms * 32));
+    const int pr = prof_begin(c, SSLIC_PHASE_BINS, st);  // timed with the bins it reads
+    if (ndim == 3)
+        tile::tile_lists_kernel<3><<<(unsigned)lgrid, tile::kListWarps * 32, 0, st>>>(
+            c->g, w.ctr, w.bin_start, w.bin_items, w.tile_lists, tile0, ntiles, ntx, nty, tx, ty, tz, w.ovf_tiles,
+            w.ovf_count);
+    else
+        tile::tile_lists_kernel<2><<<(unsigned)lgrid, tile::kListWarps * 32, 0, st>>>(
+            c->g, w.ctr, w.bin_start, w.bin_items, w.tile_lists, tile0, ntiles, ntx, nty, tx, ty, tz, w.ovf_tiles,
+            w.ovf_count);
+    count_launch(c);
+    prof_end(c, pr, st);
+    return cuda_check(c, cudaGetLastError(), "tile_lists_kernel");
+}
 
 // the most tiles any shape cuts the image into (sizes the crowded-tile list)
 int64_t assign_num_tiles(const Geom& g)

@@ -222,6 +222,11 @@ size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
 int tile_list_stride();  // ints per per-tile candidate record
+constexpr int kTileListStride = 49;  // a record: count, then up to 48 centre indices in ascending order
+// per-tile candidate records for tiles [tile0, tile0 + ntiles) of a tx x ty x tz
+// tiling (ntx x nty tiles per plane of tiles), into the workspace's list buffer
+int launch_tile_lists(sslic_ctx* c, int ndim, int tx, int ty, int tz, int ntx, int nty, int64_t tile0,
+                      int64_t ntiles, cudaStream_t st);
 bool has_tile_kernel(const Geom& g);  // integer images with a tile kernel (2-D, 3-D)
 // TMA tensor map of an image as bytes [N_2][N_1][N_0 * C * esz] (tma.cu);
 // map points at 128 bytes, 64-byte aligned

@@ -35,6 +35,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -112,7 +114,8 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
                int32_t* __restrict__ labels, unsigned long long* __restrict__ acc, double* __restrict__ facc,
                int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count, unsigned* __restrict__ err,
                unsigned long long* __restrict__ rechecks, int ntx, int nty, int64_t tile0,
-               float* __restrict__ dbg_dots, int* __restrict__ dbg_cand, float* __restrict__ dbg_mu)
+               float* __restrict__ dbg_dots, int* __restrict__ dbg_cand, float* __restrict__ dbg_mu,
+               const int* __restrict__ lists)
 {
     using TL = Tile<NDIM>;
     using LY = Lay<CT, MMA>;
@@ -130,6 +133,10 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
     const int Z0 = (int)(tile / ((int64_t)ntx * nty)) * TZ;
     const int ex = (int)imin64(TX, g.N[0] - X0), ey = (int)imin64(TY, g.N[1] - Y0), ez = (int)imin64(TZ, g.N[2] - Z0);
 
+    // with lists: this thread's entry of the tile's candidate record (count,
+    // then the indices in ascending order), loaded before the features
+    int lk = -1;
+    if (lists && tid < kTileListStride) lk = __ldg(lists + tile * kTileListStride + tid);
     if (tid == 0) { f.nstage = 0; f.ncand = 0; f.nrecheck = 0; }
     if (MMA) {
         if (warp == 0) {
@@ -174,51 +181,71 @@ hc_tile_kernel(Geom g, const float* __restrict__ img, const float* __restrict__ 
         bhi[d] = min((int)g.nb[d] - 1, (T0[d] + E[d] - 1) / g.S[d] + 1);
     }
     const int nbx = bhi[0] - blo[0] + 1, nby = bhi[1] - blo[1] + 1, nbz = bhi[2] - blo[2] + 1;
+    if (lists && tid == 0) f.ncand = lk;
     __syncthreads();
-    for (int b = tid; b < nbx * nby * nbz; b += kThreads) {
-        const int bx = blo[0] + b % nbx, by = blo[1] + (b / nbx) % nby, bz = blo[2] + b / (nbx * nby);
-        const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
-        for (unsigned i = bin_start[bin]; i < bin_start[bin + 1]; ++i) {
-            const int pos = atomicAdd(&f.nstage, 1);
-            if (pos < kStage) f.stage[pos] = bin_items[i];
+    int nc;
+    if (lists) {
+        nc = f.ncand;
+        if (nc < 0 || nc > kNC) {  // block-uniform: the per-voxel kernel takes this tile
+            if (nc > kNC && tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = tile;
+            if (MMA && warp == 0) tc::tmem_dealloc(f.tmem, 32);
+            return;
+        }
+        if (tid >= 1 && tid <= nc) {
+            const int r = tid - 1;
+            f.cand[r] = lk;
+            const float* row = ctr + (int64_t)lk * g.CW;
+            f.cpos[r][0] = row[C];
+            f.cpos[r][1] = row[C + 1];
+            f.cpos[r][2] = row[C + 2];
+        }
+    } else {
+        for (int b = tid; b < nbx * nby * nbz; b += kThreads) {
+            const int bx = blo[0] + b % nbx, by = blo[1] + (b / nbx) % nby, bz = blo[2] + b / (nbx * nby);
+            const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
+            for (unsigned i = bin_start[bin]; i < bin_start[bin + 1]; ++i) {
+                const int pos = atomicAdd(&f.nstage, 1);
+                if (pos < kStage) f.stage[pos] = bin_items[i];
+            }
+        }
+        __syncthreads();
+        const int nst = f.nstage;
+        for (int i = tid; i < min(nst, kStage); i += kThreads) {
+            const int k = f.stage[i];
+            const float* p = ctr + (int64_t)k * g.CW + C;
+            bool hit = true;
+            for (int d = 0; d < NDIM; ++d) {
+                const int lo = (int)ceilf(p[d]) - g.S[d];
+                hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
+            }
+            if (hit) {
+                const int pos = atomicAdd(&f.ncand, 1);
+                if (pos < kNC) f.tmp[pos] = k;
+            }
+        }
+        __syncthreads();
+        nc = f.ncand;
+        if (nst > kStage || nc > kNC) {
+            if (tile0 < 0 && tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = tile;
+            if (MMA && warp == 0) tc::tmem_dealloc(f.tmem, 32);
+            return;  // block-uniform: the per-voxel kernel takes this tile
+        }
+        for (int i = tid; i < nc; i += kThreads) {
+            const int k = f.tmp[i];
+            int r = 0;
+            for (int j = 0; j < nc; ++j) r += (f.tmp[j] < k);
+            f.cand[r] = k;
+            const float* row = ctr + (int64_t)k * g.CW;
+            f.cpos[r][0] = row[C];
+            f.cpos[r][1] = row[C + 1];
+            f.cpos[r][2] = row[C + 2];
         }
     }
     __syncthreads();
-    const int nst = f.nstage;
-    for (int i = tid; i < min(nst, kStage); i += kThreads) {
-        const int k = f.stage[i];
-        const float* p = ctr + (int64_t)k * g.CW + C;
-        bool hit = true;
-        for (int d = 0; d < NDIM; ++d) {
-            const int lo = (int)ceilf(p[d]) - g.S[d];
-            hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
-        }
-        if (hit) {
-            const int pos = atomicAdd(&f.ncand, 1);
-            if (pos < kNC) f.tmp[pos] = k;
-        }
-    }
-    __syncthreads();
-    const int nc = f.ncand;
-    if (nst > kStage || nc > kNC) {
-        if (tile0 < 0 && tid == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = tile;
-        if (MMA && warp == 0) tc::tmem_dealloc(f.tmem, 32);
-        return;  // block-uniform: the per-voxel kernel takes this tile
-    }
-    for (int i = tid; i < nc; i += kThreads) {
-        const int k = f.tmp[i];
-        int r = 0;
-        for (int j = 0; j < nc; ++j) r += (f.tmp[j] < k);
-        f.cand[r] = k;
-        const float* row = ctr + (int64_t)k * g.CW;
-        f.cpos[r][0] = row[C];
-        f.cpos[r][1] = row[C + 1];
-        f.cpos[r][2] = row[C + 2];
-    }
-    __syncthreads();
-    for (int i = tid; i < kNC * CT; i += kThreads) {
+    // the listed centres' features (rows beyond nc are never read)
+    for (int i = tid; i < nc * CT; i += kThreads) {
         const int r = i / CT, c = i % CT;
-        cf[i] = (r < nc && c < C) ? ctr[(int64_t)f.cand[r] * g.CW + c] : 0.0f;
+        cf[i] = c < C ? ctr[(int64_t)f.cand[r] * g.CW + c] : 0.0f;
     }
     __syncthreads();
 
@@ -523,15 +550,26 @@ int launch_hc_ct(sslic_ctx* c, const float* img, int32_t* labels, cudaStream_t s
     const int ntx = (int)((g.N[0] + TL::TX - 1) / TL::TX), nty = (int)((g.N[1] + TL::TY - 1) / TL::TY);
     const int64_t ntiles = hc_num_tiles(g);
     constexpr size_t smem = hc::smem_bytes<CT, MMA>();
-    int rc = cuda_check(c, cudaFuncSetAttribute(hc::hc_tile_kernel<NDIM, MMA, CT>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                        "smem attribute");
-    if (rc) return rc;
+    // the shared-memory limit is raised once per device (a host call that
+    // otherwise costs every launch of this short kernel)
+    static std::atomic<unsigned> smem_set{0};
+    const unsigned dbit = 1u << (c->device & 31);
+    int rc;
+    if (!(smem_set.load(std::memory_order_relaxed) & dbit)) {
+        if ((rc = cuda_check(c, cudaFuncSetAttribute(hc::hc_tile_kernel<NDIM, MMA, CT>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                             "smem attribute")))
+            return rc;
+        smem_set.fetch_or(dbit);
+    }
     if ((rc = cuda_check(c, cudaMemsetAsync(w.ovf_count, 0, sizeof(unsigned), st), "memset ovf"))) return rc;
+    // the tiles' candidate records (not for the one-tile probe)
+    const bool lists = w.tile_lists && tile0 < 0;
+    if (lists && (rc = launch_tile_lists(c, NDIM, TL::TX, TL::TY, TL::TZ, ntx, nty, 0, ntiles, st))) return rc;
     const int pr = tile0 < 0 ? prof_begin(c, SSLIC_PHASE_ASSIGN, st) : -1;
     hc::hc_tile_kernel<NDIM, MMA, CT><<<tile0 < 0 ? (unsigned)ntiles : 1u, hc::kThreads, smem, st>>>(
         g, img, w.ctr, w.bin_start, w.bin_items, labels, w.acc, w.facc, w.ovf_tiles, w.ovf_count, w.hc_err,
-        w.hc_rechecks, ntx, nty, tile0, dbg_dots, dbg_cand, dbg_mu);
+        w.hc_rechecks, ntx, nty, tile0, dbg_dots, dbg_cand, dbg_mu, lists ? w.tile_lists : nullptr);
     count_launch(c);
     prof_end(c, pr, st);
     if ((rc = cuda_check(c, cudaGetLastError(), "hc_tile_kernel"))) return rc;

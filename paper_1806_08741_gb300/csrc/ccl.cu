@@ -211,7 +211,6 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int Lp = __shfl_up_sync(0xffffffffu, L, 1);
         const unsigned m = __ballot_sync(0xffffffffu, lane == 0 || L != Lp);
         lab[e] = L;
-        sz[e] = 0u;
         const int head = 31 - __clz(m & (lt | (1u << lane)));
         par[e] = L == INT_MIN ? -1 : (e - lane + head);
     }
@@ -220,7 +219,9 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     //     in 3-D, 8 consecutive rows in 2-D), so that B2 may rely on them.  A
     //     pair of touching runs is united where its overlap starts: the voxel
     //     matches the one below and either the voxel before it does not, or
-    //     it starts a new run.
+    //     it starts a new run.  The warp first lists the pairs of all its rows
+    //     (in the sizes array, not yet in use), then unites them one per lane,
+    //     so few lanes idle while the walks run.
     if constexpr (NDIM == 1) {
 #pragma unroll 1
         for (int i = 1; i < RPW; ++i) {
@@ -228,6 +229,8 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             if (lane == 0 && lab[e] != INT_MIN && lab[e - 1] == lab[e]) uf_unite_local(par, e, e - 1, err);
         }
     } else {
+        unsigned* pl = sz + warp * (RPW * 32);  // packed pairs (a << 16 | b), a, b < 2048
+        int np = 0;
 #pragma unroll 1
         for (int i = 1; i < RPW; ++i) {
             const int e = (warp * RPW + i) * 32 + lane;
@@ -235,8 +238,12 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             const int yl = (e / TX) % TY;
             const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
             const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
-            if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite_local(par, e, e - TX, err);
+            const unsigned want = my & (starts | ~(my << 1));
+            if (want >> lane & 1u) pl[np + __popc(want & lt)] = ((unsigned)e << 16) | (unsigned)(e - TX);
+            np += __popc(want);
         }
+        __syncwarp();
+        for (int j = lane; j < np; j += 32) uf_unite_local(par, (int)(pl[j] >> 16), (int)(pl[j] & 0xffffu), err);
     }
     __syncthreads();
     // B2. unions across warps (atomic linking): along z in 3-D, along y at
@@ -255,6 +262,8 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         if ((my & (starts | ~(my << 1))) >> lane & 1u) uf_unite_local(par, e, e - TX, err);
     } else {
         constexpr int P = TX * TY;
+        unsigned* pl = sz + warp * (RPW * 32);  // listed as in B1, then united one per lane
+        int np = 0;
 #pragma unroll 1
         for (int i = 0; i < RPW; ++i) {
             const int e = (warp * RPW + i) * 32 + lane;
@@ -265,8 +274,11 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             const bool via_y = zm && yl > 0 && lab[e - TX] == L && lab[e - TX - P] == L;
             const unsigned mz = __ballot_sync(0xffffffffu, zm);
             const unsigned want = mz & (starts | ~(mz << 1)) & ~__ballot_sync(0xffffffffu, via_y);
-            if (want >> lane & 1u) uf_unite_local(par, e, e - P, err);
+            if (want >> lane & 1u) pl[np + __popc(want & lt)] = ((unsigned)e << 16) | (unsigned)(e - P);
+            np += __popc(want);
         }
+        __syncwarp();
+        for (int j = lane; j < np; j += 32) uf_unite_local(par, (int)(pl[j] >> 16), (int)(pl[j] & 0xffffu), err);
     }
     __syncthreads();
     // C. roots: every run head (the first voxel of a run; path halving may
@@ -278,6 +290,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
         const int L = lab[e];
+        sz[e] = 0u;  // the pair lists are consumed
         if (L != INT_MIN && (lane == 0 || L != lab[e - (lane > 0)])) {
             const int r = uf_root(par, e, kCclTV, err);
             for (int x = e, n = 0; r >= 0 && x != r && n < kWalkLimit; ++n) {  // r < 0: flagged, left alone

@@ -286,12 +286,23 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     //    it -- no unions run any more, so every store writes a final root.
     //    Every parent pointer names a run head, so afterwards any voxel's
     //    root is par[par[e]].
+    //    The warp lists the heads of all its rows (in the local-id array,
+    //    not yet in use) and walks them one per lane.
+    {
+        uint16_t* hl = lidv + warp * (RPW * 32);
+        int nh = 0;
 #pragma unroll 1
-    for (int i = 0; i < RPW; ++i) {
-        const int e = (warp * RPW + i) * 32 + lane;
-        const int L = lab[e];
-        sz[e] = 0u;  // the pair lists are consumed
-        if (L != INT_MIN && (lane == 0 || L != lab[e - (lane > 0)])) {
+        for (int i = 0; i < RPW; ++i) {
+            const int e = (warp * RPW + i) * 32 + lane;
+            const int L = lab[e];
+            sz[e] = 0u;  // the pair lists are consumed
+            const unsigned hm = __ballot_sync(0xffffffffu, L != INT_MIN && (lane == 0 || L != lab[e - (lane > 0)]));
+            if (hm >> lane & 1u) hl[nh + __popc(hm & lt)] = (uint16_t)e;
+            nh += __popc(hm);
+        }
+        __syncwarp();
+        for (int j = lane; j < nh; j += 32) {
+            const int e = hl[j];
             const int r = uf_root(par, e, kCclTV, err);
             for (int x = e, n = 0; r >= 0 && x != r && n < kWalkLimit; ++n) {  // r < 0: flagged, left alone
                 const int nx = par[x];
@@ -402,6 +413,7 @@ template <int NDIM>
 struct FaceHash {
     static constexpr int kSize = NDIM == 4 ? 4096 : 2048;
     static constexpr int kShift = NDIM == 4 ? 20 : 21;  // 32 - log2(kSize)
+    static constexpr int kPairs = NDIM == 4 ? 2624 : 576;  // face pixels of a tile, at most
 };
 
 template <int NDIM>
@@ -414,11 +426,14 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
     constexpr int HS = FaceHash<NDIM>::kSize;
     __shared__ unsigned hset[HS];
+    __shared__ int2 plist[FaceHash<NDIM>::kPairs];  // the distinct pairs, united after the scan
+    __shared__ unsigned npairs;
     const int64_t tile = blockIdx.x;
     int64_t X0, Y0, Z0, W0;
     ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     const int EX = (int)imin64(TX, g.N[0] - X0), EY = (int)imin64(TY, g.N[1] - Y0), EZ = (int)imin64(TZ, g.N[2] - Z0);
     for (int i = threadIdx.x; i < HS; i += kCclThreads) hset[i] = 0u;
+    if (threadIdx.x == 0) npairs = 0u;
     __syncthreads();
     const int base_here = tile_base[tile];
     const int64_t sy = g.N[0], sz = g.N[0] * g.N[1], sw4 = sz * g.N[2];
@@ -455,8 +470,13 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
             if (old == key) break;
             h = (h + 1) & (HS - 1);
         }
-        if (fresh) uf_unite(gparent, base_here + (int)la, tile_base[nb] + (int)lb, (int)counters[0], &counters[3]);
+        if (fresh) plist[atomicAdd(&npairs, 1u)] = make_int2(base_here + (int)la, tile_base[nb] + (int)lb);
     }
+    // one union per thread (the scan leaves few fresh pairs per warp and step)
+    __syncthreads();
+    const int np = (int)npairs;
+    for (int i = threadIdx.x; i < np; i += kCclThreads)
+        uf_unite(gparent, plist[i].x, plist[i].y, (int)counters[0], &counters[3]);
 }
 
 // every record's parent becomes its root (read-only walks: a concurrent

@@ -133,6 +133,36 @@ __device__ __forceinline__ void uf_unite_local(int* par, int a, int b, unsigned*
     if (a != b) atomicExch(err, 1u);
 }
 
+// First voxels of components are kept as packed coordinates: x in the low
+// bits, then y, z and the fourth axis, each in ceil(log2 N_d) bits.  Packed
+// keys compare exactly as raster indices (dimension 0 fastest) do, so the
+// minimum over a component and the ranking of new labels are unchanged, and
+// unpacking takes shifts and masks instead of 64-bit divisions.
+struct RasterKey {
+    int sh[kMaxDims];
+    unsigned long long mask[kMaxDims];
+};
+
+static bool make_raster_key(const Geom& g, RasterKey& k)
+{
+    int s = 0;
+    for (int d = 0; d < kMaxDims; ++d) {
+        int b = 0;
+        while (((int64_t)1 << b) < g.N[d]) ++b;
+        k.sh[d] = s;
+        k.mask[d] = ((unsigned long long)1 << b) - 1ull;
+        s += b;
+    }
+    return s <= 63;
+}
+
+__device__ __forceinline__ unsigned long long raster_pack(const RasterKey& k, int64_t x, int64_t y, int64_t z,
+                                                          int64_t w)
+{
+    return (unsigned long long)x << k.sh[0] | (unsigned long long)y << k.sh[1] | (unsigned long long)z << k.sh[2] |
+           (unsigned long long)w << k.sh[3];
+}
+
 template <int NDIM>
 __device__ __forceinline__ int64_t ccl_tile_of(const Geom& g, int64_t x, int64_t y, int64_t z, int64_t w, int64_t ntx,
                                                int64_t nty, int64_t ntz)
@@ -170,7 +200,7 @@ __global__ void __launch_bounds__(kCclThreads)
 ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restrict__ lid_img,
                  int* __restrict__ tile_base, int* __restrict__ tile_cnt, int* __restrict__ comp_label, unsigned* __restrict__ comp_size,
                  unsigned long long* __restrict__ comp_first, int* __restrict__ gparent,
-                 unsigned* __restrict__ counters, int64_t m_cap, int64_t ntx, int64_t nty, int64_t ntz)
+                 unsigned* __restrict__ counters, int64_t m_cap, RasterKey rk, int64_t ntx, int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
@@ -182,6 +212,9 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     __shared__ uint16_t lidv[kCclTV];
     __shared__ unsigned sz[kCclTV];
     __shared__ unsigned rowoff[kRows];
+    __shared__ unsigned rhead[kRows];  // per row: lanes that start a run (of any label)
+    __shared__ unsigned vhead[kRows];  // ... and start a run of a voxel inside the image
+    __shared__ unsigned rroot[kRows];  // ... and are the root of their local component
     __shared__ unsigned s_total;
     __shared__ int s_base;
 
@@ -194,6 +227,11 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     const int ez = (int)imin64(TZ, g.N[2] - Z0);
     const unsigned lt = (1u << lane) - 1u;
     unsigned* err = &counters[3];
+    // voxel index of tile element e: the tile origin plus in-tile offsets
+    const int64_t p0 = vidx(g, X0, Y0, Z0, W0), sy = g.N[0], sxy = g.N[0] * g.N[1];
+    auto vox = [&](int e) -> int64_t {
+        return p0 + e % TX + (int64_t)((e / TX) % TY) * sy + (int64_t)(e / (TX * TY)) * sxy;
+    };
 
     // A. labels in (all of the warp's rows in flight at once), run heads
     int Lr[RPW];
@@ -202,7 +240,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int e = (warp * RPW + i) * 32 + lane;
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         const bool v = xl < ex && yl < ey && zl < ez;
-        Lr[i] = v ? labels[vidx(g, X0 + xl, Y0 + yl, Z0 + zl, W0)] : INT_MIN;
+        Lr[i] = v ? labels[vox(e)] : INT_MIN;
     }
 #pragma unroll
     for (int i = 0; i < RPW; ++i) {
@@ -210,7 +248,12 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int L = Lr[i];
         const int Lp = __shfl_up_sync(0xffffffffu, L, 1);
         const unsigned m = __ballot_sync(0xffffffffu, lane == 0 || L != Lp);
+        const unsigned vm = __ballot_sync(0xffffffffu, L != INT_MIN);
         lab[e] = L;
+        if (lane == 0) {
+            rhead[warp * RPW + i] = m;
+            vhead[warp * RPW + i] = m & vm;
+        }
         const int head = 31 - __clz(m & (lt | (1u << lane)));
         par[e] = L == INT_MIN ? -1 : (e - lane + head);
     }
@@ -236,7 +279,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             const int e = (warp * RPW + i) * 32 + lane;
             const int L = lab[e];
             const int yl = (e / TX) % TY;
-            const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
+            const unsigned starts = rhead[warp * RPW + i];
             const unsigned my = __ballot_sync(0xffffffffu, yl > 0 && L != INT_MIN && lab[e - TX] == L);
             const unsigned want = my & (starts | ~(my << 1));
             if (want >> lane & 1u) pl[np + __popc(want & lt)] = ((unsigned)e << 16) | (unsigned)(e - TX);
@@ -269,7 +312,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
             const int e = (warp * RPW + i) * 32 + lane;
             const int L = lab[e];
             const int yl = (e / TX) % TY, zl = e / P;
-            const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || L != lab[e - (lane > 0)]);
+            const unsigned starts = rhead[warp * RPW + i];
             const bool zm = zl > 0 && L != INT_MIN && lab[e - P] == L;
             const bool via_y = zm && yl > 0 && lab[e - TX] == L && lab[e - TX - P] == L;
             const unsigned mz = __ballot_sync(0xffffffffu, zm);
@@ -294,9 +337,8 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
 #pragma unroll 1
         for (int i = 0; i < RPW; ++i) {
             const int e = (warp * RPW + i) * 32 + lane;
-            const int L = lab[e];
             sz[e] = 0u;  // the pair lists are consumed
-            const unsigned hm = __ballot_sync(0xffffffffu, L != INT_MIN && (lane == 0 || L != lab[e - (lane > 0)]));
+            const unsigned hm = vhead[warp * RPW + i];
             if (hm >> lane & 1u) hl[nh + __popc(hm & lt)] = (uint16_t)e;
             nh += __popc(hm);
         }
@@ -312,14 +354,19 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         }
     }
     __syncthreads();
+    // Every voxel's parent becomes its root (-1 where the invariant broke,
+    // which is reported): a concurrent reader of par[h] sees the root either
+    // way.  The roots of each row are counted and their lanes kept.
     unsigned cnt_row = 0;  // lane i < RPW: roots in row warp * RPW + i
 #pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
         const int h = par[e];
-        const int r = h < 0 ? -1 : par[h];
-        if (r >= 0 && par[r] != r) atomicExch(err, 1u);  // broken invariant: reported, never used as an index
+        int r = h < 0 ? -1 : par[h];
+        if (r >= 0 && par[r] != r) { atomicExch(err, 1u); r = -1; }  // broken invariant: never used as an index
+        if (r != h) par[e] = r;
         const unsigned rm = __ballot_sync(0xffffffffu, r == e);
+        if (lane == 0) rroot[warp * RPW + i] = rm;
         if (lane == i) cnt_row = __popc(rm);
     }
     // D. rank the roots (raster order = row order, then lane order)
@@ -351,26 +398,20 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
 #pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
-        const int h = par[e];
-        const int r = h < 0 ? -1 : par[h];
-        const unsigned rm = __ballot_sync(0xffffffffu, r == e);
-        if (r == e) lidv[e] = (uint16_t)(rowoff[warp * RPW + i] + __popc(rm & lt));
+        const unsigned rm = rroot[warp * RPW + i];
+        if (rm >> lane & 1u) lidv[e] = (uint16_t)(rowoff[warp * RPW + i] + __popc(rm & lt));
     }
     __syncthreads();
-    // E. local ids out; sizes per run; par[] becomes the root of every voxel
+    // E. local ids out; sizes per run
 #pragma unroll 1
     for (int i = 0; i < RPW; ++i) {
         const int e = (warp * RPW + i) * 32 + lane;
-        const int h = par[e];
-        int r = h < 0 ? -1 : par[h];
-        if (r >= 0 && par[r] != r) r = -1;  // flagged above
-        const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
-        const int L = lab[e];
-        const bool head = lane == 0 || L != lab[e - (lane > 0)];  // first voxel of a run (of any label)
-        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        const int r = par[e];
+        const unsigned hm = rhead[warp * RPW + i];  // first voxels of runs (of any label)
+        const bool head = hm >> lane & 1u;
         if (r >= 0) {
             const uint16_t l = lidv[r];
-            lid_img[vidx(g, X0 + xl, Y0 + yl, Z0 + zl, W0)] = l;
+            lid_img[vox(e)] = l;
             if (head) {
                 const unsigned later = hm & ~(lt | (1u << lane));
                 const int len = (later ? __ffs(later) - 1 : 32) - lane;
@@ -385,7 +426,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         comp_label[r] = lab[e];
         comp_size[r] = sz[lidv[e]];
-        comp_first[r] = (unsigned long long)vidx(g, X0 + xl, Y0 + yl, Z0 + zl, W0);
+        comp_first[r] = raster_pack(rk, X0 + xl, Y0 + yl, Z0 + zl, W0);
         gparent[r] = r;
     }
     if (tid == 0) {
@@ -482,18 +523,39 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
 // every record's parent becomes its root (read-only walks: a concurrent
 // store only ever replaces a parent by the root), and the root collects the
 // component's size and first voxel
+constexpr int kFlattenBatch = 2;
 __global__ void ccl_flatten_kernel(int* gparent, const unsigned* __restrict__ comp_size,
                                    const unsigned long long* __restrict__ comp_first,
                                    unsigned long long* __restrict__ root_size,
                                    unsigned long long* __restrict__ root_first, unsigned* counters)
 {
+    // kFlattenBatch records a grid stride apart per thread: their parents,
+    // sizes and first voxels are loaded together before the walks
     const int64_t M = counters[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const int r = uf_root(gparent, (int)i, (int)M, &counters[3]);
-        if (r < 0) continue;  // flagged
-        gparent[i] = r;
-        atomicAdd(&root_size[r], (unsigned long long)comp_size[i]);
-        atomicMin(&root_first[r], comp_first[i]);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const volatile int* vp = gparent;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < M; i0 += stride * kFlattenBatch) {
+        int par[kFlattenBatch];
+        unsigned cs[kFlattenBatch];
+        unsigned long long cf[kFlattenBatch];
+#pragma unroll
+        for (int b = 0; b < kFlattenBatch; ++b) {
+            const int64_t i = i0 + b * stride;
+            const bool in = i < M;
+            par[b] = in ? vp[i] : -1;
+            cs[b] = in ? comp_size[i] : 0u;
+            cf[b] = in ? comp_first[i] : 0ull;
+        }
+#pragma unroll
+        for (int b = 0; b < kFlattenBatch; ++b) {
+            const int64_t i = i0 + b * stride;
+            if (i >= M) continue;
+            const int r = par[b] == (int)i ? (int)i : uf_root(gparent, par[b], (int)M, &counters[3]);
+            if (r < 0) continue;  // flagged
+            if (r != par[b]) gparent[i] = r;
+            atomicAdd(&root_size[r], (unsigned long long)cs[b]);
+            atomicMin(&root_first[r], cf[b]);
+        }
     }
 }
 
@@ -535,6 +597,7 @@ __global__ void conn_phase1_kernel(Geom g, const float* __restrict__ ctr, const 
 
 constexpr int kPendingMerge = -2;
 constexpr int kPendingNew = -3;
+constexpr int kPhase2Batch = 2;
 
 template <int NDIM>
 __global__ void conn_phase2_kernel(Geom g, const int* __restrict__ gparent, const int* __restrict__ comp_label,
@@ -543,32 +606,65 @@ __global__ void conn_phase2_kernel(Geom g, const int* __restrict__ gparent, cons
                                    const uint8_t* __restrict__ fin, const uint16_t* __restrict__ lid_img,
                                    const int* __restrict__ tile_base, int* __restrict__ out_label,
                                    int* __restrict__ link, unsigned long long* __restrict__ new_key,
-                                   int* __restrict__ new_val, unsigned* __restrict__ counters, int64_t ntx,
-                                   int64_t nty, int64_t ntz)
+                                   int* __restrict__ new_val, unsigned* __restrict__ counters, RasterKey rk,
+                                   int64_t ntx, int64_t nty, int64_t ntz)
 {
+    // kPhase2Batch records a grid stride apart per thread, their loads issued
+    // together (the merge lookup is two dependent random loads)
     const int64_t M = counters[0];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        if (gparent[i] != (int)i) continue;
-        if (fin[i]) { out_label[i] = comp_label[i]; continue; }
-        const unsigned long long f = root_first[i];
-        if (4ull * root_size[i] > (unsigned long long)g.sprod || f == 0ull) {
-            unsigned pos = atomicAdd(&counters[2], 1u);
-            new_key[pos] = f;
-            new_val[pos] = (int)i;
-            out_label[i] = kPendingNew;
-            continue;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < M; i0 += stride * kPhase2Batch) {
+        bool root[kPhase2Batch], merge[kPhase2Batch];
+        uint8_t fn[kPhase2Batch];
+        unsigned long long f[kPhase2Batch], sz[kPhase2Batch];
+        int64_t tix[kPhase2Batch], vix[kPhase2Batch];
+#pragma unroll
+        for (int b = 0; b < kPhase2Batch; ++b) {
+            const int64_t i = i0 + b * stride;
+            root[b] = i < M && gparent[i] == (int)i;
         }
-        int64_t x[kMaxDims];
-        unsigned long long r = f;
-        for (int d = 0; d < kMaxDims; ++d) {
-            x[d] = (int64_t)(r % (unsigned long long)g.N[d]);
-            r /= (unsigned long long)g.N[d];
+#pragma unroll
+        for (int b = 0; b < kPhase2Batch; ++b) {
+            const int64_t i = i0 + b * stride;
+            fn[b] = root[b] ? fin[i] : 0;
+            f[b] = root[b] ? root_first[i] : 0ull;
+            sz[b] = root[b] ? root_size[i] : 0ull;
         }
-        int d = 0;
-        while (x[d] == 0) ++d;
-        x[d] -= 1;
-        link[i] = gparent[gid_of<NDIM>(g, lid_img, tile_base, x[0], x[1], x[2], x[3], ntx, nty, ntz)];
-        out_label[i] = kPendingMerge;
+#pragma unroll
+        for (int b = 0; b < kPhase2Batch; ++b) {
+            const int64_t i = i0 + b * stride;
+            merge[b] = false;
+            tix[b] = vix[b] = 0;
+            if (!root[b]) continue;
+            if (fn[b]) { out_label[i] = comp_label[i]; continue; }
+            if (4ull * sz[b] > (unsigned long long)g.sprod || f[b] == 0ull) {
+                unsigned pos = atomicAdd(&counters[2], 1u);
+                new_key[pos] = f[b];
+                new_val[pos] = (int)i;
+                out_label[i] = kPendingNew;
+                continue;
+            }
+            int64_t x[kMaxDims];
+#pragma unroll
+            for (int d = 0; d < kMaxDims; ++d) x[d] = (int64_t)((f[b] >> rk.sh[d]) & rk.mask[d]);
+            bool stepped = false;  // x - e_d for the smallest d with x_d > 0 (f != 0, so there is one)
+#pragma unroll
+            for (int d = 0; d < kMaxDims; ++d)
+                if (!stepped && x[d] > 0) { x[d] -= 1; stepped = true; }
+            tix[b] = ccl_tile_of<NDIM>(g, x[0], x[1], x[2], x[3], ntx, nty, ntz);
+            vix[b] = vidx(g, x[0], x[1], x[2], x[3]);
+            merge[b] = true;
+        }
+        int at[kPhase2Batch];
+#pragma unroll
+        for (int b = 0; b < kPhase2Batch; ++b) at[b] = merge[b] ? tile_base[tix[b]] + (int)lid_img[vix[b]] : 0;
+#pragma unroll
+        for (int b = 0; b < kPhase2Batch; ++b) {
+            if (!merge[b]) continue;
+            const int64_t i = i0 + b * stride;
+            link[i] = gparent[at[b]];
+            out_label[i] = kPendingMerge;
+        }
     }
 }
 
@@ -633,68 +729,100 @@ __global__ void assign_new_kernel(const int* __restrict__ val, int* __restrict__
         out_label[val[r]] = (int)(K + r);
 }
 
+// Each thread takes kResolveBatch records a grid stride apart and issues
+// their loads together, so the dependent loads of one record (its link, then
+// the label there) overlap those of the others.
+constexpr int kResolveBatch = 4;
 __global__ void conn_resolve_kernel(const int* __restrict__ gparent, const int* __restrict__ link,
                                     volatile int* out_label, unsigned* counters)
 {
     const int64_t M = counters[0];
     const int* ol = const_cast<const int*>(out_label);  // plain loads for the filter
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        if (gparent[i] != (int)i || ol[i] != kPendingMerge) continue;
-        int j = link[i];
-        int o = out_label[j];
-        // pending merge: follow its link (first voxels strictly decrease, so
-        // the walk is shorter than the component count)
-        for (int64_t step = 0; o < 0; ++step) {
-            if (step > M) { atomicExch(&counters[3], 1u); o = 0; break; }
-            j = link[j];
-            o = out_label[j];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < M; i0 += stride * kResolveBatch) {
+        bool pend[kResolveBatch];
+        int j[kResolveBatch], o[kResolveBatch];
+#pragma unroll
+        for (int b = 0; b < kResolveBatch; ++b) {
+            const int64_t i = i0 + b * stride;
+            pend[b] = i < M && gparent[i] == (int)i && ol[i] == kPendingMerge;
         }
-        out_label[i] = o;
+#pragma unroll
+        for (int b = 0; b < kResolveBatch; ++b) j[b] = pend[b] ? link[i0 + b * stride] : 0;
+#pragma unroll
+        for (int b = 0; b < kResolveBatch; ++b) o[b] = pend[b] ? out_label[j[b]] : 0;
+        // a pending merge that links to another pending one follows the links
+        // on (first voxels strictly decrease, so the walk is shorter than the
+        // component count)
+#pragma unroll
+        for (int b = 0; b < kResolveBatch; ++b) {
+            if (!pend[b]) continue;
+            for (int64_t step = 0; o[b] < 0; ++step) {
+                if (step > M) { atomicExch(&counters[3], 1u); o[b] = 0; break; }
+                j[b] = link[j[b]];
+                o[b] = out_label[j[b]];
+            }
+            out_label[i0 + b * stride] = o[b];
+        }
     }
 }
 
 template <int NDIM>
-__global__ void __launch_bounds__(kCclThreads)
+__global__ void __launch_bounds__(kCclThreads, 8)
 conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
                     const int* __restrict__ tile_cnt, const int* __restrict__ gparent,
                     const int* __restrict__ out_label, const int* __restrict__ comp_label,
                     int32_t* __restrict__ labels_out, int inplace, int64_t ntx, int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
-    constexpr int TX = Cfg::TX, TY = Cfg::TY;
-    __shared__ int tab[kCclTV];       // local component -> output label
-    __shared__ uint8_t chg[kCclTV];   // ... and whether it differs from the input label
+    constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
+    __shared__ int tab[kCclTV];  // local component -> output label
     const int64_t tile = blockIdx.x;
     int64_t X0, Y0, Z0, W0;
     ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
-    const int base = tile_base[tile];
-    const int nloc = tile_cnt[tile];
-    int any = 0;
-    for (int l = threadIdx.x; l < nloc; l += kCclThreads) {
-        const int r = base + l;
-        const int G = gparent[r];
-        const int o = out_label[G];
-        tab[l] = o;
-        chg[l] = (o != comp_label[r]) ? 1 : 0;
-        any |= chg[l];
-    }
-    // in place, a tile none of whose components changes label is left alone
-    if (!__syncthreads_or(any) && inplace) return;
-    // the thread's voxels: all local ids in flight first, then the stores
+    // the thread's voxels: their local ids are loaded first, in flight while
+    // the table is built (0xffff marks a voxel outside the image)
     constexpr int PT = kCclTV / kCclThreads;
-    int64_t qv[PT];
-    int lv[PT];
+    static_assert(PT % 2 == 0, "local ids are kept two per register");
+    const int64_t p0 = vidx(g, X0, Y0, Z0, W0), sy = g.N[0], sxy = g.N[0] * g.N[1];
+    const int ex = (int)imin64(TX, g.N[0] - X0), ey = (int)imin64(TY, g.N[1] - Y0), ez = (int)imin64(TZ, g.N[2] - Z0);
+    auto inside = [&](int e) { return e % TX < ex && (e / TX) % TY < ey && e / (TX * TY) < ez; };
+    auto vox = [&](int e) -> int64_t {
+        return p0 + e % TX + (int64_t)((e / TX) % TY) * sy + (int64_t)(e / (TX * TY)) * sxy;
+    };
+    unsigned lv[PT / 2];
 #pragma unroll
     for (int i = 0; i < PT; ++i) {
         const int e = threadIdx.x + i * kCclThreads;
-        const int64_t x = X0 + e % TX, y = Y0 + (e / TX) % TY, z = Z0 + e / (TX * TY);
-        const bool in = x < g.N[0] && y < g.N[1] && z < g.N[2];
-        qv[i] = in ? vidx(g, x, y, z, W0) : -1;
-        lv[i] = in ? (int)lid_img[qv[i]] : 0;
+        const unsigned l = inside(e) ? (unsigned)lid_img[vox(e)] : 0xffffu;
+        if (i % 2 == 0) lv[i / 2] = l;
+        else lv[i / 2] |= l << 16;
     }
+    const int base = tile_base[tile];
+    const int nloc = tile_cnt[tile];
+    // the table: two records per thread and pass, so that both records'
+    // dependent loads (parent, then its label) are in flight together
+    int any = 0;
+    for (int l = threadIdx.x; l < nloc; l += 2 * kCclThreads) {
+        const bool two = l + kCclThreads < nloc;
+        const int r0 = base + l, r1 = two ? r0 + kCclThreads : r0;
+        const int G0 = gparent[r0], G1 = gparent[r1];
+        const int c0 = comp_label[r0], c1 = comp_label[r1];
+        const int o0 = out_label[G0], o1 = out_label[G1];
+        tab[l] = o0;
+        if (two) tab[l + kCclThreads] = o1;
+        any |= (o0 != c0) | (o1 != c1);
+    }
+    // in place, a tile none of whose components changes label is left alone;
+    // otherwise all of its voxels are stored, so that every 32-byte sector is
+    // written whole
+    if (!__syncthreads_or(any) && inplace) return;
 #pragma unroll
-    for (int i = 0; i < PT; ++i)
-        if (qv[i] >= 0 && lv[i] < nloc && (!inplace || chg[lv[i]])) labels_out[qv[i]] = tab[lv[i]];
+    for (int i = 0; i < PT; ++i) {
+        const int e = threadIdx.x + i * kCclThreads;
+        const unsigned l = (lv[i / 2] >> (16 * (i % 2))) & 0xffffu;
+        if (l < (unsigned)nloc) labels_out[vox(e)] = tab[l];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -711,12 +839,14 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     const int64_t ntiles = ntx * nty * ntz * g.N[3];  // one slice of tiles per index along a fourth axis
     int rc;
     unsigned hc[4];
+    RasterKey rk;
+    if (!make_raster_key(g, rk)) return set_error(c, SSLIC_EUNSUPPORTED, "packed voxel coordinates exceed 63 bits");
     const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
     for (int attempt = 0; attempt < 2; ++attempt) {
         if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
         ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
                                                               w.comp_label, w.comp_size, w.comp_first, w.gparent,
-                                                              w.counters, w.m_cap, ntx, nty, ntz);
+                                                              w.counters, w.m_cap, rk, ntx, nty, ntz);
         count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
         if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -737,9 +867,12 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     const int gb = c->sms * 8;
-    // per-record passes: one thread per record, so the walks' latencies overlap
-    const unsigned gm = (unsigned)imax64(1, imin64((M + 255) / 256, (int64_t)1 << 30));
-    ccl_flatten_kernel<<<gm, 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
+    // per-record passes: a few records per thread, all of them in flight at
+    // once, so that the walks' latencies overlap
+    auto rec_grid = [M](int batch) {
+        return (unsigned)imax64(1, imin64((M + 256 * batch - 1) / (256 * batch), (int64_t)1 << 30));
+    };
+    ccl_flatten_kernel<<<rec_grid(kFlattenBatch), 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
                                            w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
@@ -747,9 +880,9 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
                                                                  w.gparent, w.root_size, w.fin, ntx, nty, ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase1_kernel"))) return rc;
-    conn_phase2_kernel<NDIM><<<gm, 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
+    conn_phase2_kernel<NDIM><<<rec_grid(kPhase2Batch), 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
                                                   w.lid, w.tile_base, w.out_label, w.link, w.new_key, w.new_val,
-                                                  w.counters, ntx, nty, ntz);
+                                                  w.counters, rk, ntx, nty, ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase2_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -792,7 +925,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
         count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "assign_new_kernel"))) return rc;
     }
-    conn_resolve_kernel<<<gm, 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
+    conn_resolve_kernel<<<rec_grid(kResolveBatch), 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
     conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,

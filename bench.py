@@ -328,6 +328,18 @@ def run_ours(args, w):
         h_cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, pin_memory=True)
         ctx.run_host(h_img, h_lab, h_cen, stream=stream)   # warm-up (allocates device buffers)
         torch.cuda.synchronize()
+        # this machine's host link on the same buffers, to read the end-to-end
+        # figure against (h_img holds the device image, so the upload
+        # rewrites it unchanged; the label download is overwritten below)
+        link = {}
+        for name, dst, src in (("h2d", img, h_img), ("d2h", h_lab, labels)):
+            l0 = torch.cuda.Event(enable_timing=True)
+            l1 = torch.cuda.Event(enable_timing=True)
+            l0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            l1.record(stream)
+            torch.cuda.synchronize()
+            link[name + "_gbs"] = src.numel() * src.element_size() / (l0.elapsed_time(l1) / 1e3) / 1e9
         if dist:
             dist.barrier()
         n_e2e = max(1, min(args.steps, 3))
@@ -342,7 +354,8 @@ def run_ours(args, w):
         e2e = {"value": job_throughput(world, V, iters, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(h_img.numel() * h_img.element_size()),
                "d2h_bytes_per_step": int(h_lab.numel() * 4 + h_cen.numel() * 4),
-               "ms_per_step": dt * 1e3, "ms_per_call": calls, "labels_equal_device_run": same}
+               "ms_per_step": dt * 1e3, "ms_per_call": calls, "labels_equal_device_run": same,
+               "host_link": link}
         del h_img, h_lab, h_cen
 
     streamed = None

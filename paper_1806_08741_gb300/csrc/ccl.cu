@@ -116,19 +116,52 @@ __device__ __noinline__ void uf_unite(int* par, int a, int b, int n, unsigned* e
     if (a != b) atomicExch(err, 1u);
 }
 
-// The same union for a tile's forest in shared memory, inlined so the walks
-// and the link use shared-memory instructions
+// A tile's forest in shared memory: indices are masked into the tile, so no
+// walk can leave the array, and since parents strictly decrease along a
+// chain a walk ends within kCclTV steps (a broken invariant shows up as a
+// root that is not a root, which the kernel checks and reports).
+constexpr int kTileMask = kCclTV - 1;
+static_assert((kCclTV & kTileMask) == 0, "the tile size is a power of two");
+
+__device__ __forceinline__ int uf_find_tile(int* par, int x)
+{
+    volatile int* vp = par;
+    x &= kTileMask;
+    for (int i = 0; i < kCclTV; ++i) {
+        const int p = vp[x] & kTileMask;
+        if (p == x) break;
+        const int gp = vp[p] & kTileMask;
+        if (gp == p) return p;
+        vp[x] = gp;  // path halving
+        x = gp;
+    }
+    return x;
+}
+
+__device__ __forceinline__ int uf_root_tile(const int* par, int x)
+{
+    const volatile int* vp = par;
+    x &= kTileMask;
+    for (int i = 0; i < kCclTV; ++i) {
+        const int p = vp[x] & kTileMask;
+        if (p == x) break;
+        x = p;
+    }
+    return x;
+}
+
+// The same union for a tile's forest, inlined so the walks and the link use
+// shared-memory instructions
 __device__ __forceinline__ void uf_unite_local(int* par, int a, int b, unsigned* err)
 {
-    a = uf_find(par, a, kCclTV, err);
-    b = uf_find(par, b, kCclTV, err);
-    for (int i = 0; i < kWalkLimit && a != b; ++i) {
-        if (a < 0 || b < 0) return;  // flagged
+    a = uf_find_tile(par, a);
+    b = uf_find_tile(par, b);
+    for (int i = 0; i < kCclTV && a != b; ++i) {
         if (a < b) { int t = a; a = b; b = t; }
         const int old = atomicMin(&par[a], b);
         if (old == a) return;
-        a = uf_find(par, old, kCclTV, err);
-        b = uf_find(par, b, kCclTV, err);
+        a = uf_find_tile(par, old);
+        b = uf_find_tile(par, b);
     }
     if (a != b) atomicExch(err, 1u);
 }
@@ -345,9 +378,9 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         __syncwarp();
         for (int j = lane; j < nh; j += 32) {
             const int e = hl[j];
-            const int r = uf_root(par, e, kCclTV, err);
-            for (int x = e, n = 0; r >= 0 && x != r && n < kWalkLimit; ++n) {  // r < 0: flagged, left alone
-                const int nx = par[x];
+            const int r = uf_root_tile(par, e);
+            for (int x = e, n = 0; x != r && n < kCclTV; ++n) {
+                const int nx = par[x] & kTileMask;
                 par[x] = r;
                 x = nx;
             }

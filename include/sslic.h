@@ -166,7 +166,10 @@ SSLIC_API int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* ce
 /* Connectivity enforcement (Sec. 3.1 stage 3) of a label image produced
  * with the given centres.  labels_in_dev and labels_out_dev may alias.
  * num_labels_host (may be NULL) receives K + the number of new labels.
- * Synchronises the stream once (the component count sizes the scratch). */
+ * Synchronises the stream once (the component count sizes the scratch).
+ * SSLIC_EUNSUPPORTED when more than 2^31 components or labels arise, or
+ * when a voxel's coordinates packed in ceil(log2 N_d) bits per axis need
+ * more than 63 bits (no image that fits in device memory does). */
 SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* labels_in_dev,
                        int32_t* labels_out_dev, void* stream, int64_t* num_labels_host);
 

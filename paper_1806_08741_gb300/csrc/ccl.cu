@@ -52,12 +52,13 @@ constexpr int kCclTV = 2048;
 
 // ---- union-find with atomicMin linking (parents only ever decrease) --------
 // Parent indices strictly decrease along every chain, so walks end within
-// the number of nodes; every walk is still bounded and reports a broken
-// invariant through *err instead of spinning.
+// the number of nodes.  The walks over the global records are still bounded
+// and report a broken invariant through *err instead of spinning; the
+// tile-local walks further below mask their indices into the tile instead.
 constexpr int kWalkLimit = 1 << 26;
 
-// Every walk checks its index against the forest's size n and gives up
-// (flag 2) instead of leaving it.
+// Every global walk checks its index against the forest's size n and gives
+// up (flag 2) instead of leaving it.
 __device__ __forceinline__ bool uf_bad(int x, int n, unsigned* err)
 {
     if (x >= 0 && x < n) return false;

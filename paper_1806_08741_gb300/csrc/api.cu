@@ -142,14 +142,12 @@ int ensure_ccl_capacity(sslic_ctx* c, int64_t m)
         if ((rc = dalloc(c, &w.counters, 4, "counters"))) return rc;
     }
     if (m <= w.m_cap) return SSLIC_OK;
-    dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
+    dfree(w.comp_label); dfree(w.gparent);
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
     dfree(w.new_key); dfree(w.new_val);
     w.m_cap = 0;
     const size_t n = (size_t)m;
     if ((rc = dalloc(c, &w.comp_label, n, "components"))) return rc;
-    if ((rc = dalloc(c, &w.comp_size, n, "components"))) return rc;
-    if ((rc = dalloc(c, &w.comp_first, n, "components"))) return rc;
     if ((rc = dalloc(c, &w.gparent, n, "components"))) return rc;
     if ((rc = dalloc(c, &w.root_size, n, "components"))) return rc;
     if ((rc = dalloc(c, &w.root_first, n, "components"))) return rc;
@@ -170,7 +168,7 @@ static void free_all(sslic_ctx* c)
     dfree(w.bin_count); dfree(w.bin_start); dfree(w.bin_cursor); dfree(w.bin_items); dfree(w.bin_of);
     dfree(w.scan_tmp); dfree(w.ovf_tiles); dfree(w.ovf_count); dfree(w.tile_lists); dfree(w.hc_err); dfree(w.hc_rechecks);
     dfree(w.lid); dfree(w.tile_base); dfree(w.tile_cnt); dfree(w.counters);
-    dfree(w.comp_label); dfree(w.comp_size); dfree(w.comp_first); dfree(w.gparent);
+    dfree(w.comp_label); dfree(w.gparent);
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
     dfree(w.new_key); dfree(w.new_val); dfree(w.sort_key); dfree(w.sort_val);
     dfree(w.img_dev); dfree(w.lab_dev); dfree(w.cen_dev);

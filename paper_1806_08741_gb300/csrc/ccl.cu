@@ -17,7 +17,7 @@
 //     the row runs with atomicMin linking; local roots are the
 //     tile-raster-first voxels and get dense local ids (uint16 per voxel)
 //     and global record ids (tile base + local id) with label, size and
-//     first voxel.
+//     first voxel (left where the root statistics will be collected).
 //  2. ccl_faces: union of the records across tile faces (global union-find).
 //  3. flatten, with the root statistics: component size = sum, first voxel = min.
 //  4. phase 1 (per centre) sets the final flag of its component.
@@ -232,8 +232,9 @@ __device__ __forceinline__ void ccl_tile_origin(int64_t t, int64_t ntx, int64_t 
 template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restrict__ lid_img,
-                 int* __restrict__ tile_base, int* __restrict__ tile_cnt, int* __restrict__ comp_label, unsigned* __restrict__ comp_size,
-                 unsigned long long* __restrict__ comp_first, int* __restrict__ gparent,
+                 int* __restrict__ tile_base, int* __restrict__ tile_cnt, int* __restrict__ comp_label,
+                 unsigned long long* __restrict__ root_size, unsigned long long* __restrict__ root_first,
+                 uint8_t* __restrict__ fin, int* __restrict__ gparent,
                  unsigned* __restrict__ counters, int64_t m_cap, RasterKey rk, int64_t ntx, int64_t nty, int64_t ntz)
 {
     using Cfg = CclCfg<NDIM>;
@@ -459,8 +460,9 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
         const int r = base + lidv[e];
         const int xl = e % TX, yl = (e / TX) % TY, zl = e / (TX * TY);
         comp_label[r] = lab[e];
-        comp_size[r] = sz[lidv[e]];
-        comp_first[r] = raster_pack(rk, X0 + xl, Y0 + yl, Z0 + zl, W0);
+        root_size[r] = sz[lidv[e]];
+        root_first[r] = raster_pack(rk, X0 + xl, Y0 + yl, Z0 + zl, W0);
+        fin[r] = 0;
         gparent[r] = r;
     }
     if (tid == 0) {
@@ -555,39 +557,44 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
 }
 
 // every record's parent becomes its root (read-only walks: a concurrent
-// store only ever replaces a parent by the root), and the root collects the
-// component's size and first voxel
+// store only ever replaces a parent by the root), and every record that is
+// not a root adds its own size and first voxel -- left in its root_size /
+// root_first entries by the tile pass -- into its root's.  Only roots take
+// atomics and roots add nothing, so no entry is read while it changes.
 constexpr int kFlattenBatch = 2;
-__global__ void ccl_flatten_kernel(int* gparent, const unsigned* __restrict__ comp_size,
-                                   const unsigned long long* __restrict__ comp_first,
-                                   unsigned long long* __restrict__ root_size,
-                                   unsigned long long* __restrict__ root_first, unsigned* counters)
+__global__ void ccl_flatten_kernel(int* gparent, unsigned long long* root_size, unsigned long long* root_first,
+                                   unsigned* counters)
 {
     // kFlattenBatch records a grid stride apart per thread: their parents,
-    // sizes and first voxels are loaded together before the walks
+    // then the non-roots' sizes and first voxels, are loaded together before
+    // the walks
     const int64_t M = counters[0];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const volatile int* vp = gparent;
     for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < M; i0 += stride * kFlattenBatch) {
         int par[kFlattenBatch];
-        unsigned cs[kFlattenBatch];
-        unsigned long long cf[kFlattenBatch];
+        bool child[kFlattenBatch];
+        unsigned long long cs[kFlattenBatch], cf[kFlattenBatch];
 #pragma unroll
         for (int b = 0; b < kFlattenBatch; ++b) {
             const int64_t i = i0 + b * stride;
-            const bool in = i < M;
-            par[b] = in ? vp[i] : -1;
-            cs[b] = in ? comp_size[i] : 0u;
-            cf[b] = in ? comp_first[i] : 0ull;
+            par[b] = i < M ? vp[i] : -1;
+            child[b] = i < M && par[b] != (int)i;
         }
 #pragma unroll
         for (int b = 0; b < kFlattenBatch; ++b) {
             const int64_t i = i0 + b * stride;
-            if (i >= M) continue;
-            const int r = par[b] == (int)i ? (int)i : uf_root(gparent, par[b], (int)M, &counters[3]);
+            cs[b] = child[b] ? root_size[i] : 0ull;
+            cf[b] = child[b] ? root_first[i] : 0ull;
+        }
+#pragma unroll
+        for (int b = 0; b < kFlattenBatch; ++b) {
+            if (!child[b]) continue;
+            const int64_t i = i0 + b * stride;
+            const int r = uf_root(gparent, par[b], (int)M, &counters[3]);
             if (r < 0) continue;  // flagged
             if (r != par[b]) gparent[i] = r;
-            atomicAdd(&root_size[r], (unsigned long long)cs[b]);
+            atomicAdd(&root_size[r], cs[b]);
             atomicMin(&root_first[r], cf[b]);
         }
     }
@@ -879,7 +886,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     for (int attempt = 0; attempt < 2; ++attempt) {
         if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
         ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
-                                                              w.comp_label, w.comp_size, w.comp_first, w.gparent,
+                                                              w.comp_label, w.root_size, w.root_first, w.fin, w.gparent,
                                                               w.counters, w.m_cap, rk, ntx, nty, ntz);
         count_launch(c);
         if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
@@ -893,9 +900,6 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     }
     const int64_t M = hc[0];
     if (M > INT_MAX) return set_error(c, SSLIC_EUNSUPPORTED, "more than 2^31 components");
-    if ((rc = cuda_check(c, cudaMemsetAsync(w.root_size, 0, M * sizeof(unsigned long long), st), "memset"))) return rc;
-    if ((rc = cuda_check(c, cudaMemsetAsync(w.root_first, 0xff, M * sizeof(unsigned long long), st), "memset"))) return rc;
-    if ((rc = cuda_check(c, cudaMemsetAsync(w.fin, 0, M, st), "memset"))) return rc;
     ccl_faces_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.gparent,
                                                            w.counters, ntx, nty, ntz);
     count_launch(c);
@@ -906,8 +910,7 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     auto rec_grid = [M](int batch) {
         return (unsigned)imax64(1, imin64((M + 256 * batch - 1) / (256 * batch), (int64_t)1 << 30));
     };
-    ccl_flatten_kernel<<<rec_grid(kFlattenBatch), 256, 0, st>>>(w.gparent, w.comp_size, w.comp_first, w.root_size, w.root_first,
-                                           w.counters);
+    ccl_flatten_kernel<<<rec_grid(kFlattenBatch), 256, 0, st>>>(w.gparent, w.root_size, w.root_first, w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
     conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,

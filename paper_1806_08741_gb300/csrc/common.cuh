@@ -154,9 +154,9 @@ struct Workspace {
     unsigned* counters = nullptr;       // [0] M, [1] overflow, [2] new count
     int64_t m_cap = 0;
     int* comp_label = nullptr;
-    unsigned* comp_size = nullptr;
-    unsigned long long* comp_first = nullptr;
     int* gparent = nullptr;
+    // per record: its own size and first voxel as the tile pass leaves them;
+    // after the flatten pass a root's entries hold its whole component's
     unsigned long long* root_size = nullptr;
     unsigned long long* root_first = nullptr;
     uint8_t* fin = nullptr;

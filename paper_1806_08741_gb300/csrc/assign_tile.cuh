@@ -26,12 +26,13 @@
 //     (the window test is folded into the distance);
 //  3. each warp sweeps boxes of 32 lanes x VL voxels (VL = 2 or 4 consecutive
 //     voxels along x per lane, in packed .f32x2 pairs), visiting only the
-//     centres that reach its box, and leaves the winning slot of every voxel
-//     in shared memory;
-//  4. one sweep over 16-voxel row segments writes the int32 labels with
-//     16-byte stores and sums [I, x, y, z, 1] along runs of equal slots (a
-//     run of four equal slots takes one byte-sum instruction per channel)
-//     into per-tile accumulators;
+//     centres that reach its box.  Integer images finish the box at once:
+//     each lane writes its voxels' int32 labels (one vector store) and adds
+//     every voxel's [I, x, y, z, 1] to its slot's per-tile sums with C + 2
+//     shared atomics.  Float images leave the winning slot of every voxel in
+//     shared memory instead, and
+//  4. one sweep over 16-voxel row segments writes their labels and sums the
+//     features in FP32 along runs of equal slots;
 //  5. per-tile sums leave through one uint64 atomic per (centre, field).
 // Tiles reached by more than kCap centres are handed to the per-voxel kernel.
 #pragma once
@@ -100,6 +101,10 @@ struct Smem {
     static constexpr int PPB = kF ? (PPB_RAW + 8 + 15) / 16 * 16 : PPB_RAW + 4 * ((4 - (PPB_RAW / 4) % 32 + 32) % 32);
     static constexpr int CPB = ((TZ * PPB + 15) / 16) * 16;
     static constexpr int NBOX = (TX / (G::VL * G::WX)) * (TY / G::WY) * (TZ / G::WZ);
+    // integer images take the map step inside the box pass (each voxel adds
+    // its [I, x, y, z, 1] with C + 2 shared atomics); float images keep the
+    // slot array and the row-segment sweep
+    static constexpr bool kInBox = !kF;
     alignas(16) unsigned char cd[(kCap + 1) * CandLayout<C, SH>::CDS];  // [kCap]: a dummy that reaches nothing
     uint8_t blist[NBOX][kCap + 2];       // per warp box: reaching slots, ascending, even length
     uint8_t bcnt[NBOX];
@@ -115,7 +120,7 @@ struct Smem {
     int tmp[kCap];
     int stage[kStage];
     uint32_t bmask[kCap];
-    alignas(16) uint8_t slot[TV];
+    alignas(16) uint8_t slot[kInBox ? 16 : TV];
     int nstage, ncand;
 };
 
@@ -330,6 +335,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     constexpr int SPR = TX / kSeg;  // segments per row
     static_assert(NBOX % kWarps == 0, "boxes per warp");
     static_assert(TV <= 4096 && TX <= 64 && TY <= 32 && TZ <= 8, "packed per-tile sums");
+    static_assert(!S::kInBox || C == 1 || (C == 3 && sizeof(T) == 1), "packed 64-bit feature sums");
     static_assert(NBX + NBY + NBZ <= 32, "box mask bits");
     static_assert(TX % kSeg == 0, "row segments");
 
@@ -571,6 +577,8 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
 
     // ---- 3. warp boxes: assignment ------------------------------------------
     const int lx = lane % WX, ly = (lane / WX) % WY, lz = lane / (WX * WY);
+    const bool lvec4 = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
+    const bool lvec2 = (N0 % 2 == 0) && (((uintptr_t)labels & 7) == 0);
     const uint32_t cdb = (uint32_t)__cvta_generic_to_shared(&s.cd[0]);
     constexpr int CDS = CL::CDS;
 #pragma unroll 1
@@ -647,127 +655,168 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
             take(Da, sa);
             take(Db, sb);
         }
-        uint8_t* so = &s.slot[(zl * TY + yl) * TX + xl];
-        if constexpr (VL == 2) *reinterpret_cast<uint16_t*>(so) = (uint16_t)(bs[0] | (bs[1] << 8));
-        else *reinterpret_cast<uint32_t*>(so) = (uint32_t)bs[0] | ((uint32_t)bs[1] << 8) | ((uint32_t)bs[2] << 16) |
-                                                ((uint32_t)bs[3] << 24);
+        if constexpr (S::kInBox) {
+            // map step for the lane's own voxels: labels out (one vector
+            // store when the row allows it), and [I, x, y, z, 1] of every
+            // labelled voxel into its slot's packed per-tile sums
+            const bool rowin = yl < ey && zl < ez;
+            unsigned val[C][VL];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int q = 0; q < NP; ++q) split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), val[c][2 * q], val[c][2 * q + 1]);
+            int lab[VL];
+            // copy: the lanes that share one differ in more than one axis of
+            // the box, so that they seldom add to the same slot at once
+            unsigned* const mypk = s.pk + ((lane ^ (lane >> 3)) & (S::kCopies - 1)) * S::kPkStride;
+#pragma unroll
+            for (int v = 0; v < VL; ++v) {
+                const bool in = rowin && xl + v < ex && bs[v] != kNoSlot;
+                lab[v] = in ? s.cand[bs[v]] : -1;
+                if (in) {
+                    unsigned* w = mypk + bs[v] * (C + 2);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) atomicAdd(&w[c], val[c][v]);
+                    atomicAdd(&w[C], (unsigned)(xl + v) | (1u << PackedSums::kCnt));
+                    atomicAdd(&w[C + 1], (unsigned)yl | ((unsigned)zl << PackedSums::kZ));
+                }
+            }
+            if (rowin) {
+                int32_t* lp = labels + vidx(g, X0 + xl, Y0 + yl, Z0 + zl);
+                if (xl + VL <= ex && ((VL == 4 && lvec4) || (VL == 2 && lvec2))) {
+                    if constexpr (VL == 4) *reinterpret_cast<int4*>(lp) = make_int4(lab[0], lab[1], lab[2], lab[3]);
+                    else *reinterpret_cast<int2*>(lp) = make_int2(lab[0], lab[1]);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < VL; ++v)
+                        if (xl + v < ex) lp[v] = lab[v];
+                }
+            }
+        } else {
+            uint8_t* so = &s.slot[(zl * TY + yl) * TX + xl];
+            if constexpr (VL == 2) *reinterpret_cast<uint16_t*>(so) = (uint16_t)(bs[0] | (bs[1] << 8));
+            else *reinterpret_cast<uint32_t*>(so) = (uint32_t)bs[0] | ((uint32_t)bs[1] << 8) |
+                                                    ((uint32_t)bs[2] << 16) | ((uint32_t)bs[3] << 24);
+        }
     }
     __syncthreads();
 
-    // ---- 4. row segments: labels out, run sums in -------------------------------
-    unsigned* const mypk = s.pk + (lane & (S::kCopies - 1)) * S::kPkStride;
-    const bool vec_ok = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
-    for (int sg = tid; sg < TY * TZ * SPR; sg += kThreads) {
-        // lanes of a warp take segments in different z planes (different
-        // labels, fewer same-address flushes); 2-D: consecutive segments
-        int h, yl, zl;
-        if constexpr (TZ > 1) {
-            zl = sg % TZ;
-            h = (sg / TZ) % SPR;
-            yl = sg / (TZ * SPR);
-        } else {
-            h = sg % SPR;
-            yl = sg / SPR;
-            zl = 0;
-        }
-        const int r = zl * TY + yl;
-        if (yl >= ey || zl >= ez) continue;
-        const int xs0 = h * kSeg;
-        const int n = min(kSeg, ex - xs0);
-        if (n <= 0) continue;
-        int32_t* lrow = labels + vidx(g, X0 + xs0, Y0 + yl, Z0 + zl);
-        const unsigned char* prow = s.planes + zl * S::PPB + yl * S::RPB;
-        // the segment's slots, read word by word in a lane-rotated order
-        // (spreads the lanes of a warp over the banks)
-        uint32_t sw[kSeg / 4];
-        const uint32_t* sp = reinterpret_cast<const uint32_t*>(&s.slot[r * TX + xs0]);
-#pragma unroll
-        for (int j = 0; j < kSeg / 4; ++j) {
-            const int jj = (j + (TZ > 1 ? (lane & 7) : (lane >> 3))) & (kSeg / 4 - 1);
-            sw[jj] = sp[jj];
-        }
-        int cur = kNoSlot, curlab = -1;
-        FeatAcc<T> fs[C];
-        unsigned xs = 0, cnt = 0;
-#pragma unroll
-        for (int c = 0; c < C; ++c) fs[c] = 0;
-        // start a new run at slot sl (flushing the previous one)
-        auto next_run = [&](int sl) {
-            flush_run<T, C>(mypk, cur, fs, xs, cnt, yl, zl);
-            cur = sl;
-            curlab = sl == kNoSlot ? -1 : s.cand[sl];
-#pragma unroll
-            for (int c = 0; c < C; ++c) fs[c] = 0;
-            xs = 0;
-            cnt = 0;
-        };
-        if (n == kSeg) {
+    if constexpr (!S::kInBox) {
+        // ---- 4. row segments: labels out, run sums in -------------------------------
+        unsigned* const mypk = s.pk + (lane & (S::kCopies - 1)) * S::kPkStride;
+        const bool vec_ok = (N0 % 4 == 0) && (((uintptr_t)labels & 15) == 0);
+        for (int sg = tid; sg < TY * TZ * SPR; sg += kThreads) {
+            // lanes of a warp take segments in different z planes (different
+            // labels, fewer same-address flushes); 2-D: consecutive segments
+            int h, yl, zl;
+            if constexpr (TZ > 1) {
+                zl = sg % TZ;
+                h = (sg / TZ) % SPR;
+                yl = sg / (TZ * SPR);
+            } else {
+                h = sg % SPR;
+                yl = sg / SPR;
+                zl = 0;
+            }
+            const int r = zl * TY + yl;
+            if (yl >= ey || zl >= ez) continue;
+            const int xs0 = h * kSeg;
+            const int n = min(kSeg, ex - xs0);
+            if (n <= 0) continue;
+            int32_t* lrow = labels + vidx(g, X0 + xs0, Y0 + yl, Z0 + zl);
+            const unsigned char* prow = s.planes + zl * S::PPB + yl * S::RPB;
+            // the segment's slots, read word by word in a lane-rotated order
+            // (spreads the lanes of a warp over the banks)
+            uint32_t sw[kSeg / 4];
+            const uint32_t* sp = reinterpret_cast<const uint32_t*>(&s.slot[r * TX + xs0]);
 #pragma unroll
             for (int j = 0; j < kSeg / 4; ++j) {
-                const uint32_t w = sw[j];
-                const int xq = xs0 + 4 * j;
-                int lab4[4];
-                if (sizeof(T) == 1 && w == (w & 0xffu) * 0x01010101u) {
-                    // four voxels, one slot: byte sums of the planes' words
-                    const int sl = (int)(w & 0xffu);
+                const int jj = (j + (TZ > 1 ? (lane & 7) : (lane >> 3))) & (kSeg / 4 - 1);
+                sw[jj] = sp[jj];
+            }
+            int cur = kNoSlot, curlab = -1;
+            FeatAcc<T> fs[C];
+            unsigned xs = 0, cnt = 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c) fs[c] = 0;
+            // start a new run at slot sl (flushing the previous one)
+            auto next_run = [&](int sl) {
+                flush_run<T, C>(mypk, cur, fs, xs, cnt, yl, zl);
+                cur = sl;
+                curlab = sl == kNoSlot ? -1 : s.cand[sl];
+#pragma unroll
+                for (int c = 0; c < C; ++c) fs[c] = 0;
+                xs = 0;
+                cnt = 0;
+            };
+            if (n == kSeg) {
+#pragma unroll
+                for (int j = 0; j < kSeg / 4; ++j) {
+                    const uint32_t w = sw[j];
+                    const int xq = xs0 + 4 * j;
+                    int lab4[4];
+                    if (sizeof(T) == 1 && w == (w & 0xffu) * 0x01010101u) {
+                        // four voxels, one slot: byte sums of the planes' words
+                        const int sl = (int)(w & 0xffu);
+                        if (sl != cur) next_run(sl);
+                        if (sl != kNoSlot) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c)
+                                fs[c] += __vsadu4(*reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq), 0u);
+                            xs += 4u * (unsigned)xq + 6u;
+                            cnt += 4u;
+                        }
+                        lab4[0] = lab4[1] = lab4[2] = lab4[3] = curlab;
+                    } else {
+                        uint32_t pw[C];
+                        if constexpr (sizeof(T) == 1) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c)
+                                pw[c] = *reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq);
+                        }
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int sl = (int)((w >> (8 * b)) & 0xffu);
+                            if (sl != cur) next_run(sl);
+                            if (sl != kNoSlot) {
+#pragma unroll
+                                for (int c = 0; c < C; ++c) {
+                                    if constexpr (sizeof(T) == 1) fs[c] += (pw[c] >> (8 * b)) & 0xffu;
+                                    else fs[c] += (FeatAcc<T>)*reinterpret_cast<const T*>(
+                                        prow + c * S::CPB + (xq + b) * (int)sizeof(T));
+                                }
+                                xs += (unsigned)(xq + b);
+                                cnt += 1u;
+                            }
+                            lab4[b] = curlab;
+                        }
+                    }
+                    if (vec_ok) {
+                        *reinterpret_cast<int4*>(lrow + 4 * j) = make_int4(lab4[0], lab4[1], lab4[2], lab4[3]);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) lrow[4 * j + b] = lab4[b];
+                    }
+                }
+            } else {
+                for (int b = 0; b < n; ++b) {
+                    const uint32_t wb = b < 4 ? sw[0] : (b < 8 ? sw[1] : (b < 12 ? sw[2] : sw[3]));
+                    const int sl = (int)((wb >> (8 * (b & 3))) & 0xffu);
                     if (sl != cur) next_run(sl);
                     if (sl != kNoSlot) {
 #pragma unroll
                         for (int c = 0; c < C; ++c)
-                            fs[c] += __vsadu4(*reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq), 0u);
-                        xs += 4u * (unsigned)xq + 6u;
-                        cnt += 4u;
+                            fs[c] += (FeatAcc<T>)*reinterpret_cast<const T*>(prow + c * S::CPB + (xs0 + b) * (int)sizeof(T));
+                        xs += (unsigned)(xs0 + b);
+                        cnt += 1u;
                     }
-                    lab4[0] = lab4[1] = lab4[2] = lab4[3] = curlab;
-                } else {
-                    uint32_t pw[C];
-                    if constexpr (sizeof(T) == 1) {
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-                            pw[c] = *reinterpret_cast<const uint32_t*>(prow + c * S::CPB + xq);
-                    }
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const int sl = (int)((w >> (8 * b)) & 0xffu);
-                        if (sl != cur) next_run(sl);
-                        if (sl != kNoSlot) {
-#pragma unroll
-                            for (int c = 0; c < C; ++c) {
-                                if constexpr (sizeof(T) == 1) fs[c] += (pw[c] >> (8 * b)) & 0xffu;
-                                else fs[c] += (FeatAcc<T>)*reinterpret_cast<const T*>(
-                                    prow + c * S::CPB + (xq + b) * (int)sizeof(T));
-                            }
-                            xs += (unsigned)(xq + b);
-                            cnt += 1u;
-                        }
-                        lab4[b] = curlab;
-                    }
-                }
-                if (vec_ok) {
-                    *reinterpret_cast<int4*>(lrow + 4 * j) = make_int4(lab4[0], lab4[1], lab4[2], lab4[3]);
-                } else {
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) lrow[4 * j + b] = lab4[b];
+                    lrow[b] = curlab;
                 }
             }
-        } else {
-            for (int b = 0; b < n; ++b) {
-                const uint32_t wb = b < 4 ? sw[0] : (b < 8 ? sw[1] : (b < 12 ? sw[2] : sw[3]));
-                const int sl = (int)((wb >> (8 * (b & 3))) & 0xffu);
-                if (sl != cur) next_run(sl);
-                if (sl != kNoSlot) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c)
-                        fs[c] += (FeatAcc<T>)*reinterpret_cast<const T*>(prow + c * S::CPB + (xs0 + b) * (int)sizeof(T));
-                    xs += (unsigned)(xs0 + b);
-                    cnt += 1u;
-                }
-                lrow[b] = curlab;
-            }
+            flush_run<T, C>(mypk, cur, fs, xs, cnt, yl, zl);
         }
-        flush_run<T, C>(mypk, cur, fs, xs, cnt, yl, zl);
+        __syncthreads();
     }
-    __syncthreads();
 
     // ---- 5. per-tile sums, shifted to global coordinates ----------------------
     // the copies are summed field by field (each field's total fits its width)

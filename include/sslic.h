@@ -182,8 +182,11 @@ SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const i
  * file-scope device array of about 3 MB, which every GPU that loads this
  * library holds until the process exits.  That array bounds the request:
  * K <= 16384 clusters, C <= 4 channels and at most 65536 assignment tiles
- * (a tile is 32x16x8 voxels in 3-D, 64x32 pixels in 2-D); larger requests
- * return SSLIC_EINVAL.  The first call on a device looks up the array's
+ * counted with the smallest tile (16x8x8 voxels in 3-D, 32x16 pixels in
+ * 2-D), i.e. about 67M voxels or 33.5M pixels; larger requests return
+ * SSLIC_EINVAL.  It always stages the image with plain loads (a TMA-staged
+ * tile shape recorded by sslic_autotune or sslic_tune_record runs its
+ * plain twin here).  The first call on a device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current, so make
  * it before any stream capture.  All calls share the array and it keeps the
  * previous call's contents: the sums are cleared at the start of each call,

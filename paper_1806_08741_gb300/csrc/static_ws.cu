@@ -27,7 +27,10 @@ namespace stat {
 
 constexpr int64_t kMaxK = 16384;          // clusters
 constexpr int kMaxC = 4;                  // channels
-constexpr int64_t kMaxTiles = 65536;      // assignment tiles (~268M voxels of full 3-D tiles)
+// assignment tiles; the count is taken over every base tile shape, so the
+// smallest tile sets it: 65536 tiles of 16x8x8 voxels (3-D) or 32x16
+// pixels (2-D), i.e. about 67M voxels or 33.5M pixels
+constexpr int64_t kMaxTiles = 65536;
 constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -106,6 +109,14 @@ extern "C" int sslic_iterate_static(const sslic_params* p, const void* image_dev
     c.p = *p;
     c.g = g;
     c.device = dev;
+    // the tile shape with plain-load staging: a TMA-staged shape recorded by
+    // the autotuner would need a status word and its check, which the array
+    // does not provide
+    if (has_tile_kernel(g)) {
+        int sh = tuned_tile_shape(g);
+        if (sh < 0) sh = default_tile_shape(g);
+        c.tile_shape = sh % num_base_shapes(g.n);
+    }
     if (cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SSLIC_ECUDA;
     stat::carve(c.ws, (unsigned char*)stat::g_scratch_addr[dev]);
     cudaStream_t st = (cudaStream_t)stream;

@@ -98,32 +98,75 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def _bind(L):
+    """Declare the argument and result types of a loaded oracle library."""
+    P = ctypes.POINTER(_Params)
+    vp, dp = ctypes.c_void_p, ctypes.c_void_p
+    L.oracle_num_clusters.argtypes = [P]
+    L.oracle_num_clusters.restype = ctypes.c_int64
+    L.oracle_seed.argtypes = [P, vp, dp]
+    L.oracle_gradient.argtypes = [P, vp, ctypes.c_int64]
+    L.oracle_gradient.restype = ctypes.c_double
+    L.oracle_assign.argtypes = [P, vp, dp, ctypes.c_int64, vp]
+    L.oracle_update.argtypes = [P, vp, vp, ctypes.c_int64, dp, vp, vp]
+    L.oracle_distance.argtypes = [P, dp, vp, dp]
+    L.oracle_distance.restype = ctypes.c_double
+    L.oracle_connectivity.argtypes = [P, dp, ctypes.c_int64, vp, vp, vp]
+    L.oracle_slic.argtypes = [P, vp, vp, dp, vp, vp, vp]
+    L.oracle_slic_from.argtypes = [P, vp, dp, vp, dp, vp, vp, vp]
+    L.oracle_srgb_to_lab.argtypes = [vp, ctypes.c_int64, dp]
+    L.oracle_assign_voxels.argtypes = [P, vp, dp, ctypes.c_int64, vp, ctypes.c_int64, vp, vp, vp]
+    L.oracle_assign_voxels.restype = ctypes.c_int
+    for f in ("oracle_seed", "oracle_assign", "oracle_update", "oracle_srgb_to_lab",
+              "oracle_connectivity", "oracle_slic", "oracle_slic_from"):
+        getattr(L, f).restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        P = ctypes.POINTER(_Params)
-        vp, dp = ctypes.c_void_p, ctypes.c_void_p
-        L = _lib
-        L.oracle_num_clusters.argtypes = [P]
-        L.oracle_num_clusters.restype = ctypes.c_int64
-        L.oracle_seed.argtypes = [P, vp, dp]
-        L.oracle_gradient.argtypes = [P, vp, ctypes.c_int64]
-        L.oracle_gradient.restype = ctypes.c_double
-        L.oracle_assign.argtypes = [P, vp, dp, ctypes.c_int64, vp]
-        L.oracle_update.argtypes = [P, vp, vp, ctypes.c_int64, dp, vp, vp]
-        L.oracle_distance.argtypes = [P, dp, vp, dp]
-        L.oracle_distance.restype = ctypes.c_double
-        L.oracle_connectivity.argtypes = [P, dp, ctypes.c_int64, vp, vp, vp]
-        L.oracle_slic.argtypes = [P, vp, vp, dp, vp, vp, vp]
-        L.oracle_slic_from.argtypes = [P, vp, dp, vp, dp, vp, vp, vp]
-        L.oracle_srgb_to_lab.argtypes = [vp, ctypes.c_int64, dp]
-        L.oracle_assign_voxels.argtypes = [P, vp, dp, ctypes.c_int64, vp, ctypes.c_int64, vp, vp, vp]
-        L.oracle_assign_voxels.restype = ctypes.c_int
-        for f in ("oracle_seed", "oracle_assign", "oracle_update", "oracle_srgb_to_lab",
-                  "oracle_connectivity", "oracle_slic", "oracle_slic_from"):
-            getattr(L, f).restype = ctypes.c_int
+        _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def build_variant(src_text: str, out_dir: str) -> str:
+    """Compile a modified copy of the oracle source (the tests plant known
+    mistakes in it to show that the pins catch them); returns the path of
+    the shared library, built with the same flags as build()."""
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "sslic_oracle.c")
+    with open(src, "w") as f:
+        f.write(src_text)
+    out = os.path.join(out_dir, "liboracle_variant.so")
+    cmd = ["cc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-I", _HERE,
+           "-fPIC", "-shared", "-o", out, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+class use_library:
+    """Context manager: route every oracle call through the library at
+    ``path`` (a variant from build_variant) until the block ends."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = lib()
+        _lib = _bind(ctypes.CDLL(self.path))
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+        return False
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _ptr(a: np.ndarray):

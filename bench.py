@@ -54,6 +54,12 @@ TRAFFIC_BYTES = {
 }
 
 
+# thread instructions per voxel of the dominant kernel (ncu
+# smsp__inst_executed.sum x 32 / voxels on the profiling workload), keyed by
+# the SHA-256 of the kernel's source file like TRAFFIC_BYTES
+INST_PER_VOXEL = {}
+
+
 def _sha(path):
     with open(path, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
@@ -156,9 +162,27 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(w, edge):
-    """The corner crop [0, edge)^n of the workload's image, run by the
-    single-threaded oracle with the workload's parameters."""
+def host_cores():
+    """Host cores this process may run on, and the CPU model if known."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Architecture"):
+                model += (", " if model else "") + ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return n, model
+
+
+def oracle_sample(w, edge, threads=None):
+    """The corner crop [0, edge)^n of the workload's image, run by the oracle
+    with the workload's parameters: single-threaded (threads None), or in the
+    paper's region-decomposed form on `threads` host threads (same results)."""
     import numpy as np
 
     import oracle
@@ -169,12 +193,15 @@ def oracle_sample(w, edge):
     p = oracle.params_for(img, w.grid, m=w.m, max_iter=w.max_iter, perturb=w.perturb,
                           enforce_connectivity=w.connectivity)
     t0 = time.perf_counter()
-    r = oracle.slic(p, img)
+    r = oracle.slic(p, img) if threads is None else oracle.slic_regions(p, img, threads)
     dt = time.perf_counter() - t0
     vox = int(np.prod(ext))
+    form = ("single-threaded C oracle" if threads is None else
+            f"C oracle in the paper's region-decomposed form (Sec. 3.1) on {threads} host threads, "
+            "connectivity sequential")
     desc = (f"corner crop {'x'.join(map(str, ext))} of the same image (K={oracle.num_clusters(p)}), "
             f"{w.max_iter} iterations + {'connectivity' if w.connectivity else 'no connectivity'}, "
-            f"single-threaded C oracle, {dt:.1f} s")
+            f"{form}, {dt:.1f} s")
     return vox * r["iterations"] / dt / 1e9, desc, dt
 
 
@@ -184,8 +211,9 @@ def run_reference(args, w):
         return 0
     steps = []
     desc = ""
+    cores, model = host_cores()
     for i in range(args.warmup + args.steps):
-        v, desc, dt = oracle_sample(w, args.reference_edge)
+        v, desc, dt = oracle_sample(w, args.reference_edge, threads=cores)
         if i >= args.warmup:
             steps.append((v, dt))
     val = statistics.median(v for v, _ in steps)
@@ -196,7 +224,8 @@ def run_reference(args, w):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": _config(w),
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                         "host": model},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -301,16 +330,28 @@ def run_ours(args, w):
     # per (voxel, covering centre) pair the canonical D^2 costs C subtractions,
     # C products and C - 1 + n sums once the per-axis terms are tabulated per
     # tile, plus one comparison; a voxel is covered by prod_d (2 S_d) K / V
-    # windows on average; peak = 152 SMs x 128 FP32 lanes x the SM clock
+    # windows on average; peak = the device's SMs x 128 FP32 lanes x the
+    # median SM clock sampled during the timed region.  Beside it, the
+    # instruction-issue fraction: the kernel's thread instructions per voxel
+    # (ncu capture, keyed like the traffic) against 4 warp instructions per
+    # SM and clock
     roof_alu = None
     if a_calls:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
         cover = float(np.prod([2 * s_ for s_ in w.grid])) * ctx.K / V
         ops_pair = 2 * spec.channels + (spec.channels - 1) + spec.ndim + 1
-        alu_peak = 152 * 128 * 2.07e9 / 1e12
-        ach = V * cover * ops_pair / (a_ms / a_calls / 1e3) / 1e12
+        alu_peak = sms * 128 * mhz * 1e6 / 1e12
+        t_launch = a_ms / a_calls / 1e3
+        ach = V * cover * ops_pair / t_launch / 1e12
         roof_alu = {"kernel": roof["kernel"], "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": ach / alu_peak, "ops_per_voxel": cover * ops_pair, "covering_centres_per_voxel": cover,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
+                    "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median sampled SM clock)"}
+        ipv = INST_PER_VOXEL.get(src)
+        if ipv:
+            issue_peak = sms * 4 * 32 * mhz * 1e6  # thread instructions per second
+            roof_alu["issue"] = {"thread_inst_per_voxel": ipv, "frac": V * ipv / t_launch / issue_peak,
+                                 "source": "ncu smsp__inst_executed.sum x 32 / voxels of the profiling capture"}
     phases = {k: {"ms_per_step": v[0] / args.steps, "calls_per_step": v[1] / args.steps}
               for k, v in prof.items() if k in S.PHASES}
     # the iterated assign/update loop alone (bins + assignment + reduction),
@@ -379,8 +420,11 @@ def run_ours(args, w):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, _ = oracle_sample(w, args.cpu_edge)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        cores, model = host_cores()
+        v, desc, _ = oracle_sample(w, args.cpu_edge_all, threads=cores)
+        v1, desc1, _ = oracle_sample(w, args.cpu_edge)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc, "host": model,
+               "cores_1": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1}}
 
     if rank == 0:
         line = {
@@ -710,8 +754,9 @@ def main():
     ap.add_argument("--lab-only", action="store_true",
                     help="only the CIE-Lab float form of the workload (--tile-shape fixes its shape)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the CPU-baseline crop")
-    ap.add_argument("--reference-edge", type=int, default=128,
+    ap.add_argument("--cpu-edge", type=int, default=256, help="edge of the single-core CPU-baseline crop")
+    ap.add_argument("--cpu-edge-all", type=int, default=384, help="edge of the all-cores CPU-baseline crop")
+    ap.add_argument("--reference-edge", type=int, default=256,
                     help="edge of the crop each reference-arm step runs")
     ap.add_argument("--serve", action="store_true",
                     help="only the request-stream benchmark (served vs plain form)")

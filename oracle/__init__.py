@@ -21,6 +21,7 @@ _SRC = os.path.join(_HERE, "sslic_oracle.c")
 _HDR = os.path.join(_HERE, "sslic_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 
 U8, U16, F32 = 0, 1, 2
 FP32, FP64 = 0, 1
@@ -80,19 +81,26 @@ class Params:
         return p
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with the system C compiler (no fast-math, no
-    contraction) into ``oracle/_build/liboracle.so``."""
+def _compile(out: str, extra, force: bool) -> str:
     os.makedirs(_BUILD, exist_ok=True)
-    stale = (not os.path.exists(_LIB)) or force or any(
-        os.path.getmtime(s) > os.path.getmtime(_LIB) for s in (_SRC, _HDR))
+    stale = (not os.path.exists(out)) or force or any(
+        os.path.getmtime(s) > os.path.getmtime(out) for s in (_SRC, _HDR))
     if stale:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["cc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["cc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", *extra,
                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the system C compiler (no fast-math, no
+    contraction) into ``oracle/_build/liboracle.so``, and the same source
+    with OpenMP into ``liboracle_omp.so`` (the region-decomposed form of
+    ``slic_regions`` then runs on several host threads)."""
+    _compile(_LIB_OMP, ["-fopenmp"], force)
+    return _compile(_LIB, [], force)
 
 
 _lib = None
@@ -117,6 +125,10 @@ def _bind(L):
     L.oracle_srgb_to_lab.argtypes = [vp, ctypes.c_int64, dp]
     L.oracle_assign_voxels.argtypes = [P, vp, dp, ctypes.c_int64, vp, ctypes.c_int64, vp, vp, vp]
     L.oracle_assign_voxels.restype = ctypes.c_int
+    L.oracle_slic_regions.argtypes = [P, vp, vp, dp, vp, vp, vp, ctypes.c_int]
+    L.oracle_slic_regions.restype = ctypes.c_int
+    L.oracle_threads_available.argtypes = []
+    L.oracle_threads_available.restype = ctypes.c_int
     for f in ("oracle_seed", "oracle_assign", "oracle_update", "oracle_srgb_to_lab",
               "oracle_connectivity", "oracle_slic", "oracle_slic_from"):
         getattr(L, f).restype = ctypes.c_int
@@ -128,6 +140,18 @@ def lib():
     if _lib is None:
         _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+_lib_omp = None
+
+
+def lib_omp():
+    """The OpenMP build of the same source (region-decomposed form)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = _bind(ctypes.CDLL(_LIB_OMP))
+    return _lib_omp
 
 
 def build_variant(src_text: str, out_dir: str) -> str:
@@ -301,5 +325,32 @@ def slic(p: Params, image: np.ndarray, init_centres: np.ndarray | None = None) -
                                     _ptr(centres), ctypes.byref(it), ctypes.byref(res),
                                     ctypes.byref(n))
     _check(rc, "slic")
+    return {"labels": labels, "centres": centres, "iterations": int(it.value),
+            "residual": float(res.value), "num_labels": int(n.value)}
+
+
+def threads_available() -> int:
+    """Host threads the OpenMP build uses by default."""
+    return int(lib_omp().oracle_threads_available())
+
+
+def slic_regions(p: Params, image: np.ndarray, threads: int, openmp: bool = True) -> dict:
+    """The whole method in the paper's multi-threaded form (Sec. 3.1): the
+    image split into non-overlapping regions of planes, assigned and mapped
+    per region on ``threads`` host threads (OpenMP build), the per-region
+    sums merged per label.  Same results as ``slic`` bit for bit."""
+    image = _img(image)
+    K = num_clusters(p)
+    if K < 0:
+        raise RuntimeError("oracle slic_regions failed: invalid parameters")
+    labels = np.empty(image.shape[:-1], np.int32)
+    centres = np.zeros((K, p.channels + p.ndim), np.float64)
+    it = ctypes.c_int32(0)
+    res = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    L = lib_omp() if openmp else lib()
+    _check(L.oracle_slic_regions(ctypes.byref(p.to_c()), _ptr(image), _ptr(labels), _ptr(centres),
+                                 ctypes.byref(it), ctypes.byref(res), ctypes.byref(n), int(threads)),
+           "slic_regions")
     return {"labels": labels, "centres": centres, "iterations": int(it.value),
             "residual": float(res.value), "num_labels": int(n.value)}

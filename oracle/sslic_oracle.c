@@ -55,6 +55,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_OK 0
 #define ORACLE_EINVAL (-1)
@@ -356,14 +359,22 @@ static int in_window(const geom* g, int d, int64_t xd, double c)
     return (float)(xd - g->S[d]) < cf && cf <= (float)(xd + g->S[d]);
 }
 
-static int assign(const geom* g, const void* image, const double* centres, int64_t K,
-                  int32_t* labels)
+/* The assignment of the voxels in planes plo .. phi-1 of the last axis
+ * (all of them: plo = 0, phi = N_{n-1}).  A voxel sees the same centres in
+ * the same order whatever range it is assigned in, so splitting the image
+ * into such ranges leaves every label unchanged (the paper's non-overlapping
+ * regions, Sec. 3.1). */
+static int assign_planes(const geom* g, const void* image, const double* centres, int64_t K,
+                         int32_t* labels, int64_t plo, int64_t phi)
 {
     const int width = g->C + g->n;
+    const int last = g->n - 1;
+    const int64_t qlo = plo * g->stride[last], qhi = phi * g->stride[last];
+    const int64_t nq = qhi - qlo;
     float* d32 = NULL;
     double* d64 = NULL;
-    if (g->fp64) d64 = (double*)malloc((size_t)g->V * sizeof(double));
-    else d32 = (float*)malloc((size_t)g->V * sizeof(float));
+    if (g->fp64) d64 = (double*)malloc((size_t)(nq > 0 ? nq : 1) * sizeof(double));
+    else d32 = (float*)malloc((size_t)(nq > 0 ? nq : 1) * sizeof(float));
     float* f32 = (float*)malloc((size_t)g->C * sizeof(float));
     double* f64 = (double*)malloc((size_t)g->C * sizeof(double));
     int64_t* xs[ND] = {NULL};
@@ -379,10 +390,10 @@ static int assign(const geom* g, const void* image, const double* centres, int64
         return ORACLE_ENOMEM;
     }
     /* R4: reset l = undefined (-1), d = +inf */
-    for (int64_t q = 0; q < g->V; ++q) {
+    for (int64_t q = qlo; q < qhi; ++q) {
         labels[q] = -1;
-        if (g->fp64) d64[q] = INFINITY;
-        else d32[q] = INFINITY;
+        if (g->fp64) d64[q - qlo] = INFINITY;
+        else d32[q - qlo] = INFINITY;
     }
     for (int64_t k = 0; k < K; ++k) {
         const double* ctr = centres + k * width;
@@ -397,6 +408,7 @@ static int assign(const geom* g, const void* image, const double* centres, int64
             int64_t fl = (int64_t)floor(c);
             for (int64_t xd = fl - g->S[d] - 1; xd <= fl + g->S[d] + 1; ++xd) {
                 if (xd < 0 || xd >= g->N[d]) continue;
+                if (d == last && (xd < plo || xd >= phi)) continue;
                 if (in_window(g, d, xd, c)) xs[d][len[d]++] = xd;
             }
         }
@@ -413,17 +425,23 @@ static int assign(const geom* g, const void* image, const double* centres, int64
             if (g->fp64) {
                 for (int c = 0; c < g->C; ++c) f64[c] = pix(g, image, q, c);
                 double D = dist64(g, f64, x, ctr);
-                if (D < d64[q]) { d64[q] = D; labels[q] = (int32_t)k; }
+                if (D < d64[q - qlo]) { d64[q - qlo] = D; labels[q] = (int32_t)k; }
             } else {
                 for (int c = 0; c < g->C; ++c) f32[c] = (float)pix(g, image, q, c);
                 float D = dist32(g, f32, x, ctr);
-                if (D < d32[q]) { d32[q] = D; labels[q] = (int32_t)k; }
+                if (D < d32[q - qlo]) { d32[q - qlo] = D; labels[q] = (int32_t)k; }
             }
         }
     }
     free(d32); free(d64); free(f32); free(f64);
     for (int d = 0; d < ND; ++d) free(xs[d]);
     return ORACLE_OK;
+}
+
+static int assign(const geom* g, const void* image, const double* centres, int64_t K,
+                  int32_t* labels)
+{
+    return assign_planes(g, image, centres, K, labels, 0, g->N[g->n - 1]);
 }
 
 int oracle_assign(const oracle_params* p, const void* image, const double* centres,
@@ -489,6 +507,50 @@ int oracle_assign_voxels(const oracle_params* p, const void* image, const double
 
 /* ---- update (Sec. 2.2 "Update clusters", Sec. 3.1 map-reduce; R9, R10) --- */
 
+/* map: accumulate [I(x), x] of the voxels qlo .. qhi-1 per label */
+static int update_map(const geom* g, const void* image, const int32_t* labels, int64_t K, int64_t qlo,
+                      int64_t qhi, int64_t* cnt, int64_t* isum, double* fsum)
+{
+    const int width = g->C + g->n;
+    for (int64_t q = qlo; q < qhi; ++q) {
+        int32_t k = labels[q];
+        if (k < 0) continue; /* R8 */
+        if (k >= K) return ORACLE_EINVAL;
+        int64_t x[ND];
+        coords(g, q, x);
+        cnt[k] += 1;
+        for (int c = 0; c < g->C; ++c) {
+            if (g->dt == ORACLE_F32) fsum[k * g->C + c] += pix(g, image, q, c);
+            else isum[k * width + c] += pix_int(g, image, q, c);
+        }
+        for (int d = 0; d < g->n; ++d) isum[k * width + g->C + d] += x[d];
+    }
+    return ORACLE_OK;
+}
+
+/* reduce, one cluster: its new centre as the member mean (an empty cluster
+ * keeps its centre); returns the cluster's residual term sqrt(D^2(C_prev,
+ * C_new)), or -1 when it is empty */
+static double update_divide(const geom* g, int64_t k, const int64_t* cnt, const int64_t* isum,
+                            const double* fsum, double* centres)
+{
+    const int width = g->C + g->n;
+    double* row = centres + k * width;
+    if (cnt[k] == 0) return -1.0;
+    double n = (double)cnt[k];
+    double D2 = 0.0;
+    for (int j = 0; j < width; ++j) {
+        double s = (j < g->C && g->dt == ORACLE_F32) ? fsum[k * g->C + j]
+                                                      : (double)isum[k * width + j];
+        double mean = s / n;
+        double v = g->fp64 ? mean : (double)(float)mean;
+        double diff = v - row[j];
+        D2 += (j < g->C) ? diff * diff : g->w64[j - g->C] * (diff * diff);
+        row[j] = v;
+    }
+    return sqrt(D2);
+}
+
 static int update(const geom* g, const void* image, const int32_t* labels, int64_t K,
                   double* centres, int64_t* counts_out, double* residual)
 {
@@ -500,39 +562,16 @@ static int update(const geom* g, const void* image, const int32_t* labels, int64
         free(cnt); free(isum); free(fsum);
         return ORACLE_ENOMEM;
     }
-    /* map: accumulate [I(x), x] per label */
-    for (int64_t q = 0; q < g->V; ++q) {
-        int32_t k = labels[q];
-        if (k < 0) continue; /* R8 */
-        if (k >= K) { free(cnt); free(isum); free(fsum); return ORACLE_EINVAL; }
-        int64_t x[ND];
-        coords(g, q, x);
-        cnt[k] += 1;
-        for (int c = 0; c < g->C; ++c) {
-            if (g->dt == ORACLE_F32) fsum[k * g->C + c] += pix(g, image, q, c);
-            else isum[k * width + c] += pix_int(g, image, q, c);
-        }
-        for (int d = 0; d < g->n; ++d) isum[k * width + g->C + d] += x[d];
-    }
+    int rc = update_map(g, image, labels, K, 0, g->V, cnt, isum, fsum);
+    if (rc != ORACLE_OK) { free(cnt); free(isum); free(fsum); return rc; }
     /* reduce: divide, keep empty clusters unchanged */
     double rsum = 0.0;
     int64_t nonempty = 0;
     for (int64_t k = 0; k < K; ++k) {
-        double* row = centres + k * width;
         if (counts_out) counts_out[k] = cnt[k];
-        if (cnt[k] == 0) continue;
-        double n = (double)cnt[k];
-        double D2 = 0.0;
-        for (int j = 0; j < width; ++j) {
-            double s = (j < g->C && g->dt == ORACLE_F32) ? fsum[k * g->C + j]
-                                                          : (double)isum[k * width + j];
-            double mean = s / n;
-            double v = g->fp64 ? mean : (double)(float)mean;
-            double diff = v - row[j];
-            D2 += (j < g->C) ? diff * diff : g->w64[j - g->C] * (diff * diff);
-            row[j] = v;
-        }
-        rsum += sqrt(D2);
+        double t = update_divide(g, k, cnt, isum, fsum, centres);
+        if (t < 0.0) continue;
+        rsum += t;
         nonempty += 1;
     }
     if (residual) *residual = nonempty ? rsum / (double)nonempty : 0.0;
@@ -664,6 +703,144 @@ int oracle_connectivity(const oracle_params* p, const double* centres, int64_t K
     if (rc != ORACLE_OK) return rc;
     if (!centres || !labels_in || !labels_out || K < 0 || K > 0x7fffffffLL) return ORACLE_EINVAL;
     return connectivity(&g, centres, K, labels_in, labels_out, num_labels);
+}
+
+/* ---- region decomposition (Sec. 3.1, "Create non-overlapping regions") --
+ * The paper's multi-threaded form: the image is split into non-overlapping
+ * regions, here ranges of planes along the last axis; each thread assigns
+ * the voxels of its region, visiting every centre whose window meets the
+ * region in ascending k (so every voxel sees the centres in the same order
+ * as in assign() and keeps the same label), then maps its region's voxels
+ * into per-region sums that a reduce merges per label.  Integer sums are
+ * exact, so the merged sums -- and the centres -- equal the sequential
+ * ones; float images keep the sequential map (their double sums are then
+ * added in the same raster order).  Connectivity stays sequential: its
+ * raster pass is the paper's largest single-threaded part (Sec. 4).
+ * Compiled with -fopenmp the regions run on `threads` threads; without it
+ * the pragmas are ignored and the regions run one after another. */
+static void region_planes(const geom* g, int nreg, int r, int64_t* plo, int64_t* phi)
+{
+    const int64_t NL = g->N[g->n - 1];
+    *plo = NL * r / nreg;
+    *phi = NL * (r + 1) / nreg;
+}
+
+static int assign_regions(const geom* g, const void* image, const double* centres, int64_t K,
+                          int32_t* labels, int nreg, int threads)
+{
+    int rc_all = ORACLE_OK;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads)
+    for (int r = 0; r < nreg; ++r) {
+        int64_t plo, phi;
+        region_planes(g, nreg, r, &plo, &phi);
+        int rc = assign_planes(g, image, centres, K, labels, plo, phi);
+        if (rc != ORACLE_OK) {
+#pragma omp critical
+            rc_all = rc;
+        }
+    }
+    return rc_all;
+}
+
+static int update_regions(const geom* g, const void* image, const int32_t* labels, int64_t K,
+                          double* centres, double* residual, int nreg, int threads)
+{
+    if (g->dt == ORACLE_F32) return update(g, image, labels, K, centres, NULL, residual);
+    const int width = g->C + g->n;
+    const int last = g->n - 1;
+    int64_t* cnt = (int64_t*)calloc((size_t)(nreg * K), sizeof(int64_t));
+    int64_t* isum = (int64_t*)calloc((size_t)(nreg * K * width), sizeof(int64_t));
+    double* term = (double*)malloc((size_t)(K > 0 ? K : 1) * sizeof(double));
+    if (!cnt || !isum || !term) {
+        free(cnt); free(isum); free(term);
+        return ORACLE_ENOMEM;
+    }
+    int rc_all = ORACLE_OK;
+    /* map, per region */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads)
+    for (int r = 0; r < nreg; ++r) {
+        int64_t plo, phi;
+        region_planes(g, nreg, r, &plo, &phi);
+        int rc = update_map(g, image, labels, K, plo * g->stride[last], phi * g->stride[last], cnt + r * K,
+                            isum + r * K * width, NULL);
+        if (rc != ORACLE_OK) {
+#pragma omp critical
+            rc_all = rc;
+        }
+    }
+    if (rc_all == ORACLE_OK) {
+        /* reduce per label, then divide */
+#pragma omp parallel for schedule(static) num_threads(threads)
+        for (int64_t k = 0; k < K; ++k) {
+            for (int r = 1; r < nreg; ++r) {
+                cnt[k] += cnt[r * K + k];
+                for (int j = 0; j < width; ++j) isum[k * width + j] += isum[(r * K + k) * width + j];
+            }
+            term[k] = update_divide(g, k, cnt, isum, NULL, centres);
+        }
+        /* the residual's sum in ascending k, as in update() */
+        double rsum = 0.0;
+        int64_t nonempty = 0;
+        for (int64_t k = 0; k < K; ++k) {
+            if (term[k] < 0.0) continue;
+            rsum += term[k];
+            nonempty += 1;
+        }
+        if (residual) *residual = nonempty ? rsum / (double)nonempty : 0.0;
+    }
+    free(cnt); free(isum); free(term);
+    return rc_all;
+}
+
+int oracle_threads_available(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+int oracle_slic_regions(const oracle_params* p, const void* image, int32_t* labels, double* centres_out,
+                        int32_t* iters_done, double* residual, int64_t* num_labels, int threads)
+{
+    geom g;
+    int rc = make_geom(p, &g);
+    if (rc != ORACLE_OK) return rc;
+    if (!image || !labels || threads < 1) return ORACLE_EINVAL;
+    const int width = g.C + g.n;
+    /* several regions per thread, so that uneven regions balance */
+    int64_t nreg64 = 4 * (int64_t)threads;
+    if (nreg64 > g.N[g.n - 1]) nreg64 = g.N[g.n - 1];
+    const int nreg = (int)nreg64;
+    double* ctr = (double*)malloc((size_t)(g.K * width) * sizeof(double));
+    if (!ctr) return ORACLE_ENOMEM;
+    rc = seed(&g, p->perturb, image, ctr);
+    int32_t it = 0;
+    double res = 0.0;
+    for (it = 0; rc == ORACLE_OK && it < p->max_iter; ++it) {
+        rc = assign_regions(&g, image, ctr, g.K, labels, nreg, threads);
+        if (rc == ORACLE_OK) rc = update_regions(&g, image, labels, g.K, ctr, &res, nreg, threads);
+        if (rc == ORACLE_OK && p->conv_threshold > 0.0 && res < p->conv_threshold) { ++it; break; }
+    }
+    if (rc == ORACLE_OK) {
+        if (iters_done) *iters_done = it;
+        if (residual) *residual = res;
+        if (centres_out) memcpy(centres_out, ctr, (size_t)(g.K * width) * sizeof(double));
+        if (p->enforce_connectivity) {
+            int32_t* tmp = (int32_t*)malloc((size_t)g.V * sizeof(int32_t));
+            if (!tmp) rc = ORACLE_ENOMEM;
+            else {
+                memcpy(tmp, labels, (size_t)g.V * sizeof(int32_t));
+                rc = connectivity(&g, ctr, g.K, tmp, labels, num_labels);
+                free(tmp);
+            }
+        } else if (num_labels) {
+            *num_labels = g.K;
+        }
+    }
+    free(ctr);
+    return rc;
 }
 
 /* ---- CIE-Lab conversion (R16) -------------------------------------------- */

@@ -115,6 +115,21 @@ int oracle_slic_from(const oracle_params* p, const void* image,
                      double* centres_out, int32_t* iters_done,
                      double* residual, int64_t* num_labels);
 
+/* The whole method in the paper's multi-threaded form (Sec. 3.1): the
+ * image split into non-overlapping regions (ranges of planes along the last
+ * axis), each assigned and mapped by one thread, the per-region sums merged
+ * per label.  Same results as oracle_slic, bit for bit (float images keep
+ * the sequential map so that their double sums are added in raster order;
+ * connectivity is sequential).  threads >= 1; the library built with
+ * OpenMP runs the regions on that many threads, the plain build one after
+ * another. */
+int oracle_slic_regions(const oracle_params* p, const void* image, int32_t* labels,
+                        double* centres_out, int32_t* iters_done, double* residual,
+                        int64_t* num_labels, int threads);
+
+/* Threads OpenMP would use by default (1 in the build without OpenMP). */
+int oracle_threads_available(void);
+
 /* 8-bit sRGB -> CIE-Lab in double precision (reading R16 in the source):
  * rgb holds n interleaved (R, G, B) triples, lab receives n (L, a, b). */
 int oracle_srgb_to_lab(const uint8_t* rgb, int64_t n, double* lab);

@@ -132,19 +132,25 @@ SSLIC_API int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labe
  * (seeding reads two planes on either side); each slab adds its exact sums
  * to the centres' sums, so integer images give the labels and centres of
  * sslic_run bit for bit.  Device memory: the context's centres, sums and
- * bins plus two slabs (image planes + int32 labels).
+ * bins plus two slabs (image planes + int32 labels).  With connectivity
+ * enforcement (Sec. 3.1 stage 3) the labels then pass through the device
+ * slab by slab twice more (see sslic_conn_slabs_*): the component records
+ * and 16-bit component ids of the whole image stay on the device meanwhile
+ * (2 bytes per voxel plus about 45 bytes per component).
  *   image_host   the whole image (layout as sslic_run), host memory;
  *                page-locked memory overlaps best
  *   labels_host  receives the final labels (host, V int32)
  *   centres_host receives the final centres (host, K x (C+n) float, may be NULL)
- *   slab_planes  planes per slab: a positive multiple of 32
+ *   slab_planes  planes per slab: a positive multiple of 32; with
+ *                connectivity also of 64 in 2-D, and at least S along the
+ *                last axis
  *   stream       cudaStream_t for the kernels (a copy stream of the context
  *                carries the transfers), or NULL for the legacy default stream
- * 2-D and 3-D images without connectivity enforcement or the precision form
- * (else SSLIC_EUNSUPPORTED); float images with 16 or more channels take the
- * per-voxel kernel here.  Synchronous: returns when the labels are in
- * labels_host.  Errors: SSLIC_EINVAL (pointers, slab_planes), SSLIC_ENOMEM,
- * SSLIC_ECUDA, SSLIC_EBUSY. */
+ * 2-D and 3-D images without the precision form (else SSLIC_EUNSUPPORTED);
+ * float images with 16 or more channels take the per-voxel kernel here.
+ * Synchronous: returns when the labels are in labels_host.  Errors:
+ * SSLIC_EINVAL (pointers, slab_planes), SSLIC_ENOMEM, SSLIC_ECUDA,
+ * SSLIC_EBUSY. */
 SSLIC_API int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_host, float* centres_host,
                                  int64_t slab_planes, void* stream, sslic_result* out);
 
@@ -172,6 +178,65 @@ SSLIC_API int sslic_iterate(sslic_ctx* c, const void* image_dev, const float* ce
  * more than 63 bits (no image that fits in device memory does). */
 SSLIC_API int sslic_connectivity(sslic_ctx* c, const float* centres_dev, const int32_t* labels_in_dev,
                        int32_t* labels_out_dev, void* stream, int64_t* num_labels_host);
+
+/* ---- one image shared by several GPUs (slabs of planes) -------------------
+ * The paper's map-reduce update (Sec. 3.1: non-overlapping regions map their
+ * pixels into per-label sums, a reduce merges them) across GPUs: each rank
+ * holds a slab of planes [lo, hi) along the last axis (z in 3-D, y in 2-D)
+ * and a context created with the WHOLE image's parameters.  Assignment is
+ * voxel-centric and needs only the centres (replicated), so a slab needs no
+ * halo for it.  Per iteration a rank computes its slab's exact integer sums
+ * (sslic_shard_map), the caller sums them over the ranks (one all-reduce of
+ * K x (C + 4) int64, plus K x C double for float images), and every rank
+ * divides identically (sslic_shard_finalize): integer images then get the
+ * labels and centres of sslic_run bit for bit.  Slab bounds are multiples
+ * of 8 planes (3-D) or 64 rows (2-D), the last ending at N_{n-1}; 2-D and
+ * 3-D images, precision 0 (else SSLIC_EUNSUPPORTED).  The library does no
+ * communication: the caller's collective library does (NCCL, gloo...). */
+
+/* Seeds of the lattice planes in [lo, hi) (Sec. 3.1 step 1), perturbed by
+ * gradients read from planes lo-2 .. hi+1.  image_dev holds planes
+ * [a, b) of the image, a = max(0, lo - 2), b = min(N_{n-1}, hi + 2).  Writes
+ * the whole K x (C+n) centre table, rows of seeds outside the slab zero, so
+ * that a sum over the ranks gives every seed. */
+SSLIC_API int sslic_shard_seed(sslic_ctx* c, const void* image_dev, int64_t lo, int64_t hi, float* centres_dev,
+                               void* stream);
+
+/* Element counts of one rank's sums: n_u64 uint64 (K x (C + 4): features,
+ * three positions, count; sum them as int64) followed, for float images, by
+ * n_f64 doubles (K x C feature sums). */
+SSLIC_API int sslic_shard_sums_size(const sslic_ctx* c, int64_t* n_u64, int64_t* n_f64);
+
+/* Assignment of the slab's voxels (Sec. 2.2 / 3.1 step 2) from centres_dev
+ * (K x (C+n)) and the map of their [I(x), x] into sums_dev (the layout of
+ * sslic_shard_sums_size, device memory).  image_dev / labels_dev hold
+ * planes [lo, hi) only. */
+SSLIC_API int sslic_shard_map(sslic_ctx* c, const void* image_dev, int32_t* labels_dev, int64_t lo, int64_t hi,
+                              const float* centres_dev, void* sums_dev, void* stream);
+
+/* The reduce: centres = member means of the summed sums_dev (every rank's
+ * sums added), empty clusters keeping centres_prev_dev's rows; writes
+ * centres_out_dev (may alias centres_prev_dev) and, if residual_host is
+ * non-NULL, the centre residual (synchronises the stream). */
+SSLIC_API int sslic_shard_finalize(sslic_ctx* c, const void* sums_dev, const float* centres_prev_dev,
+                                   float* centres_out_dev, double* residual_host, void* stream);
+
+/* Connectivity enforcement (Sec. 3.1 stage 3) of an image handed over slab
+ * by slab, with the result of sslic_connectivity: begin (with the centres
+ * the labels were assigned from), add every slab's labels in order of their
+ * planes (slab bounds multiples of 8 planes in 3-D, 64 rows in 2-D; every
+ * slab but the last at least S planes deep), finish (the component count:
+ * one read-back), then relabel any slab.  The context keeps the component
+ * records and the 16-bit component ids of the whole image on the device
+ * (2 bytes per voxel plus about 45 bytes per component), and S planes of the
+ * previous slab's labels; a slab's buffer is free again when its call
+ * returns.  Used by sslic_run_streamed, and by a rank that collects the
+ * slabs of an image shared by several GPUs. */
+SSLIC_API int sslic_conn_slabs_begin(sslic_ctx* c, const float* centres_dev, void* stream);
+SSLIC_API int sslic_conn_slabs_add(sslic_ctx* c, const int32_t* labels_dev, int64_t lo, int64_t hi, void* stream);
+SSLIC_API int sslic_conn_slabs_finish(sslic_ctx* c, void* stream, int64_t* num_labels_host);
+SSLIC_API int sslic_conn_slabs_relabel(sslic_ctx* c, int32_t* labels_out_dev, int64_t lo, int64_t hi,
+                                       void* stream);
 
 /* One assign + update iteration (the same step as sslic_iterate) that
  * allocates nothing.  The paper has no counterpart to this call.  It serves

@@ -160,6 +160,61 @@ int ensure_ccl_capacity(sslic_ctx* c, int64_t m)
     return SSLIC_OK;
 }
 
+int grow_ccl_records(sslic_ctx* c, int64_t m, int64_t keep, cudaStream_t st)
+{
+    Workspace& w = c->ws;
+    if (m <= w.m_cap) return SSLIC_OK;
+    int rc;
+    // the arrays the tile pass fills: copied; the later passes' arrays: fresh
+    int* comp_label = nullptr;
+    int* gparent = nullptr;
+    unsigned long long* root_size = nullptr;
+    unsigned long long* root_first = nullptr;
+    uint8_t* fin = nullptr;
+    const size_t n = (size_t)m;
+    if ((rc = dalloc(c, &comp_label, n, "components")) || (rc = dalloc(c, &gparent, n, "components")) ||
+        (rc = dalloc(c, &root_size, n, "components")) || (rc = dalloc(c, &root_first, n, "components")) ||
+        (rc = dalloc(c, &fin, n, "components"))) {
+        dfree(comp_label); dfree(gparent); dfree(root_size); dfree(root_first); dfree(fin);
+        return rc;
+    }
+    const size_t k = (size_t)keep;
+    if (k > 0 &&
+        ((rc = cuda_check(c, cudaMemcpyAsync(comp_label, w.comp_label, k * sizeof(int), cudaMemcpyDeviceToDevice, st), "grow")) ||
+         (rc = cuda_check(c, cudaMemcpyAsync(gparent, w.gparent, k * sizeof(int), cudaMemcpyDeviceToDevice, st), "grow")) ||
+         (rc = cuda_check(c, cudaMemcpyAsync(root_size, w.root_size, k * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st), "grow")) ||
+         (rc = cuda_check(c, cudaMemcpyAsync(root_first, w.root_first, k * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st), "grow")) ||
+         (rc = cuda_check(c, cudaMemcpyAsync(fin, w.fin, k, cudaMemcpyDeviceToDevice, st), "grow")) ||
+         (rc = cuda_check(c, cudaStreamSynchronize(st), "sync")))) {
+        dfree(comp_label); dfree(gparent); dfree(root_size); dfree(root_first); dfree(fin);
+        return rc;
+    }
+    dfree(w.comp_label); dfree(w.gparent); dfree(w.root_size); dfree(w.root_first); dfree(w.fin);
+    w.comp_label = comp_label; w.gparent = gparent; w.root_size = root_size; w.root_first = root_first; w.fin = fin;
+    dfree(w.out_label); dfree(w.link); dfree(w.new_key); dfree(w.new_val);
+    w.m_cap = 0;
+    if ((rc = dalloc(c, &w.out_label, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.link, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.new_key, n, "components"))) return rc;
+    if ((rc = dalloc(c, &w.new_val, n, "components"))) return rc;
+    w.m_cap = m;
+    return SSLIC_OK;
+}
+
+int ensure_conn_slab_scratch(sslic_ctx* c)
+{
+    Workspace& w = c->ws;
+    const Geom& g = c->g;
+    int rc;
+    if (!w.conn_seed && (rc = dalloc(c, &w.conn_seed, (size_t)g.K, "connectivity seeds"))) return rc;
+    if (!w.conn_carry) {
+        int64_t plane = 1;
+        for (int d = 0; d < g.n - 1; ++d) plane *= g.N[d];
+        if ((rc = dalloc(c, &w.conn_carry, (size_t)(g.S[g.n - 1] * plane), "connectivity carry"))) return rc;
+    }
+    return SSLIC_OK;
+}
+
 static void free_all(sslic_ctx* c)
 {
     Workspace& w = c->ws;
@@ -172,6 +227,7 @@ static void free_all(sslic_ctx* c)
     dfree(w.root_size); dfree(w.root_first); dfree(w.fin); dfree(w.out_label); dfree(w.link);
     dfree(w.new_key); dfree(w.new_val); dfree(w.sort_key); dfree(w.sort_val);
     dfree(w.img_dev); dfree(w.lab_dev); dfree(w.cen_dev);
+    dfree(w.conn_seed); dfree(w.conn_carry);
     for (int i = 0; i < 2; ++i) { dfree(w.slab_img[i]); dfree(w.slab_lab[i]); }
     for (int i = 0; i < 8; ++i)
         if (w.slab_ev[i]) { cudaEventDestroy(w.slab_ev[i]); w.slab_ev[i] = nullptr; }
@@ -406,10 +462,12 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
     if (!c || !image_host || !labels_host) return SSLIC_EINVAL;
     const Geom& g = c->g;
     if (g.n != 2 && g.n != 3) return set_error(c, SSLIC_EUNSUPPORTED, "streamed form: 2-D and 3-D images");
-    if (c->p.enforce_connectivity || c->p.precision)
-        return set_error(c, SSLIC_EUNSUPPORTED, "streamed form: no connectivity enforcement or precision form");
+    if (c->p.precision) return set_error(c, SSLIC_EUNSUPPORTED, "streamed form: no precision form");
     if (slab_planes < 32 || slab_planes % 32 != 0)
         return set_error(c, SSLIC_EINVAL, "slab depth must be a positive multiple of 32 planes");
+    if (c->p.enforce_connectivity && ((g.n == 2 && slab_planes % 64 != 0) || slab_planes < g.S[g.n - 1]))
+        return set_error(c, SSLIC_EINVAL,
+                         "streamed connectivity: slabs of a multiple of 64 rows (2-D) and at least S planes");
     Busy b(c);
     if (!b.ok) return SSLIC_EBUSY;
     Workspace& w = c->ws;
@@ -527,9 +585,45 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
     if ((rc = cuda_check(c, cudaStreamSynchronize(ds), "sync"))) return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(cs), "sync"))) return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    int64_t num_labels = g.K;
+    if (c->p.enforce_connectivity) {
+        // connectivity slab by slab (Sec. 3.1 stage 3): the labels of each
+        // slab go up once for the components and once more, relabelled, come
+        // back; the component records and ids of the whole image stay on the
+        // device
+        const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
+        if ((rc = conn_slabs_begin(c, st))) return rc;
+        for (int64_t s = 0; s < nslab; ++s) {
+            const int64_t lo = s * depth, hi = imin64(NL, lo + depth);
+            if ((rc = cuda_check(c, cudaMemcpyAsync(w.slab_lab[0], labels_host + lo * plane,
+                                                    (size_t)(hi - lo) * plane * sizeof(int32_t),
+                                                    cudaMemcpyHostToDevice, st),
+                                 "slab labels up")))
+                return rc;
+            if ((rc = conn_slabs_add(c, w.slab_lab[0], lo, hi, st))) return rc;
+        }
+        if ((rc = conn_slabs_finish(c, st, &num_labels))) return rc;
+        for (int64_t s = 0; s < nslab; ++s) {
+            const int i = (int)(s & 1);
+            const int64_t lo = s * depth, hi = imin64(NL, lo + depth);
+            if ((rc = cuda_check(c, cudaStreamWaitEvent(st, lab_free[i], 0), "wait"))) return rc;
+            if ((rc = conn_slabs_relabel(c, w.slab_lab[i], lo, hi, st))) return rc;
+            if ((rc = cuda_check(c, cudaEventRecord(lab_done[i], st), "event"))) return rc;
+            if ((rc = cuda_check(c, cudaStreamWaitEvent(ds, lab_done[i], 0), "wait"))) return rc;
+            if ((rc = cuda_check(c, cudaMemcpyAsync(labels_host + lo * plane, w.slab_lab[i],
+                                                    (size_t)(hi - lo) * plane * sizeof(int32_t),
+                                                    cudaMemcpyDeviceToHost, ds),
+                                 "slab labels down")))
+                return rc;
+            if ((rc = cuda_check(c, cudaEventRecord(lab_free[i], ds), "event"))) return rc;
+        }
+        if ((rc = cuda_check(c, cudaStreamSynchronize(ds), "sync"))) return rc;
+        if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+        prof_end(c, pr, st);
+    }
     if (out) {
         out->num_clusters = g.K;
-        out->num_labels = g.K;
+        out->num_labels = num_labels;
         out->iterations = it;
         out->residual = res;
     }

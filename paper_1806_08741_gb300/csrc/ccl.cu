@@ -235,7 +235,8 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
                  int* __restrict__ tile_base, int* __restrict__ tile_cnt, int* __restrict__ comp_label,
                  unsigned long long* __restrict__ root_size, unsigned long long* __restrict__ root_first,
                  uint8_t* __restrict__ fin, int* __restrict__ gparent,
-                 unsigned* __restrict__ counters, int64_t m_cap, RasterKey rk, int64_t ntx, int64_t nty, int64_t ntz)
+                 unsigned* __restrict__ counters, int64_t m_cap, RasterKey rk, int64_t ntx, int64_t nty, int64_t ntz,
+                 int64_t tile0)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
@@ -254,7 +255,7 @@ ccl_local_kernel(Geom g, const int32_t* __restrict__ labels, uint16_t* __restric
     __shared__ int s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = tile0 + blockIdx.x;
     int64_t X0, Y0, Z0, W0;
     ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     const int ex = (int)imin64(TX, g.N[0] - X0);
@@ -497,15 +498,19 @@ template <int NDIM>
 __global__ void __launch_bounds__(kCclThreads)
 ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __restrict__ lid_img,
                  const int* __restrict__ tile_base, int* gparent, unsigned* counters, int64_t ntx,
-                 int64_t nty, int64_t ntz)
+                 int64_t nty, int64_t ntz, int64_t tile0, const int32_t* __restrict__ carry, int64_t qlo,
+                 int64_t cbase)
 {
+    // labels of voxels before qlo (the planes below a slab, see the slab form)
+    // come from the carried planes, indexed from voxel cbase
+    auto lab_at = [&](int64_t q) -> int { return q < qlo ? carry[q - cbase] : labels[q]; };
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
     constexpr int HS = FaceHash<NDIM>::kSize;
     __shared__ unsigned hset[HS];
     __shared__ int2 plist[FaceHash<NDIM>::kPairs];  // the distinct pairs, united after the scan
     __shared__ unsigned npairs;
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = tile0 + blockIdx.x;
     int64_t X0, Y0, Z0, W0;
     ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     const int EX = (int)imin64(TX, g.N[0] - X0), EY = (int)imin64(TY, g.N[1] - Y0), EZ = (int)imin64(TZ, g.N[2] - Z0);
@@ -533,7 +538,7 @@ ccl_faces_kernel(Geom g, const int32_t* __restrict__ labels, const uint16_t* __r
         else rest = iw * (d == 2 ? sy : sz);
         const int64_t ia = p0 + iu * su + rest, ib = ia - st;
         const int64_t ja = iu > 0 ? ia - su : ia, jb = iu > 0 ? ib - su : ib;
-        const int L = labels[ia], Lb = labels[ib], La1 = labels[ja], Lb1 = labels[jb];
+        const int L = labels[ia], Lb = lab_at(ib), La1 = labels[ja], Lb1 = lab_at(jb);
         const unsigned la = lid_img[ia], lb = lid_img[ib];
         if (L != Lb) continue;
         if (iu > 0 && La1 == L && Lb1 == L) continue;  // same pair as the predecessor along u
@@ -633,6 +638,69 @@ __global__ void conn_phase1_kernel(Geom g, const float* __restrict__ ctr, const 
     }
     if (s[0] < 0) return;
     const int G = gparent[gid_of<NDIM>(g, lid_img, tile_base, s[0], s[1], s[2], s[3], ntx, nty, ntz)];
+    if (4ull * root_size[G] > (unsigned long long)g.sprod) fin[G] = 1;
+}
+
+// Slab form, phase 1's seed voxel: every centre whose S-box ends in the
+// planes [lo, hi) of the last axis finds it here -- the voxel at its rounded
+// centre when that carries its label, else the raster-first voxel of its
+// label in the box (the same rule as conn_phase1_kernel).  The box spans at
+// most S planes along the last axis, so the planes below lo that it reaches
+// are among the carried ones (labels of voxels before qlo come from carry,
+// indexed from voxel cbase).  -1: no such voxel.
+template <int NDIM>
+__global__ void conn_seek_kernel(Geom g, const float* __restrict__ ctr, const int32_t* __restrict__ labels,
+                                 const int32_t* __restrict__ carry, int64_t qlo, int64_t cbase, int64_t lo,
+                                 int64_t hi, long long* __restrict__ seed_vox)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= g.K) return;
+    const int L = g.n - 1;
+    const float* pc = ctr + k * g.CW + g.C;
+    int64_t p[kMaxDims] = {0, 0, 0, 0};
+    for (int d = 0; d < g.n; ++d) {
+        int64_t v = (int64_t)floor((double)pc[d] + 0.5);
+        p[d] = v < 0 ? 0 : (v > g.N[d] - 1 ? g.N[d] - 1 : v);
+    }
+    int64_t blo[kMaxDims], bhi[kMaxDims];
+    for (int d = 0; d < kMaxDims; ++d) {
+        blo[d] = imax64(0, p[d] - g.S[d] / 2);
+        bhi[d] = imin64(g.N[d] - 1, p[d] + (g.S[d] + 1) / 2 - 1);
+    }
+    if (bhi[L] < lo || bhi[L] >= hi) return;  // another slab holds the box's last plane
+    auto lab = [&](int64_t q) -> int32_t { return q < qlo ? carry[q - cbase] : labels[q]; };
+    long long s = -1;
+    const int64_t q0 = vidx(g, p[0], p[1], p[2], p[3]);
+    if (lab(q0) == (int32_t)k) {
+        s = q0;
+    } else {
+        for (int64_t w = blo[3]; w <= bhi[3] && s < 0; ++w)
+            for (int64_t z = blo[2]; z <= bhi[2] && s < 0; ++z)
+                for (int64_t y = blo[1]; y <= bhi[1] && s < 0; ++y)
+                    for (int64_t x = blo[0]; x <= bhi[0]; ++x) {
+                        const int64_t q = vidx(g, x, y, z, w);
+                        if (lab(q) == (int32_t)k) { s = q; break; }
+                    }
+    }
+    seed_vox[k] = s;
+}
+
+// Slab form, phase 1 proper: the component through each centre's seed voxel
+// is final if 4 * size > prod S (after every slab's records are united)
+template <int NDIM>
+__global__ void conn_phase1_seeded_kernel(Geom g, const long long* __restrict__ seed_vox,
+                                          const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
+                                          const int* __restrict__ gparent,
+                                          const unsigned long long* __restrict__ root_size, uint8_t* __restrict__ fin,
+                                          int64_t ntx, int64_t nty, int64_t ntz)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= g.K) return;
+    const long long s = seed_vox[k];
+    if (s < 0) return;
+    const int64_t x = s % g.N[0], y = (s / g.N[0]) % g.N[1], z = (s / (g.N[0] * g.N[1])) % g.N[2],
+                  w = s / (g.N[0] * g.N[1] * g.N[2]);
+    const int G = gparent[gid_of<NDIM>(g, lid_img, tile_base, x, y, z, w, ntx, nty, ntz)];
     if (4ull * root_size[G] > (unsigned long long)g.sprod) fin[G] = 1;
 }
 
@@ -813,12 +881,13 @@ __global__ void __launch_bounds__(kCclThreads, 8)
 conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __restrict__ tile_base,
                     const int* __restrict__ tile_cnt, const int* __restrict__ gparent,
                     const int* __restrict__ out_label, const int* __restrict__ comp_label,
-                    int32_t* __restrict__ labels_out, int inplace, int64_t ntx, int64_t nty, int64_t ntz)
+                    int32_t* __restrict__ labels_out, int inplace, int64_t ntx, int64_t nty, int64_t ntz,
+                    int64_t tile0)
 {
     using Cfg = CclCfg<NDIM>;
     constexpr int TX = Cfg::TX, TY = Cfg::TY, TZ = Cfg::TZ;
     __shared__ int tab[kCclTV];  // local component -> output label
-    const int64_t tile = blockIdx.x;
+    const int64_t tile = tile0 + blockIdx.x;
     int64_t X0, Y0, Z0, W0;
     ccl_tile_origin<NDIM>(tile, ntx, nty, ntz, X0, Y0, Z0, W0);
     // the thread's voxels: their local ids are loaded first, in flight while
@@ -868,42 +937,31 @@ conn_relabel_kernel(Geom g, const uint16_t* __restrict__ lid_img, const int* __r
 
 // ---------------------------------------------------------------------------
 template <int NDIM>
-static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,
-                             int64_t* num_labels)
+struct CclGrid {
+    int64_t ntx, nty, ntz, ntiles;
+    explicit CclGrid(const Geom& g)
+    {
+        using Cfg = CclCfg<NDIM>;
+        ntx = (g.N[0] + Cfg::TX - 1) / Cfg::TX;
+        nty = (g.N[1] + Cfg::TY - 1) / Cfg::TY;
+        ntz = (g.N[2] + Cfg::TZ - 1) / Cfg::TZ;
+        ntiles = ntx * nty * ntz * g.N[3];  // one slice of tiles per index along a fourth axis
+    }
+};
+
+// Steps 3-5 on the complete record forest (M records): flatten, phase 1
+// (from the label image, or -- labels_in null -- from the seed voxels the
+// slab form found), phase 2, the ranking of new labels, the link walks.
+// *Mn receives the number of new labels.
+template <int NDIM>
+static int conn_resolve_records(sslic_ctx* c, const int32_t* labels_in, const RasterKey& rk, int64_t M,
+                                cudaStream_t st, int64_t* Mn_out)
 {
-    using Cfg = CclCfg<NDIM>;
     const Geom& g = c->g;
     Workspace& w = c->ws;
-    const int64_t ntx = (g.N[0] + Cfg::TX - 1) / Cfg::TX;
-    const int64_t nty = (g.N[1] + Cfg::TY - 1) / Cfg::TY;
-    const int64_t ntz = (g.N[2] + Cfg::TZ - 1) / Cfg::TZ;
-    const int64_t ntiles = ntx * nty * ntz * g.N[3];  // one slice of tiles per index along a fourth axis
+    const CclGrid<NDIM> t(g);
     int rc;
     unsigned hc[4];
-    RasterKey rk;
-    if (!make_raster_key(g, rk)) return set_error(c, SSLIC_EUNSUPPORTED, "packed voxel coordinates exceed 63 bits");
-    const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
-        ccl_local_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
-                                                              w.comp_label, w.root_size, w.root_first, w.fin, w.gparent,
-                                                              w.counters, w.m_cap, rk, ntx, nty, ntz);
-        count_launch(c);
-        if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
-        if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
-                             "read component count")))
-            return rc;
-        if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
-        if (!hc[1]) break;
-        if (attempt == 1) return set_error(c, SSLIC_ENOMEM, "component records still overflow");
-        if ((rc = ensure_ccl_capacity(c, (int64_t)hc[0] + hc[0] / 4 + 4096))) return rc;
-    }
-    const int64_t M = hc[0];
-    if (M > INT_MAX) return set_error(c, SSLIC_EUNSUPPORTED, "more than 2^31 components");
-    ccl_faces_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.gparent,
-                                                           w.counters, ntx, nty, ntz);
-    count_launch(c);
-    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     const int gb = c->sms * 8;
     // per-record passes: a few records per thread, all of them in flight at
     // once, so that the walks' latencies overlap
@@ -913,13 +971,18 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     ccl_flatten_kernel<<<rec_grid(kFlattenBatch), 256, 0, st>>>(w.gparent, w.root_size, w.root_first, w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_flatten_kernel"))) return rc;
-    conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,
-                                                                 w.gparent, w.root_size, w.fin, ntx, nty, ntz);
+    if (labels_in)
+        conn_phase1_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, labels_in, w.lid, w.tile_base,
+                                                                     w.gparent, w.root_size, w.fin, t.ntx, t.nty, t.ntz);
+    else
+        conn_phase1_seeded_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.conn_seed, w.lid, w.tile_base,
+                                                                            w.gparent, w.root_size, w.fin, t.ntx,
+                                                                            t.nty, t.ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase1_kernel"))) return rc;
     conn_phase2_kernel<NDIM><<<rec_grid(kPhase2Batch), 256, 0, st>>>(g, w.gparent, w.comp_label, w.root_size, w.root_first, w.fin,
                                                   w.lid, w.tile_base, w.out_label, w.link, w.new_key, w.new_val,
-                                                  w.counters, rk, ntx, nty, ntz);
+                                                  w.counters, rk, t.ntx, t.nty, t.ntz);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_phase2_kernel"))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
@@ -965,19 +1028,253 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     conn_resolve_kernel<<<rec_grid(kResolveBatch), 256, 0, st>>>(w.gparent, w.link, w.out_label, w.counters);
     count_launch(c);
     if ((rc = cuda_check(c, cudaGetLastError(), "conn_resolve_kernel"))) return rc;
-    conn_relabel_kernel<NDIM><<<ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,
-                                                              w.out_label, w.comp_label, labels_out,
-                                                              labels_in == labels_out ? 1 : 0, ntx, nty, ntz);
-    count_launch(c);
-    if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
-    if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+    *Mn_out = Mn;
+    return SSLIC_OK;
+}
+
+// the error flag of the bounded walks, read after a stream sync
+static int conn_status(sslic_ctx* c, cudaStream_t st)
+{
+    unsigned hc[4];
+    int rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(hc, c->ws.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
                          "read status")))
         return rc;
     if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
-    prof_end(c, pr, st);
     if (hc[3]) return set_error(c, SSLIC_ECUDA, "connectivity: a bounded walk ran out or an internal check failed (code %u)", hc[3]);
+    return SSLIC_OK;
+}
+
+template <int NDIM>
+static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,
+                             int64_t* num_labels)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    const CclGrid<NDIM> t(g);
+    int rc;
+    unsigned hc[4];
+    RasterKey rk;
+    if (!make_raster_key(g, rk)) return set_error(c, SSLIC_EUNSUPPORTED, "packed voxel coordinates exceed 63 bits");
+    const int pr = prof_begin(c, SSLIC_PHASE_CONNECTIVITY, st);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
+        ccl_local_kernel<NDIM><<<t.ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.tile_cnt,
+                                                                w.comp_label, w.root_size, w.root_first, w.fin,
+                                                                w.gparent, w.counters, w.m_cap, rk, t.ntx, t.nty,
+                                                                t.ntz, 0);
+        count_launch(c);
+        if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
+        if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                             "read component count")))
+            return rc;
+        if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+        if (!hc[1]) break;
+        if (attempt == 1) return set_error(c, SSLIC_ENOMEM, "component records still overflow");
+        if ((rc = ensure_ccl_capacity(c, (int64_t)hc[0] + hc[0] / 4 + 4096))) return rc;
+    }
+    const int64_t M = hc[0];
+    if (M > INT_MAX) return set_error(c, SSLIC_EUNSUPPORTED, "more than 2^31 components");
+    ccl_faces_kernel<NDIM><<<t.ntiles, kCclThreads, 0, st>>>(g, labels_in, w.lid, w.tile_base, w.gparent,
+                                                             w.counters, t.ntx, t.nty, t.ntz, 0, nullptr, 0, 0);
+    count_launch(c);
+    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
+    int64_t Mn = 0;
+    if ((rc = conn_resolve_records<NDIM>(c, labels_in, rk, M, st, &Mn))) return rc;
+    conn_relabel_kernel<NDIM><<<t.ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,
+                                                                w.out_label, w.comp_label, labels_out,
+                                                                labels_in == labels_out ? 1 : 0, t.ntx, t.nty, t.ntz,
+                                                                0);
+    count_launch(c);
+    if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
+    if ((rc = conn_status(c, st))) return rc;
+    prof_end(c, pr, st);
     if (num_labels) *num_labels = g.K + Mn;
     return SSLIC_OK;
+}
+
+// ---- slab form -----------------------------------------------------------
+// Connectivity of an image handed over as consecutive ranges of planes along
+// its last axis (the streamed form's slabs, or the slabs of the ranks that
+// share an image), with the same result as connectivity_impl:
+//  - each slab's tiles get their local components and records (the records
+//    and the per-voxel local ids of the whole image stay on the device), and
+//    their faces are united, the face towards the previous slab against the
+//    planes carried over from it;
+//  - every centre whose S-box ends in the slab finds its phase-1 seed voxel
+//    there (the box reaches at most S planes back: those are carried);
+//  - once every slab is in, steps 3-5 run on the complete forest;
+//  - then each slab is relabelled through its records.
+// Slab bounds are multiples of the tile's extent along the last axis, and
+// every slab but the last holds at least S_last planes.
+template <int NDIM>
+static int64_t ccl_tile_depth()
+{
+    return NDIM == 3 ? CclCfg<3>::TZ : CclCfg<2>::TY;
+}
+
+template <int NDIM>
+static int conn_slab_tiles(const Geom& g, int64_t lo, int64_t hi, int64_t* tile0, int64_t* ntiles)
+{
+    const CclGrid<NDIM> t(g);
+    const int64_t td = ccl_tile_depth<NDIM>();
+    const int64_t layer = NDIM == 3 ? t.ntx * t.nty : t.ntx;
+    *tile0 = lo / td * layer;
+    *ntiles = (hi + td - 1) / td * layer - *tile0;
+    return SSLIC_OK;
+}
+
+static int64_t plane_voxels(const Geom& g)
+{
+    int64_t plane = 1;
+    for (int d = 0; d < g.n - 1; ++d) plane *= g.N[d];
+    return plane;
+}
+
+int conn_slabs_begin(sslic_ctx* c, cudaStream_t st)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    if (g.n != 2 && g.n != 3) return set_error(c, SSLIC_EUNSUPPORTED, "slab connectivity: 2-D and 3-D images");
+    RasterKey rk;
+    if (!make_raster_key(g, rk)) return set_error(c, SSLIC_EUNSUPPORTED, "packed voxel coordinates exceed 63 bits");
+    int rc;
+    if ((rc = ensure_ccl_capacity(c, 32 * g.K + g.V / 1024 + 4096))) return rc;
+    if ((rc = ensure_conn_slab_scratch(c))) return rc;
+    if ((rc = cuda_check(c, cudaMemsetAsync(w.counters, 0, 4 * sizeof(unsigned), st), "memset counters"))) return rc;
+    if ((rc = cuda_check(c, cudaMemsetAsync(w.conn_seed, 0xff, g.K * sizeof(long long), st), "memset seeds")))
+        return rc;
+    w.conn_next = 0;
+    w.conn_carried = 0;
+    return SSLIC_OK;
+}
+
+template <int NDIM>
+static int conn_slabs_add_impl(sslic_ctx* c, const int32_t* labels_slab, int64_t lo, int64_t hi, cudaStream_t st)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    const CclGrid<NDIM> t(g);
+    const int L = g.n - 1;
+    const int64_t NL = g.N[L], td = ccl_tile_depth<NDIM>(), SL = g.S[L];
+    if (lo != w.conn_next || hi <= lo || hi > NL)
+        return set_error(c, SSLIC_EINVAL, "slab connectivity: slabs must follow each other from plane 0");
+    if (lo % td != 0 || (hi % td != 0 && hi != NL))
+        return set_error(c, SSLIC_EINVAL, "slab connectivity: slab bounds must be multiples of %lld planes",
+                         (long long)td);
+    if (hi < NL && hi - lo < SL)
+        return set_error(c, SSLIC_EINVAL, "slab connectivity: a slab before the last needs at least S = %lld planes",
+                         (long long)SL);
+    RasterKey rk;
+    make_raster_key(g, rk);
+    const int64_t plane = plane_voxels(g), qlo = lo * plane;
+    const int32_t* lab = labels_slab - qlo;            // indexed by global voxel
+    const int64_t cbase = (lo - w.conn_carried) * plane;  // first voxel the carry holds
+    int64_t tile0, nt;
+    conn_slab_tiles<NDIM>(g, lo, hi, &tile0, &nt);
+    int rc;
+    unsigned hc[4];
+    if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                         "read component count")))
+        return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    const unsigned m_before = hc[0];
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        ccl_local_kernel<NDIM><<<nt, kCclThreads, 0, st>>>(g, lab, w.lid, w.tile_base, w.tile_cnt, w.comp_label,
+                                                           w.root_size, w.root_first, w.fin, w.gparent, w.counters,
+                                                           w.m_cap, rk, t.ntx, t.nty, t.ntz, tile0);
+        count_launch(c);
+        if ((rc = cuda_check(c, cudaGetLastError(), "ccl_local_kernel"))) return rc;
+        if ((rc = cuda_check(c, cudaMemcpyAsync(hc, w.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                             "read component count")))
+            return rc;
+        if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+        if (!hc[1]) break;
+        if (attempt == 1) return set_error(c, SSLIC_ENOMEM, "component records still overflow");
+        // grow (keeping the earlier slabs' records) and redo this slab
+        if ((rc = grow_ccl_records(c, (int64_t)hc[0] + hc[0] / 4 + 4096, m_before, st))) return rc;
+        const unsigned reset[2] = {m_before, 0u};
+        if ((rc = cuda_check(c, cudaMemcpyAsync(w.counters, reset, 2 * sizeof(unsigned), cudaMemcpyHostToDevice, st),
+                             "reset counters")))
+            return rc;
+        if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    }
+    if (hc[0] > (unsigned)INT_MAX) return set_error(c, SSLIC_EUNSUPPORTED, "more than 2^31 components");
+    ccl_faces_kernel<NDIM><<<nt, kCclThreads, 0, st>>>(g, lab, w.lid, w.tile_base, w.gparent, w.counters, t.ntx,
+                                                       t.nty, t.ntz, tile0, w.conn_carry, qlo, cbase);
+    count_launch(c);
+    if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
+    conn_seek_kernel<NDIM><<<(g.K + 255) / 256, 256, 0, st>>>(g, w.ctr, lab, w.conn_carry, qlo, cbase, lo, hi,
+                                                             w.conn_seed);
+    count_launch(c);
+    if ((rc = cuda_check(c, cudaGetLastError(), "conn_seek_kernel"))) return rc;
+    // carry the last S planes (those the next slab's boxes and faces reach)
+    if (hi < NL) {
+        const int64_t keep = imin64(SL, hi);
+        if ((rc = cuda_check(c, cudaMemcpyAsync(w.conn_carry, labels_slab + (hi - keep - lo) * plane,
+                                                (size_t)(keep * plane) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st),
+                             "carry planes")))
+            return rc;
+        w.conn_carried = keep;
+    }
+    w.conn_next = hi;
+    return SSLIC_OK;
+}
+
+int conn_slabs_add(sslic_ctx* c, const int32_t* labels_slab, int64_t lo, int64_t hi, cudaStream_t st)
+{
+    if (c->g.n == 3) return conn_slabs_add_impl<3>(c, labels_slab, lo, hi, st);
+    if (c->g.n == 2) return conn_slabs_add_impl<2>(c, labels_slab, lo, hi, st);
+    return set_error(c, SSLIC_EUNSUPPORTED, "slab connectivity: 2-D and 3-D images");
+}
+
+int conn_slabs_finish(sslic_ctx* c, cudaStream_t st, int64_t* num_labels)
+{
+    const Geom& g = c->g;
+    if (g.n != 2 && g.n != 3) return set_error(c, SSLIC_EUNSUPPORTED, "slab connectivity: 2-D and 3-D images");
+    if (c->ws.conn_next != g.N[g.n - 1])
+        return set_error(c, SSLIC_EINVAL, "slab connectivity: not every plane has been added");
+    RasterKey rk;
+    make_raster_key(g, rk);
+    unsigned hc[4];
+    int rc;
+    if ((rc = cuda_check(c, cudaMemcpyAsync(hc, c->ws.counters, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, st),
+                         "read component count")))
+        return rc;
+    if ((rc = cuda_check(c, cudaStreamSynchronize(st), "sync"))) return rc;
+    int64_t Mn = 0;
+    rc = g.n == 3 ? conn_resolve_records<3>(c, nullptr, rk, hc[0], st, &Mn)
+                  : conn_resolve_records<2>(c, nullptr, rk, hc[0], st, &Mn);
+    if (rc) return rc;
+    if ((rc = conn_status(c, st))) return rc;
+    if (num_labels) *num_labels = g.K + Mn;
+    return SSLIC_OK;
+}
+
+template <int NDIM>
+static int conn_slabs_relabel_impl(sslic_ctx* c, int32_t* labels_out_slab, int64_t lo, int64_t hi, cudaStream_t st)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    const CclGrid<NDIM> t(g);
+    const int64_t NL = g.N[g.n - 1], td = ccl_tile_depth<NDIM>();
+    if (lo < 0 || hi <= lo || hi > NL || lo % td != 0 || (hi % td != 0 && hi != NL))
+        return set_error(c, SSLIC_EINVAL, "slab connectivity: slab bounds must be multiples of %lld planes",
+                         (long long)td);
+    int64_t tile0, nt;
+    conn_slab_tiles<NDIM>(g, lo, hi, &tile0, &nt);
+    conn_relabel_kernel<NDIM><<<nt, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent, w.out_label,
+                                                          w.comp_label, labels_out_slab - lo * plane_voxels(g), 0,
+                                                          t.ntx, t.nty, t.ntz, tile0);
+    count_launch(c);
+    return cuda_check(c, cudaGetLastError(), "conn_relabel_kernel");
+}
+
+int conn_slabs_relabel(sslic_ctx* c, int32_t* labels_out_slab, int64_t lo, int64_t hi, cudaStream_t st)
+{
+    if (c->g.n == 3) return conn_slabs_relabel_impl<3>(c, labels_out_slab, lo, hi, st);
+    if (c->g.n == 2) return conn_slabs_relabel_impl<2>(c, labels_out_slab, lo, hi, st);
+    return set_error(c, SSLIC_EUNSUPPORTED, "slab connectivity: 2-D and 3-D images");
 }
 
 int64_t ccl_num_tiles(const Geom& g)

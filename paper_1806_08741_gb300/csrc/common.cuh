@@ -179,6 +179,13 @@ struct Workspace {
     cudaStream_t copy_stream = nullptr;  // uploads
     cudaStream_t down_stream = nullptr;  // label downloads (the other direction, concurrently)
     cudaEvent_t slab_ev[8] = {};        // img ready / img free / labels done / labels free, per buffer
+    // connectivity in slabs (conn_slabs_*): the phase-1 seed voxel of every
+    // centre, the labels of the last planes of the previous slab, and how far
+    // the slabs have come
+    long long* conn_seed = nullptr;     // K
+    int32_t* conn_carry = nullptr;      // S_last planes
+    int64_t conn_next = 0;              // first plane the next slab must start at
+    int64_t conn_carried = 0;           // planes the carry holds (those just below conn_next)
 };
 
 }  // namespace sslic
@@ -252,6 +259,17 @@ template <typename T>
 int launch_voxel_tiles(sslic_ctx* c, const T* img, int32_t* labels, int tx, int ty, int tz, int ntx, int nty,
                        cudaStream_t st);
 int ensure_ccl_capacity(sslic_ctx* c, int64_t m);
+// grows the component records to m, keeping the first `keep` records the
+// tile pass has written (the slab form grows between slabs)
+int grow_ccl_records(sslic_ctx* c, int64_t m, int64_t keep, cudaStream_t st);
+int ensure_conn_slab_scratch(sslic_ctx* c);
+// connectivity of an image handed over slab by slab (ranges of planes along
+// the last axis, in order): begin, add every slab, finish, then relabel
+// each slab (ccl.cu)
+int conn_slabs_begin(sslic_ctx* c, cudaStream_t st);
+int conn_slabs_add(sslic_ctx* c, const int32_t* labels_slab, int64_t lo, int64_t hi, cudaStream_t st);
+int conn_slabs_finish(sslic_ctx* c, cudaStream_t st, int64_t* num_labels);
+int conn_slabs_relabel(sslic_ctx* c, int32_t* labels_out_slab, int64_t lo, int64_t hi, cudaStream_t st);
 int set_error(sslic_ctx* c, int code, const char* fmt, ...);
 int make_geom(const sslic_params* p, Geom* g);
 // phase brackets: prof_begin returns a record index (or -1 when timing is off)

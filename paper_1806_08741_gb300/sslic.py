@@ -29,7 +29,9 @@ EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_
            "sslic_set_tile_shape", "sslic_get_tile_shape", "sslic_autotune", "sslic_tune_forget",
            "sslic_tune_record", "sslic_tune_lookup", "sslic_precision_probe", "sslic_srgb_to_lab",
            "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
-           "sslic_strerror", "sslic_last_error")
+           "sslic_strerror", "sslic_last_error", "sslic_shard_seed", "sslic_shard_sums_size",
+           "sslic_shard_map", "sslic_shard_finalize", "sslic_conn_slabs_begin", "sslic_conn_slabs_add",
+           "sslic_conn_slabs_finish", "sslic_conn_slabs_relabel")
 PHASES = ("seed", "bins", "assign", "assign_voxel", "finalize", "connectivity")
 
 
@@ -114,6 +116,19 @@ def load(path: str = LIB_PATH):
     L.sslic_run_from.argtypes = [C, vp, vp, vp, vp, vp, R]
     L.sslic_run_host.argtypes = [C, vp, vp, vp, vp, R]
     L.sslic_run_streamed.argtypes = [C, vp, vp, vp, ctypes.c_int64, vp, R]
+    i64, pi64 = ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)
+    L.sslic_shard_seed.argtypes = [C, vp, i64, i64, vp, vp]
+    L.sslic_shard_sums_size.argtypes = [C, pi64, pi64]
+    L.sslic_shard_map.argtypes = [C, vp, vp, i64, i64, vp, vp, vp]
+    L.sslic_shard_finalize.argtypes = [C, vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp]
+    L.sslic_conn_slabs_begin.argtypes = [C, vp, vp]
+    L.sslic_conn_slabs_add.argtypes = [C, vp, i64, i64, vp]
+    L.sslic_conn_slabs_finish.argtypes = [C, vp, pi64]
+    L.sslic_conn_slabs_relabel.argtypes = [C, vp, i64, i64, vp]
+    for f in ("sslic_shard_seed", "sslic_shard_sums_size", "sslic_shard_map", "sslic_shard_finalize",
+              "sslic_conn_slabs_begin", "sslic_conn_slabs_add", "sslic_conn_slabs_finish",
+              "sslic_conn_slabs_relabel"):
+        getattr(L, f).restype = ctypes.c_int
     L.sslic_seed.argtypes = [C, vp, vp, vp]
     L.sslic_iterate.argtypes = [C, vp, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sslic_connectivity.argtypes = [C, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
@@ -341,6 +356,72 @@ class Context:
                     "sslic_run_streamed")
         return {"num_clusters": r.num_clusters, "num_labels": r.num_labels,
                 "iterations": r.iterations, "residual": r.residual}
+
+    # -- one image shared by several GPUs: the calls of one rank ----------------
+    def _plane(self) -> int:
+        return int(np.prod(self.params.size[:-1]))
+
+    def shard_seed(self, image_halo, lo: int, hi: int, centres, stream=None) -> None:
+        """Seeds of the lattice planes in [lo, hi) (sslic_shard_seed);
+        image_halo holds planes [max(0, lo-2), min(N, hi+2)) of the image;
+        the other rows of centres are left zero."""
+        NL = self.params.size[-1]
+        a, b = max(0, lo - 2), min(NL, hi + 2)
+        self._need(image_halo, (b - a) * self._plane() * self.params.channels, "image slab")
+        self._need(centres, self.K * self.centre_width, "centres")
+        self._check(self.lib.sslic_shard_seed(self._c, _ptr(image_halo), int(lo), int(hi), _ptr(centres),
+                                              _stream(stream)), "sslic_shard_seed")
+
+    def shard_sums_size(self) -> tuple:
+        """(uint64 count, double count) of one rank's sums (sslic_shard_sums_size)."""
+        nu, nf = ctypes.c_int64(0), ctypes.c_int64(0)
+        self._check(self.lib.sslic_shard_sums_size(self._c, ctypes.byref(nu), ctypes.byref(nf)),
+                    "sslic_shard_sums_size")
+        return int(nu.value), int(nf.value)
+
+    def shard_map(self, image_slab, labels_slab, lo: int, hi: int, centres, sums, stream=None) -> None:
+        """Assignment of planes [lo, hi) and the map of their sums into
+        ``sums`` (a device buffer of the sslic_shard_sums_size layout)."""
+        n = (hi - lo) * self._plane()
+        self._need(image_slab, n * self.params.channels, "image slab")
+        self._need(labels_slab, n, "label slab")
+        self._need(centres, self.K * self.centre_width, "centres")
+        nu, nf = self.shard_sums_size()
+        if sums.numel() * sums.element_size() != 8 * (nu + nf) or not sums.is_cuda:
+            raise ValueError(f"sums: expected a device buffer of {8 * (nu + nf)} bytes")
+        self._check(self.lib.sslic_shard_map(self._c, _ptr(image_slab), _ptr(labels_slab), int(lo), int(hi),
+                                             _ptr(centres), _ptr(sums), _stream(stream)), "sslic_shard_map")
+
+    def shard_finalize(self, sums, centres_prev, centres_out, residual: bool = False, stream=None):
+        """Centres from the sums of every rank (sslic_shard_finalize)."""
+        self._need(centres_prev, self.K * self.centre_width, "centres_prev")
+        self._need(centres_out, self.K * self.centre_width, "centres_out")
+        res = ctypes.c_double(0.0)
+        self._check(self.lib.sslic_shard_finalize(self._c, _ptr(sums), _ptr(centres_prev), _ptr(centres_out),
+                                                  ctypes.byref(res) if residual else None, _stream(stream)),
+                    "sslic_shard_finalize")
+        return res.value if residual else None
+
+    def conn_slabs_begin(self, centres, stream=None) -> None:
+        self._need(centres, self.K * self.centre_width, "centres")
+        self._check(self.lib.sslic_conn_slabs_begin(self._c, _ptr(centres), _stream(stream)),
+                    "sslic_conn_slabs_begin")
+
+    def conn_slabs_add(self, labels_slab, lo: int, hi: int, stream=None) -> None:
+        self._need(labels_slab, (hi - lo) * self._plane(), "label slab")
+        self._check(self.lib.sslic_conn_slabs_add(self._c, _ptr(labels_slab), int(lo), int(hi), _stream(stream)),
+                    "sslic_conn_slabs_add")
+
+    def conn_slabs_finish(self, stream=None) -> int:
+        n = ctypes.c_int64(0)
+        self._check(self.lib.sslic_conn_slabs_finish(self._c, _stream(stream), ctypes.byref(n)),
+                    "sslic_conn_slabs_finish")
+        return int(n.value)
+
+    def conn_slabs_relabel(self, labels_out_slab, lo: int, hi: int, stream=None) -> None:
+        self._need(labels_out_slab, (hi - lo) * self._plane(), "label slab")
+        self._check(self.lib.sslic_conn_slabs_relabel(self._c, _ptr(labels_out_slab), int(lo), int(hi),
+                                                      _stream(stream)), "sslic_conn_slabs_relabel")
 
     def seed(self, image, centres, stream=None) -> None:
         self._need(image, self._voxels() * self.params.channels, "image")

@@ -94,16 +94,46 @@ def test_streamed_float_within_tolerance(C):
     assert rel.max() <= 1e-5
 
 
+CONN_CASES = [("3d_rgb_ragged", lambda: _synth((70, 52, 150)), (16, 16, 16), 32),
+              ("3d_rgb_s8", lambda: _synth((64, 48, 100)), (8, 8, 8), 32),
+              ("3d_u16", lambda: _synth((48, 40, 100), 1, "u16", sigma=300), (8, 8, 8), 64),
+              ("2d_rgb_rows", lambda: _synth((300, 230)), (16, 16), 64),
+              ("2d_rgb_one_slab", lambda: _synth((130, 60)), (16, 16), 64)]
+
+
+@pytest.mark.parametrize("name,mk,grid,slab", CONN_CASES, ids=[c[0] for c in CONN_CASES])
+def test_streamed_connectivity_equals_resident_and_oracle(name, mk, grid, slab):
+    """With connectivity enforcement (Sec. 3.1 stage 3) the labels pass
+    through the device slab by slab: the result is sslic_run's and the
+    oracle's, bit for bit, label count included."""
+    img = mk()
+    kw = dict(m=10.0, max_iter=4, perturb=True, enforce_connectivity=True)
+    lab, cen, info = _streamed(img, grid, slab, **kw)
+    ref_l, ref_c, ref_i = _run(img, grid, **kw)
+    np.testing.assert_array_equal(lab, ref_l)
+    np.testing.assert_array_equal(cen, ref_c)
+    assert info["num_labels"] == ref_i["num_labels"]
+    o = O.slic(O.params_for(img, grid, **kw), img)
+    np.testing.assert_array_equal(lab, o["labels"])
+    assert info["num_labels"] == o["num_labels"]
+
+
 def test_streamed_rejects():
     import torch
     from paper_1806_08741_gb300 import sslic as S
     img = _synth((64, 48, 40))
     h = torch.from_numpy(img).pin_memory()
     lab = torch.empty(img.shape[:-1], dtype=torch.int32)
-    with S.Context(S.params_for(img, (8, 8, 8), enforce_connectivity=True)) as ctx:
-        with pytest.raises(S.SSLICError) as e:
+    with S.Context(S.params_for(img, (40, 40, 40), enforce_connectivity=True)) as ctx:
+        with pytest.raises(S.SSLICError) as e:   # slabs thinner than S along the last axis
             ctx.run_streamed(h, lab, None, slab_planes=32)
-        assert e.value.code == -6
+        assert e.value.code == -1
+    img2 = _synth((64, 96))
+    with S.Context(S.params_for(img2, (8, 8), enforce_connectivity=True)) as ctx:
+        with pytest.raises(S.SSLICError) as e:   # 2-D connectivity wants slabs of 64 rows
+            ctx.run_streamed(torch.from_numpy(img2).pin_memory(), torch.empty((96, 64), dtype=torch.int32),
+                             None, slab_planes=32)
+        assert e.value.code == -1
     with S.Context(S.params_for(img, (8, 8, 8))) as ctx:
         for bad in (0, 31, 48):
             with pytest.raises(S.SSLICError) as e:

@@ -114,7 +114,13 @@ struct Smem {
     // words -- features, then two packed words (see PackedSums) -- with an odd
     // copy stride so the copies of one word sit in different banks
     static constexpr int kCopies = 8, kPkStride = kCap * (C + 2) + 1;
-    unsigned pk[kCopies * kPkStride];
+    // integer images: kIntCopies copies of each word side by side (word w of
+    // copy j at w * kIntCopies + j), the copy chosen by lane, so that the
+    // lanes of one atomic instruction land in distinct banks (two lanes per
+    // copy: 32 copies measured slower, their shared memory costs a CTA per SM)
+    static constexpr int kIntCopies = 16;
+    unsigned pk[kInBox ? kCap * (C + 2) * kIntCopies : kCopies * kPkStride];
+    unsigned psum[kInBox ? kCap * (C + 2) : 1];  // integer images: the copies' sums
     float cpos[kCap][3];
     int cand[kCap];
     int tmp[kCap];
@@ -158,6 +164,18 @@ __device__ __forceinline__ uint64_t lds64(uint32_t addr)
     uint64_t v;
     asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
     return v;
+}
+
+// The two integer values of a pair word (two 8-bit or two 16-bit voxels) as
+// a packed FP32 pair, exactly: each value v is placed below the exponent of
+// 2^23 (the float with bits 0x4B000000 | v is 2^23 + v, for v < 2^23) and
+// 2^23 is subtracted from both halves at once.
+template <typename T>
+__device__ __forceinline__ uint64_t int_pair_to_f32x2(unsigned v)
+{
+    const unsigned lo = sizeof(T) == 1 ? __byte_perm(v, 0x4B000000u, 0x7540) : __byte_perm(v, 0x4B000000u, 0x7410);
+    const unsigned hi = sizeof(T) == 1 ? __byte_perm(v, 0x4B000000u, 0x7541) : __byte_perm(v, 0x4B000000u, 0x7432);
+    return sub2(pk2(__uint_as_float(lo), __uint_as_float(hi)), pk2(8388608.0f, 8388608.0f));
 }
 
 template <typename T>
@@ -353,7 +371,7 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     if (lists && tid < kListStride) lk = __ldg(a.lists + (int64_t)tile * kListStride + tid);
 
     if (tid == 0) { s.nstage = 0; s.ncand = 0; }
-    for (int i = tid; i < S::kCopies * S::kPkStride; i += kThreads) s.pk[i] = 0u;
+    for (int i = tid; i < (int)(sizeof(s.pk) / sizeof(unsigned)); i += kThreads) s.pk[i] = 0u;
 
     // ---- 1. stage the tile as channel planes (done by the caller when STAGED) ----
     if constexpr (STAGED) {
@@ -511,29 +529,38 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
 
     // ---- per-centre tables and warp-box reach masks -------------------------
     // t_d entry: w_d (x - c)^2 with one rounding per operation, +inf outside
-    auto entry = [&](int d, int j, float c) -> float {
-        const int lo = (int)ceilf(c) - g.S[d];
-        const int x = T0[d] + j;
-        if (x < lo || x > lo + 2 * g.S[d] - 1) return kInf;
-        const float dl = __fsub_rn((float)x, c);
-        return __fmul_rn(g.w[d], __fmul_rn(dl, dl));
-    };
-    for (int i = tid; i < nc * TX; i += kThreads) {
-        const int sl = i / TX, j = i % TX;
-        cand_at<C, SH, float>(s.cd, sl, CL::kOffT0)[j] = entry(0, j, s.cpos[sl][0]);
-    }
-    if constexpr (NDIM >= 2) {
-        for (int i = tid; i < nc * TY; i += kThreads) {
-            const int sl = i / TY, j = i % TY;
-            const float t = entry(1, j, s.cpos[sl][1]);
-            cand_at<C, SH, float2>(s.cd, sl, CL::kOffT1)[j] = make_float2(t, t);
-        }
-    }
-    if constexpr (NDIM >= 3) {
-        for (int i = tid; i < nc * TZ; i += kThreads) {
-            const int sl = i / TZ, j = i % TZ;
-            const float t = entry(2, j, s.cpos[sl][2]);
-            cand_at<C, SH, float2>(s.cd, sl, CL::kOffT2)[j] = make_float2(t, t);
+    // the window [ceil(c) - S_d, ceil(c) + S_d - 1].  One thread fills four
+    // consecutive entries of one axis of one centre (a 16-byte store for
+    // t_0, two for the paired t_1 / t_2).
+    {
+        constexpr int QX = TX / 4, QY = NDIM >= 2 ? TY / 4 : 0, QZ = NDIM >= 3 ? TZ / 4 : 0;
+        constexpr int QA = QX + QY + QZ;
+        static_assert(TX % 4 == 0 && (NDIM < 2 || TY % 4 == 0) && (NDIM < 3 || TZ % 4 == 0), "table chunks");
+        for (int i = tid; i < nc * QA; i += kThreads) {
+            const int sl = i / QA, q = i - sl * QA;
+            const int d = q < QX ? 0 : (q < QX + QY ? 1 : 2);
+            const int j0 = 4 * (d == 0 ? q : (d == 1 ? q - QX : q - QX - QY));
+            const float c = s.cpos[sl][d];
+            const int lo = (int)ceilf(c) - g.S[d];
+            const unsigned span = 2u * (unsigned)g.S[d];
+            const float wd = g.w[d];
+            float t[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int x = T0[d] + j0 + e;
+                const float dl = __fsub_rn((float)x, c);
+                const float v = __fmul_rn(wd, __fmul_rn(dl, dl));
+                t[e] = (unsigned)(x - lo) < span ? v : kInf;
+            }
+            if (d == 0) {
+                *reinterpret_cast<float4*>(cand_at<C, SH, float>(s.cd, sl, CL::kOffT0) + j0) =
+                    make_float4(t[0], t[1], t[2], t[3]);
+            } else {
+                float4* dst = reinterpret_cast<float4*>(
+                    cand_at<C, SH, float2>(s.cd, sl, d == 1 ? CL::kOffT1 : CL::kOffT2) + j0);
+                dst[0] = make_float4(t[0], t[0], t[1], t[1]);
+                dst[1] = make_float4(t[2], t[2], t[3], t[3]);
+            }
         }
     }
     for (int i = tid; i < nc; i += kThreads) {
@@ -591,13 +618,8 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
         for (int c = 0; c < C; ++c)
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                if constexpr (S::kF) {
-                    Fp[c][q] = plane_pair_f(s, c, xl + 2 * q, yl, zl);
-                } else {
-                    unsigned lo, hi;
-                    split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), lo, hi);
-                    Fp[c][q] = pk2((float)lo, (float)hi);
-                }
+                if constexpr (S::kF) Fp[c][q] = plane_pair_f(s, c, xl + 2 * q, yl, zl);
+                else Fp[c][q] = int_pair_to_f32x2<T>(plane_pair(s, c, xl + 2 * q, yl, zl));
             }
         float bd[VL];
         int bs[VL];
@@ -664,21 +686,22 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
 #pragma unroll
             for (int c = 0; c < C; ++c)
 #pragma unroll
-                for (int q = 0; q < NP; ++q) split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), val[c][2 * q], val[c][2 * q + 1]);
+                for (int q = 0; q < NP; ++q)
+                    split_pair<T>(plane_pair(s, c, xl + 2 * q, yl, zl), val[c][2 * q], val[c][2 * q + 1]);
             int lab[VL];
             // copy: the lanes that share one differ in more than one axis of
             // the box, so that they seldom add to the same slot at once
-            unsigned* const mypk = s.pk + ((lane ^ (lane >> 3)) & (S::kCopies - 1)) * S::kPkStride;
+            unsigned* const mypk = s.pk + (lane & (S::kIntCopies - 1));
 #pragma unroll
             for (int v = 0; v < VL; ++v) {
                 const bool in = rowin && xl + v < ex && bs[v] != kNoSlot;
                 lab[v] = in ? s.cand[bs[v]] : -1;
                 if (in) {
-                    unsigned* w = mypk + bs[v] * (C + 2);
+                    unsigned* w = mypk + bs[v] * (C + 2) * S::kIntCopies;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) atomicAdd(&w[c], val[c][v]);
-                    atomicAdd(&w[C], (unsigned)(xl + v) | (1u << PackedSums::kCnt));
-                    atomicAdd(&w[C + 1], (unsigned)yl | ((unsigned)zl << PackedSums::kZ));
+                    for (int c = 0; c < C; ++c) atomicAdd(&w[c * S::kIntCopies], val[c][v]);
+                    atomicAdd(&w[C * S::kIntCopies], (unsigned)(xl + v) | (1u << PackedSums::kCnt));
+                    atomicAdd(&w[(C + 1) * S::kIntCopies], (unsigned)yl | ((unsigned)zl << PackedSums::kZ));
                 }
             }
             if (rowin) {
@@ -819,19 +842,37 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     }
 
     // ---- 5. per-tile sums, shifted to global coordinates ----------------------
-    // the copies are summed field by field (each field's total fits its width)
+    // the copies are summed word by word (each field's total fits its width)
+    if constexpr (S::kInBox) {
+        // one word per thread; copy j read at (j + word) mod kIntCopies, so
+        // that the threads of a warp read distinct banks
+        for (int wd = tid; wd < nc * (C + 2); wd += kThreads) {
+            unsigned t = 0;
+#pragma unroll
+            for (int j = 0; j < S::kIntCopies; ++j) t += s.pk[wd * S::kIntCopies + ((j + wd) & (S::kIntCopies - 1))];
+            s.psum[wd] = t;
+        }
+        __syncthreads();
+    }
     for (int i = tid; i < nc * F; i += kThreads) {
         const int sl = i / F, f = i % F;
         unsigned wx = 0, wyz = 0;
         FeatAcc<T> wf = 0;
+        if constexpr (S::kInBox) {
+            const unsigned* w = s.psum + sl * (C + 2);
+            wx = w[C];
+            if (f == C + 1 || f == C + 2) wyz = w[C + 1];
+            if (f < C) wf = w[f];
+        } else {
 #pragma unroll
-        for (int k = 0; k < S::kCopies; ++k) {
-            const unsigned* w = s.pk + k * S::kPkStride + sl * (C + 2);
-            wx += w[C];
-            if (f == C + 1 || f == C + 2) wyz += w[C + 1];
-            if (f < C) {
-                if constexpr (S::kF) wf += __uint_as_float(w[f]);
-                else wf += w[f];
+            for (int k = 0; k < S::kCopies; ++k) {
+                const unsigned* w = s.pk + k * S::kPkStride + sl * (C + 2);
+                wx += w[C];
+                if (f == C + 1 || f == C + 2) wyz += w[C + 1];
+                if (f < C) {
+                    if constexpr (S::kF) wf += __uint_as_float(w[f]);
+                    else wf += w[f];
+                }
             }
         }
         const unsigned long long cnt = wx >> PackedSums::kCnt;

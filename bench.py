@@ -411,12 +411,24 @@ def run_ours(args, w):
     if rank == 0 and world == 1 and not args.no_precision:
         precision = precision_bench(steps=max(3, args.steps))
 
+    small = None
+    if rank == 0 and world == 1 and not args.no_small:
+        small = small_configs_bench()
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serve:
         ctx.close()
         del img, labels, centres
         torch.cuda.empty_cache()
-        serving = serving_bench(n_req=args.serve_requests, max_active=args.serve_max_active)
+        pool = serving_pool()
+        serving = {
+            # the arrival rate of the stream's recipe: more than either form serves
+            "overloaded": serving_bench(n_req=args.serve_requests, rate=200.0, max_active=args.serve_max_active,
+                                        pool=pool),
+            # a rate both forms keep up with
+            "under_capacity": serving_bench(n_req=args.serve_requests_low, rate=args.serve_rate_low,
+                                            max_active=args.serve_max_active, pool=pool),
+        }
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -435,7 +447,7 @@ def run_ours(args, w):
                        "num_labels": info["num_labels"], "K": info["num_clusters"]},
             "tile_shape": tune, "assign_update_loop": loop,
             "roofline": roof, "roofline_alu": roof_alu, "phases": phases, "e2e": e2e, "cpu_baseline": cpu, "serving": serving,
-            "precision": precision, "lab": lab, "streamed": streamed,
+            "precision": precision, "lab": lab, "streamed": streamed, "small_configs": small,
             "gpu_launches": prof["kernel_launches"], "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -611,21 +623,57 @@ def precision_bench(steps=3, warmup=2):
 # ---------------------------------------------------------------------------
 # serving: request stream, continuous batching vs one image per launch
 # ---------------------------------------------------------------------------
-def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=16):
-    """Poisson arrivals (rate per second) of requests mixing 2-D RGB uint8
-    tiles (side ~ U[256, 4096]) and 3-D uint16 blocks (side ~ U[128, 512]),
-    S in {8, 16, 32}, m in {5, 10, 20}, 10 iterations.  Inputs come from a
-    pool of pool_n images of each kind (made on the GPU, kept in page-locked
-    host memory).  Returns latency percentiles and throughput of the served
-    form (sslic_server_*) and of the plain form (one sslic_run_host call per
-    request, in arrival order)."""
-    import threading
+def small_configs_bench(reps=20, warmup=3):
+    """Whole-run latency of the two 2-D workloads (256x256 RGB, K = 256, no
+    connectivity; 2048x1216 RGB, K = 9728, connectivity on): seeding, 10
+    iterations and connectivity through sslic_run on a device-resident image,
+    CUDA events around each run; median and minimum of `reps` runs after
+    `warmup`.  Both fit in the L2 (a few MB), so these are latency figures."""
+    import statistics as st_
 
-    import numpy as np
     import torch
 
     from paper_1806_08741_gb300 import inputs
     from paper_1806_08741_gb300 import sslic as S
+
+    out = {}
+    for name in ("rgb2d_256", "rgb2d_2048x1216"):
+        w = inputs.WORKLOADS[name]
+        spec = w.image
+        img = torch.empty(spec.shape, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.current_stream()
+        inputs.make_image_device(spec, img.data_ptr(), stream.cuda_stream)
+        p = S.Params(size=spec.size, grid=w.grid, channels=spec.channels, dtype=S.U8, m=w.m,
+                     max_iter=w.max_iter, perturb=w.perturb, enforce_connectivity=w.connectivity)
+        ms = []
+        with S.Context(p) as ctx:
+            lab = torch.empty(spec.shape[:-1], dtype=torch.int32, device="cuda")
+            cen = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+            for i in range(warmup + reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                info = ctx.run(img, lab, cen, stream=stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if i >= warmup:
+                    ms.append(a.elapsed_time(b))
+        med = st_.median(ms)
+        out[name] = {"ms_median": med, "ms_min": min(ms), "runs": reps,
+                     "value": spec.voxels * w.max_iter / (med / 1e3) / 1e9, "unit": UNIT,
+                     "K": info["num_clusters"], "num_labels": info["num_labels"],
+                     "connectivity": w.connectivity}
+    return out
+
+
+def serving_pool(seed=1810, pool_n=12):
+    """The request stream's input images: pool_n 2-D RGB uint8 tiles (side
+    ~ U[256, 4096]) and pool_n 3-D uint16 blocks (side ~ U[128, 512]), made
+    on the GPU and kept in page-locked host memory."""
+    import numpy as np
+    import torch
+
+    from paper_1806_08741_gb300 import inputs
 
     rng = np.random.default_rng(seed)
     pool = []
@@ -648,6 +696,25 @@ def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, m
         host.append(h)
         del d
     torch.cuda.synchronize()
+    return pool, host
+
+
+def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=16, pool=None):
+    """Poisson arrivals (rate per second) of requests over the images of
+    serving_pool (2-D RGB uint8 and 3-D uint16), S in {8, 16, 32}, m in
+    {5, 10, 20}, 10 iterations.  Returns latency percentiles and throughput
+    of the served form (sslic_server_*) and of the plain form (one
+    sslic_run_host call per request, in arrival order)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1806_08741_gb300 import sslic as S
+
+    pool, host = pool if pool is not None else serving_pool(seed, pool_n)
+    pool_n = len(pool) // 2
+    rng = np.random.default_rng(seed + int(rate))
     reqs = []
     t = 0.0
     for _ in range(n_req):
@@ -761,7 +828,10 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="only the request-stream benchmark (served vs plain form)")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-stream benchmark")
-    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--no-small", action="store_true", help="skip the latency of the two 2-D workloads")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the overloaded stream")
+    ap.add_argument("--serve-requests-low", type=int, default=1000, help="requests of the under-capacity stream")
+    ap.add_argument("--serve-rate-low", type=float, default=60.0, help="arrivals per second, under capacity")
     ap.add_argument("--serve-max-active", type=int, default=16, help="requests the server advances at once")
     args = ap.parse_args()
     if args.lab_only:
@@ -783,7 +853,12 @@ def main():
     if args.serve:
         import torch
         torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
-        print(json.dumps({"serving": serving_bench(n_req=args.serve_requests, max_active=args.serve_max_active)}), flush=True)
+        pool = serving_pool()
+        out = {"overloaded": serving_bench(n_req=args.serve_requests, rate=200.0, max_active=args.serve_max_active,
+                                           pool=pool),
+               "under_capacity": serving_bench(n_req=args.serve_requests_low, rate=args.serve_rate_low,
+                                               max_active=args.serve_max_active, pool=pool)}
+        print(json.dumps({"serving": out}), flush=True)
         return 0
     from paper_1806_08741_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]

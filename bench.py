@@ -47,17 +47,19 @@ UNIT = "Gvoxel-iter/s"
 # a changed kernel reports null until it is profiled again.
 TRAFFIC_BYTES = {
     # ncu capture of the tile kernel on the 67.1 M-voxel profiling workload
-    # (rgb3d_512x512x256): 206.2 MB read + 215.6 MB written per launch,
+    # (rgb3d_512x512x256): 205.9 MB read + 225.6 MB written per launch,
     # scaled by the voxel ratio (69.4x) to the 4.66 G-voxel launch
-    ("rgb3d_2048x1216x1871", "35699e2f6ca5ead379988be9e0211bb6e09f10d298d517ea1a334f75d50b6efa"):
-        (206.195456e6 + 215.622656e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
+    ("rgb3d_2048x1216x1871", "df92a51670901b6b9f874261746970d26fa86ac3700d1c01c0016afb7f99ff61"):
+        (205.899520e6 + 225.605888e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
 }
-
 
 # thread instructions per voxel of the dominant kernel (ncu
 # smsp__inst_executed.sum x 32 / voxels on the profiling workload), keyed by
 # the SHA-256 of the kernel's source file like TRAFFIC_BYTES
-INST_PER_VOXEL = {}
+INST_PER_VOXEL = {
+    # 506,014,391 warp instructions x 32 / 67,108,864 voxels (the capture above)
+    "df92a51670901b6b9f874261746970d26fa86ac3700d1c01c0016afb7f99ff61": 506014391 * 32 / (512 * 512 * 256),
+}
 
 
 def _sha(path):

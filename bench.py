@@ -49,16 +49,16 @@ TRAFFIC_BYTES = {
     # ncu capture of the tile kernel on the 67.1 M-voxel profiling workload
     # (rgb3d_512x512x256): 205.9 MB read + 225.6 MB written per launch,
     # scaled by the voxel ratio (69.4x) to the 4.66 G-voxel launch
-    ("rgb3d_2048x1216x1871", "df92a51670901b6b9f874261746970d26fa86ac3700d1c01c0016afb7f99ff61"):
-        (205.899520e6 + 225.605888e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
+    ("rgb3d_2048x1216x1871", "24eed49e3b93b3f200d91a1b5d4d4198870934ab65437ecf8756919e3aabab26"):
+        (205.921024e6 + 225.578752e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
 }
 
 # thread instructions per voxel of the dominant kernel (ncu
 # smsp__inst_executed.sum x 32 / voxels on the profiling workload), keyed by
 # the SHA-256 of the kernel's source file like TRAFFIC_BYTES
 INST_PER_VOXEL = {
-    # 506,014,391 warp instructions x 32 / 67,108,864 voxels (the capture above)
-    "df92a51670901b6b9f874261746970d26fa86ac3700d1c01c0016afb7f99ff61": 506014391 * 32 / (512 * 512 * 256),
+    # 501,898,965 warp instructions x 32 / 67,108,864 voxels (the capture above)
+    "24eed49e3b93b3f200d91a1b5d4d4198870934ab65437ecf8756919e3aabab26": 501898965 * 32 / (512 * 512 * 256),
 }
 
 
@@ -327,7 +327,11 @@ def run_ours(args, w):
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"of {peak_src}", "bytes_per_launch": algo,
                 "bytes_per_voxel": bytes_per_vox, "avg_launch_ms": a_ms / a_calls,
-                "traffic": TRAFFIC_BYTES.get((w.name, src))}
+                "traffic": TRAFFIC_BYTES.get((w.name, src)),
+                "traffic_note": "ncu DRAM read + write of one launch on the 67.1 M-voxel profiling workload, scaled by "
+                                "the voxel ratio; labels still in the L2 when that launch ends are written back after "
+                                "it, so the write side is undercounted: a check that the image is read once, not a "
+                                "full count of the launch's writes"}
     # the same kernel against the SM's FP32 lanes, the unit that bounds it:
     # per (voxel, covering centre) pair the canonical D^2 costs C subtractions,
     # C products and C - 1 + n sums once the per-axis terms are tabulated per

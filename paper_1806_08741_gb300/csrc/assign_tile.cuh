@@ -374,30 +374,32 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     for (int i = tid; i < (int)(sizeof(s.pk) / sizeof(unsigned)); i += kThreads) s.pk[i] = 0u;
 
     // ---- 1. stage the tile as channel planes (done by the caller when STAGED) ----
+    // 8-bit colour images with full rows: every thread issues the loads of its
+    // 12-byte groups (4 voxels) here and writes them into the planes only
+    // after the candidate tables are built, so that the image's latency
+    // overlaps the record's rows and the tables
+    constexpr int GPR = TX / 4;                                 // groups per row
+    constexpr int NG = TY * TZ * GPR;                           // groups per tile
+    constexpr int GPT = (NG + kThreads - 1) / kThreads;         // groups per thread
+    constexpr bool kDefer = !STAGED && sizeof(T) == 1 && C == 3;
+    uint32_t ga[kDefer ? GPT : 1], gb[kDefer ? GPT : 1], gc[kDefer ? GPT : 1];
+    bool fast = false;
     if constexpr (STAGED) {
     } else if constexpr (sizeof(T) == 1 && C == 3) {
-        // full rows: 12-byte groups (4 voxels) -> one word per plane
-        const bool fast = (ex == TX) && ((N0 * 3) % 4 == 0) && (((uintptr_t)img & 3) == 0);
+        fast = (ex == TX) && ((N0 * 3) % 4 == 0) && (((uintptr_t)img & 3) == 0);
         if (fast) {
-            constexpr int GPR = TX / 4;  // groups per row
-            for (int i = tid; i < TY * TZ * GPR; i += kThreads) {
+#pragma unroll
+            for (int k = 0; k < GPT; ++k) {
+                const int i = tid + k * kThreads;
                 const int r = i / GPR, gi = i % GPR, yl = r % TY, zl = r / TY;
-                uint32_t a = 0, b = 0, cc = 0;
-                if (yl < ey && zl < ez) {
+                ga[k] = gb[k] = gc[k] = 0;
+                if (i < NG && yl < ey && zl < ez) {
                     const uint32_t* src = reinterpret_cast<const uint32_t*>(
                         img + (vidx(g, X0, Y0 + yl, Z0 + zl) + gi * 4) * 3);
-                    a = __ldg(src);
-                    b = __ldg(src + 1);
-                    cc = __ldg(src + 2);
+                    ga[k] = __ldg(src);
+                    gb[k] = __ldg(src + 1);
+                    gc[k] = __ldg(src + 2);
                 }
-                // bytes: a = R0 G0 B0 R1, b = G1 B1 R2 G2, cc = B2 R3 G3 B3
-                const uint32_t R = __byte_perm(__byte_perm(a, b, 0x0630), cc, 0x5210);
-                const uint32_t Gv = __byte_perm(__byte_perm(a, b, 0x0741), cc, 0x6210);
-                const uint32_t B = __byte_perm(__byte_perm(a, b, 0x0052), cc, 0x7410);
-                unsigned char* row = s.planes + zl * S::PPB + yl * S::RPB + gi * 4;
-                *reinterpret_cast<uint32_t*>(row) = R;
-                *reinterpret_cast<uint32_t*>(row + S::CPB) = Gv;
-                *reinterpret_cast<uint32_t*>(row + 2 * S::CPB) = B;
             }
         } else {
             for (int i = tid; i < TV; i += kThreads) {
@@ -581,6 +583,23 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     for (int i = tid; i < TY; i += kThreads) cand_at<C, SH, float2>(s.cd, kCap, CL::kOffT1)[i] = make_float2(kInf, kInf);
     for (int i = tid; i < TZ; i += kThreads) cand_at<C, SH, float2>(s.cd, kCap, CL::kOffT2)[i] = make_float2(kInf, kInf);
     if (tid < C) cand_at<C, SH, float2>(s.cd, kCap, CL::kOffFe)[tid] = make_float2(0.0f, 0.0f);
+    if constexpr (kDefer) {
+        if (fast) {
+            // the staged groups into the planes
+#pragma unroll
+            for (int k = 0; k < GPT; ++k) {
+                const int i = tid + k * kThreads;
+                if (i >= NG) break;
+                const int r = i / GPR, gi = i % GPR, yl = r % TY, zl = r / TY;
+                const uint32_t a_ = ga[k], b_ = gb[k], c_ = gc[k];
+                // bytes: a = R0 G0 B0 R1, b = G1 B1 R2 G2, c = B2 R3 G3 B3
+                unsigned char* row = s.planes + zl * S::PPB + yl * S::RPB + gi * 4;
+                *reinterpret_cast<uint32_t*>(row) = __byte_perm(__byte_perm(a_, b_, 0x0630), c_, 0x5210);
+                *reinterpret_cast<uint32_t*>(row + S::CPB) = __byte_perm(__byte_perm(a_, b_, 0x0741), c_, 0x6210);
+                *reinterpret_cast<uint32_t*>(row + 2 * S::CPB) = __byte_perm(__byte_perm(a_, b_, 0x0052), c_, 0x7410);
+            }
+        }
+    }
     __syncthreads();
     // per warp box: the slots whose window reaches it, ascending, padded to
     // an even count with the dummy so the sweep takes two centres per step

@@ -425,6 +425,18 @@ typedef struct {
 /* Turn phase timing on (1) or off (0); both reset the counters. */
 SSLIC_API int sslic_profile_enable(sslic_ctx* c, int32_t on);
 
+/* Replay of the iterated loop (Sec. 3.1, steps 2-3) from a CUDA graph: on (1,
+ * the default) or off (0).  When it is on, phase timing is off, the run has
+ * no convergence threshold and max_iter >= 2, sslic_run / sslic_run_from /
+ * sslic_run_host run the first iteration eagerly, capture the next one
+ * (bins, assignment + update, reduce) from a stream the context owns, and
+ * replay that graph on the caller's stream for the remaining iterations.
+ * Results are bit-identical either way; the graph only removes per-kernel
+ * launch latency, which dominates on small images.  The executable graph is
+ * cached in the context and updated in place on later runs.
+ * Returns SSLIC_EINVAL for a null context. */
+SSLIC_API int sslic_set_loop_graph(sslic_ctx* c, int32_t enable);
+
 /* Read the counters (host struct).  Synchronises on the recorded events. */
 SSLIC_API int sslic_profile_read(sslic_ctx* c, sslic_profile* out);
 

@@ -306,6 +306,54 @@ static int read_residual(sslic_ctx* c, cudaStream_t st, double* r)
     return cuda_check(c, cudaStreamSynchronize(st), "sync");
 }
 
+// A fixed number of iterations (no convergence threshold, so no host read
+// between them) launches the same dozen small kernels every iteration; on
+// small images their launch latency is most of the run.  The first iteration
+// runs eagerly (it sets kernel attributes and leaves nothing to allocate),
+// the next is captured from a private stream into a graph, and the graph is
+// replayed for the rest.  The cached executable graph is updated in place
+// when the new capture has its topology (other buffers, same tile shape), else
+// instantiated anew.  Phase timing records events per launch, so it runs
+// eagerly.
+static bool loop_graph_applies(const sslic_ctx* c)
+{
+    return c->loop_graph && !c->prof_on && !(c->p.conv_threshold > 0.0) && c->p.max_iter >= 2;
+}
+
+static int capture_iteration(sslic_ctx* c, const void* image, int32_t* labels, int64_t* per_iter)
+{
+    int rc;
+    if (!c->cap_stream &&
+        (rc = cuda_check(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "capture stream")))
+        return rc;
+    const int64_t l0 = c->launches;
+    if ((rc = cuda_check(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed), "begin capture")))
+        return rc;
+    rc = build_bins(c, c->cap_stream);
+    if (!rc) rc = launch_assign_update(c, image, labels, c->cap_stream);
+    if (!rc) rc = launch_finalize(c, c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    *per_iter = c->launches - l0;
+    c->launches = l0;
+    if (!rc) rc = cuda_check(c, e, "end capture");
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (c->loop_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->loop_exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->loop_exec);
+            c->loop_exec = nullptr;
+        }
+    }
+    if (!c->loop_exec) rc = cuda_check(c, cudaGraphInstantiate(&c->loop_exec, graph, 0), "instantiate graph");
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
 // the loop of Sec. 3.1 from the centres already in the workspace
 static int run_loop(sslic_ctx* c, const void* image, int32_t* labels, float* centres, cudaStream_t st,
                     sslic_result* out)
@@ -313,7 +361,17 @@ static int run_loop(sslic_ctx* c, const void* image, int32_t* labels, float* cen
     int rc;
     int it = 0;
     double res = 0.0;
+    const bool graph = loop_graph_applies(c);
     for (it = 0; it < c->p.max_iter; ++it) {
+        if (graph && it == 1) {
+            int64_t per_iter = 0;
+            if ((rc = capture_iteration(c, image, labels, &per_iter))) return rc;
+            for (; it < c->p.max_iter; ++it) {
+                if ((rc = cuda_check(c, cudaGraphLaunch(c->loop_exec, st), "graph launch"))) return rc;
+                count_launch(c, (int)per_iter);
+            }
+            break;
+        }
         if ((rc = build_bins(c, st))) return rc;
         if ((rc = launch_assign_update(c, image, labels, st))) return rc;
         if ((rc = launch_finalize(c, st))) return rc;
@@ -684,6 +742,13 @@ int sslic_profile_enable(sslic_ctx* c, int32_t on)
     return cuda_check(c, cudaMemset(c->ws.hc_rechecks, 0, sizeof(unsigned long long)), "reset counters");
 }
 
+int sslic_set_loop_graph(sslic_ctx* c, int32_t enable)
+{
+    if (!c) return SSLIC_EINVAL;
+    c->loop_graph = enable ? 1 : 0;
+    return SSLIC_OK;
+}
+
 int sslic_profile_read(sslic_ctx* c, sslic_profile* out)
 {
     if (!c || !out) return SSLIC_EINVAL;
@@ -710,6 +775,8 @@ void sslic_destroy(sslic_ctx* c)
     if (!c) return;
     cudaDeviceSynchronize();
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     free_all(c);
     delete c;
 }

@@ -207,6 +207,11 @@ struct sslic_ctx {
     int tile_shape = -1;   // assignment tile shape index, -1 = chosen from the grid (assign_tile.cu)
     int status_pending = 0;  // a kernel with bounded waits ran: check the status flag
     char err[512] = {0};
+    // the iterated loop of a run replayed from a CUDA graph (run_loop): the
+    // private stream it is captured from and the cached executable graph
+    int loop_graph = 1;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t loop_exec = nullptr;
     // tracing
     int prof_on = 0;
     int64_t launches = 0;

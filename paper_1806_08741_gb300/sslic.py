@@ -28,7 +28,7 @@ EXPORTS = ("sslic_default_params", "sslic_create", "sslic_num_clusters", "sslic_
            "sslic_server_destroy", "sslic_num_tile_shapes", "sslic_tile_shape_info",
            "sslic_set_tile_shape", "sslic_get_tile_shape", "sslic_autotune", "sslic_tune_forget",
            "sslic_tune_record", "sslic_tune_lookup", "sslic_precision_probe", "sslic_srgb_to_lab",
-           "sslic_profile_enable", "sslic_profile_read", "sslic_destroy",
+           "sslic_profile_enable", "sslic_profile_read", "sslic_set_loop_graph", "sslic_destroy",
            "sslic_strerror", "sslic_last_error", "sslic_shard_seed", "sslic_shard_sums_size",
            "sslic_shard_map", "sslic_shard_finalize", "sslic_conn_slabs_begin", "sslic_conn_slabs_add",
            "sslic_conn_slabs_finish", "sslic_conn_slabs_relabel")
@@ -161,6 +161,8 @@ def load(path: str = LIB_PATH):
     L.sslic_srgb_to_lab.restype = ctypes.c_int
     L.sslic_iterate_static.restype = ctypes.c_int
     L.sslic_profile_enable.argtypes = [C, ctypes.c_int32]
+    L.sslic_set_loop_graph.argtypes = [C, ctypes.c_int32]
+    L.sslic_set_loop_graph.restype = ctypes.c_int
     L.sslic_profile_read.argtypes = [C, ctypes.POINTER(_Profile)]
     L.sslic_profile_enable.restype = ctypes.c_int
     L.sslic_profile_read.restype = ctypes.c_int
@@ -495,6 +497,10 @@ class Context:
     def profile_enable(self, on: bool = True) -> None:
         """Start (or stop) per-phase CUDA-event timing; resets the counters."""
         self._check(self.lib.sslic_profile_enable(self._c, int(bool(on))), "sslic_profile_enable")
+
+    def set_loop_graph(self, on: bool = True) -> None:
+        """Replay the iterated loop of a run from a CUDA graph (default) or launch it eagerly."""
+        self._check(self.lib.sslic_set_loop_graph(self._c, int(bool(on))), "sslic_set_loop_graph")
 
     def profile_read(self) -> dict:
         """{phase: (ms, calls)} plus 'kernel_launches' since the last enable."""

@@ -119,7 +119,7 @@ struct Smem {
     // lanes of one atomic instruction land in distinct banks (two lanes per
     // copy: 32 copies measured slower, their shared memory costs a CTA per SM)
     static constexpr int kIntCopies = 16;
-    unsigned pk[kInBox ? kCap * (C + 2) * kIntCopies : kCopies * kPkStride];
+    alignas(16) unsigned pk[kInBox ? kCap * (C + 2) * kIntCopies : kCopies * kPkStride];
     unsigned psum[kInBox ? kCap * (C + 2) : 1];  // integer images: the copies' sums
     float cpos[kCap][3];
     int cand[kCap];
@@ -371,7 +371,11 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     if (lists && tid < kListStride) lk = __ldg(a.lists + (int64_t)tile * kListStride + tid);
 
     if (tid == 0) { s.nstage = 0; s.ncand = 0; }
-    for (int i = tid; i < (int)(sizeof(s.pk) / sizeof(unsigned)); i += kThreads) s.pk[i] = 0u;
+    if constexpr (sizeof(s.pk) % 16 == 0) {
+        for (int i = tid; i < (int)(sizeof(s.pk) / 16); i += kThreads) reinterpret_cast<uint4*>(s.pk)[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        for (int i = tid; i < (int)(sizeof(s.pk) / sizeof(unsigned)); i += kThreads) s.pk[i] = 0u;
+    }
 
     // ---- 1. stage the tile as channel planes (done by the caller when STAGED) ----
     // 8-bit colour images with full rows: every thread issues the loads of its
@@ -660,8 +664,16 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
             if (NDIM >= 2) t1 = lds64(a1 + so);
             if (NDIM >= 3) t2 = lds64(a2 + so);
             uint64_t fe[C];
+            // feature pairs two channels per 16-byte load where the record allows
 #pragma unroll
-            for (int c = 0; c < C; ++c) fe[c] = lds64(af + so + c * 8);
+            for (int c = 0; c < C; c += 2) {
+                if (c + 1 < C && CL::kOffFe % 16 == 0) {
+                    lds128(af + so + c * 8, fe[c], fe[c + 1]);
+                } else {
+                    fe[c] = lds64(af + so + c * 8);
+                    if (c + 1 < C) fe[c + 1] = lds64(af + so + (c + 1) * 8);
+                }
+            }
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 uint64_t dc;
@@ -863,12 +875,18 @@ __device__ __forceinline__ void tile_body(const TileArgs& a, int tile, int64_t r
     // ---- 5. per-tile sums, shifted to global coordinates ----------------------
     // the copies are summed word by word (each field's total fits its width)
     if constexpr (S::kInBox) {
-        // one word per thread; copy j read at (j + word) mod kIntCopies, so
-        // that the threads of a warp read distinct banks
+        // one word per thread, its 16 copies as four 16-byte loads; quarter q
+        // is read at step (q + word / 2) mod 4, so that the 8 threads of each
+        // load phase cover the 32 banks once
+        static_assert(S::kIntCopies == 16, "four 16-byte quarters per word");
         for (int wd = tid; wd < nc * (C + 2); wd += kThreads) {
+            const uint4* w4 = reinterpret_cast<const uint4*>(s.pk + wd * S::kIntCopies);
             unsigned t = 0;
 #pragma unroll
-            for (int j = 0; j < S::kIntCopies; ++j) t += s.pk[wd * S::kIntCopies + ((j + wd) & (S::kIntCopies - 1))];
+            for (int j = 0; j < 4; ++j) {
+                const uint4 v = w4[(j + (wd >> 1)) & 3];
+                t += (v.x + v.y) + (v.z + v.w);
+            }
             s.psum[wd] = t;
         }
         __syncthreads();

@@ -115,7 +115,13 @@ SSLIC_API int sslic_run_from(sslic_ctx* c, const void* image_dev, const float* i
  * method runs, labels (and centres if non-NULL) are copied back, and the
  * call returns after the stream is synchronised.  Page-locked buffers give
  * the full copy bandwidth; pageable ones work but copy synchronously.  The
- * context allocates its device image/label buffers on first use. */
+ * context allocates its device image/label buffers on first use.  For 2-D
+ * and 3-D images (except float images with 16 or more channels) with a grid
+ * of at least 8 along the last axis and at least 128 planes along it, the
+ * upload runs on a copy stream of the context in pieces -- first the planes
+ * seeding reads, then slabs of 64 planes -- and seeding and each slab's first
+ * assignment start as soon as their planes are in; the results are those of
+ * the single copy (bit for bit for integer images). */
 SSLIC_API int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host,
                    float* centres_host, void* stream, sslic_result* out);
 

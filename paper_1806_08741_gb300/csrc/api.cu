@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -355,14 +356,20 @@ static int capture_iteration(sslic_ctx* c, const void* image, int32_t* labels, i
 }
 
 // the loop of Sec. 3.1 from the centres already in the workspace
+// (first_it iterations already ran, e.g. overlapped with the upload)
 static int run_loop(sslic_ctx* c, const void* image, int32_t* labels, float* centres, cudaStream_t st,
-                    sslic_result* out)
+                    sslic_result* out, int first_it = 0)
 {
     int rc;
     int it = 0;
     double res = 0.0;
     const bool graph = loop_graph_applies(c);
-    for (it = 0; it < c->p.max_iter; ++it) {
+    bool stop = false;
+    if (first_it > 0 && c->p.conv_threshold > 0.0) {
+        if ((rc = read_residual(c, st, &res))) return rc;
+        stop = res < c->p.conv_threshold;
+    }
+    for (it = first_it; !stop && it < c->p.max_iter; ++it) {
         if (graph && it == 1) {
             int64_t per_iter = 0;
             if ((rc = capture_iteration(c, image, labels, &per_iter))) return rc;
@@ -480,6 +487,104 @@ int sslic_run_from(sslic_ctx* c, const void* image_dev, const float* init_centre
     return run_loop(c, image_dev, labels_dev, centres_dev, st, out);
 }
 
+}  // extern "C"
+
+namespace sslic {
+
+// sslic_run_host's upload overlapped with seeding and the first iteration:
+// images whose slabs along the last axis take the slab-restricted assignment
+// launches, with lattice rows at least 8 planes apart and at least two slabs
+static constexpr int64_t kHostSlab = 64;  // planes per slab: a multiple of every tile extent along that axis
+static bool host_pipeline_applies(const sslic_ctx* c)
+{
+    const Geom& g = c->g;
+    return (g.n == 2 || g.n == 3) && !hc_applies(g) && !c->p.precision && g.S[g.n - 1] >= 8 &&
+           c->p.max_iter >= 1 && g.N[g.n - 1] >= 2 * kHostSlab;
+}
+
+// On the context's copy stream: first the planes that seeding reads (the
+// lattice planes along the last axis and, with the perturbation, two on each
+// side of them: its gradients' reach), then the rest slab by slab.  Seeding
+// and the bins start once the first part is in; each slab's assignment of the
+// first iteration starts once its planes are in.  Integer images: each slab
+// adds its exact sums, so labels and centres equal the unsplit launch's.
+static int host_upload_first_iteration(sslic_ctx* c, const void* image_host, cudaStream_t st)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    int rc;
+    if (!w.copy_stream &&
+        (rc = cuda_check(c, cudaStreamCreateWithFlags(&w.copy_stream, cudaStreamNonBlocking), "copy stream")))
+        return rc;
+    for (int i = 0; i < 2; ++i)
+        if (!w.slab_ev[i] &&
+            (rc = cuda_check(c, cudaEventCreateWithFlags(&w.slab_ev[i], cudaEventDisableTiming), "events")))
+            return rc;
+    cudaStream_t cs = w.copy_stream;
+    const int ax = g.n - 1;
+    const int64_t NL = g.N[ax];
+    int64_t plane = 1;
+    for (int d = 0; d < ax; ++d) plane *= g.N[d];
+    const size_t esz = g.dtype == SSLIC_U8 ? 1 : (g.dtype == SSLIC_U16 ? 2 : 4);
+    const size_t pbytes = (size_t)plane * g.C * esz;
+    const unsigned char* src = (const unsigned char*)image_host;
+    unsigned char* dst = (unsigned char*)w.img_dev;
+    auto put = [&](int64_t a, int64_t b) {
+        return cuda_check(c, cudaMemcpyAsync(dst + a * pbytes, src + a * pbytes, (size_t)(b - a) * pbytes,
+                                             cudaMemcpyHostToDevice, cs),
+                          "H2D");
+    };
+    // st waits for what is on cs so far
+    auto ready = [&]() {
+        int r = cuda_check(c, cudaEventRecord(w.slab_ev[1], cs), "event");
+        return r ? r : cuda_check(c, cudaStreamWaitEvent(st, w.slab_ev[1], 0), "wait");
+    };
+    // the copies start after the work the caller queued on st
+    if ((rc = cuda_check(c, cudaEventRecord(w.slab_ev[0], st), "event")) ||
+        (rc = cuda_check(c, cudaStreamWaitEvent(cs, w.slab_ev[0], 0), "wait")))
+        return rc;
+    // 1. the planes seeding reads, as ascending disjoint intervals
+    const int64_t reach = c->p.perturb ? 2 : 0;
+    std::vector<int64_t> iv_lo, iv_hi;
+    for (int64_t j = 0; j < g.nb[ax]; ++j) {
+        const int64_t z = g.off[ax] + j * g.S[ax];
+        const int64_t a = imax64(0, z - reach), b = imin64(NL, z + reach + 1);
+        if (!iv_hi.empty() && a <= iv_hi.back()) {
+            iv_hi.back() = imax64(iv_hi.back(), b);
+        } else {
+            iv_lo.push_back(a);
+            iv_hi.push_back(b);
+        }
+    }
+    const int niv = (int)iv_lo.size();
+    for (int i = 0; i < niv; ++i)
+        if ((rc = put(iv_lo[i], iv_hi[i]))) return rc;
+    if ((rc = ready())) return rc;
+    if ((rc = launch_seed(c, w.img_dev, st))) return rc;
+    if ((rc = build_bins(c, st))) return rc;
+    // 2. the first iteration slab by slab, each behind the rest of its planes
+    int iv = 0;
+    for (int64_t lo = 0; lo < NL; lo += kHostSlab) {
+        const int64_t hi = imin64(NL, lo + kHostSlab);
+        int64_t p = lo;
+        for (; iv < niv && iv_lo[iv] < hi; ++iv) {
+            if (iv_hi[iv] <= p) continue;
+            if (iv_lo[iv] > p && (rc = put(p, iv_lo[iv]))) return rc;
+            p = imax64(p, iv_hi[iv]);
+            if (iv_hi[iv] > hi) break;  // the interval runs into the next slab
+        }
+        if (p < hi && (rc = put(p, hi))) return rc;
+        if ((rc = ready())) return rc;
+        const Slab sl{lo, hi};
+        if ((rc = launch_assign_update(c, w.img_dev, w.lab_dev, st, &sl))) return rc;
+    }
+    return launch_finalize(c, st);
+}
+
+}  // namespace sslic
+
+extern "C" {
+
 int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host, float* centres_host, void* stream,
                    sslic_result* out)
 {
@@ -499,11 +604,18 @@ int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host, f
         if ((rc = dalloc(c, &w.cen_dev, (size_t)g.K * (g.C + g.n), "centres"))) return rc;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = cuda_check(c, cudaMemcpyAsync(w.img_dev, image_host, img_bytes, cudaMemcpyHostToDevice, st), "H2D")))
-        return rc;
-    if ((rc = launch_seed(c, w.img_dev, st))) return rc;
+    int first = 0;
+    if (host_pipeline_applies(c)) {
+        if ((rc = host_upload_first_iteration(c, image_host, st))) return rc;
+        first = 1;
+    } else {
+        if ((rc = cuda_check(c, cudaMemcpyAsync(w.img_dev, image_host, img_bytes, cudaMemcpyHostToDevice, st),
+                             "H2D")))
+            return rc;
+        if ((rc = launch_seed(c, w.img_dev, st))) return rc;
+    }
     sslic_result r;
-    if ((rc = run_loop(c, w.img_dev, w.lab_dev, centres_host ? w.cen_dev : nullptr, st, &r))) return rc;
+    if ((rc = run_loop(c, w.img_dev, w.lab_dev, centres_host ? w.cen_dev : nullptr, st, &r, first))) return rc;
     if ((rc = cuda_check(c, cudaMemcpyAsync(labels_host, w.lab_dev, lab_bytes, cudaMemcpyDeviceToHost, st), "D2H")))
         return rc;
     if (centres_host &&

@@ -393,8 +393,15 @@ SSLIC_API int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, 
 /* Queue one request.  image_host (read), labels_host (V int32, written) and
  * centres_host (K x (C+n) float32, written, may be NULL) must stay valid
  * until sslic_server_wait returns for the ticket; page-locked buffers let the
- * copies overlap the computation.  SSLIC_ENOMEM if the request alone exceeds
- * the budget; SSLIC_EUNSUPPORTED for connectivity. */
+ * copies overlap the computation.  A request with enforce_connectivity
+ * leaves the batched rounds after its last iteration: a finisher thread of
+ * the server runs connectivity enforcement (Sec. 3.1 stage 3) on it on a
+ * stream of its own, one request at a time, while the rounds of the others
+ * go on, and then copies its results back.  Its workspace (2 bytes per voxel
+ * plus about 45 bytes per local component of the largest such request so
+ * far) is allocated by the server on first use, outside the budget.
+ * SSLIC_ENOMEM if the request alone exceeds the budget; SSLIC_EUNSUPPORTED
+ * for images of more than three axes. */
 SSLIC_API int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* image_host,
                                   int32_t* labels_host, float* centres_host, int64_t* ticket);
 

@@ -137,6 +137,7 @@ int ensure_ccl_capacity(sslic_ctx* c, int64_t m)
     int rc;
     if (!w.lid) {
         if ((rc = dalloc(c, &w.lid, (size_t)g.V, "component ids"))) return rc;
+        w.lid_cap = g.V;
         w.n_ccl_tiles = ccl_num_tiles(g);
         if ((rc = dalloc(c, &w.tile_base, (size_t)w.n_ccl_tiles, "tile bases"))) return rc;
         if ((rc = dalloc(c, &w.tile_cnt, (size_t)w.n_ccl_tiles, "tile counts"))) return rc;
@@ -234,6 +235,45 @@ static void free_all(sslic_ctx* c)
         if (w.slab_ev[i]) { cudaEventDestroy(w.slab_ev[i]); w.slab_ev[i] = nullptr; }
     if (w.copy_stream) { cudaStreamDestroy(w.copy_stream); w.copy_stream = nullptr; }
     if (w.down_stream) { cudaStreamDestroy(w.down_stream); w.down_stream = nullptr; }
+}
+
+sslic_ctx* conn_ctx_create(int device, int sms)
+{
+    sslic_ctx* c = new (std::nothrow) sslic_ctx();
+    if (!c) return nullptr;
+    c->device = device;
+    c->sms = sms;
+    c->loop_graph = 0;
+    return c;
+}
+
+int conn_ctx_run(sslic_ctx* c, const sslic_params& p, const Geom& g, const float* ctr, int32_t* labels,
+                 cudaStream_t st, int64_t* num_labels)
+{
+    Workspace& w = c->ws;
+    c->p = p;
+    c->g = g;
+    // the per-voxel ids and per-tile arrays follow the largest image so far
+    if (w.lid && (g.V > w.lid_cap || ccl_num_tiles(g) > w.n_ccl_tiles)) {
+        dfree(w.lid); dfree(w.tile_base); dfree(w.tile_cnt); dfree(w.counters);
+        w.lid_cap = 0;
+        w.n_ccl_tiles = 0;
+    }
+    int rc = ensure_ccl_capacity(c, 32 * g.K + g.V / 1024 + 4096);
+    if (rc) return rc;
+    w.ctr = const_cast<float*>(ctr);  // read by phase 1 only; borrowed for the call
+    rc = run_connectivity(c, labels, labels, st, num_labels);
+    w.ctr = nullptr;
+    return rc;
+}
+
+void conn_ctx_destroy(sslic_ctx* c)
+{
+    if (!c) return;
+    c->ws.ctr = nullptr;
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    free_all(c);
+    delete c;
 }
 
 static int alloc_core(sslic_ctx* c)

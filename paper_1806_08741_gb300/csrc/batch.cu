@@ -298,7 +298,8 @@ private:
 };
 
 // ---- requests on the host side ------------------------------------------------
-enum SlotState { kQueued = 0, kUploading = 1, kActive = 2, kFinishing = 3, kDone = 4, kFailed = 5 };
+// kConnecting: iterations done, connectivity enforcement pending or running on the finisher thread
+enum SlotState { kQueued = 0, kUploading = 1, kActive = 2, kFinishing = 3, kDone = 4, kFailed = 5, kConnecting = 6 };
 
 struct Slot {
     int64_t ticket = 0;
@@ -319,6 +320,7 @@ struct Slot {
     int state = kQueued;
     int status = SSLIC_OK;
     cudaEvent_t ev_up = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_iter = nullptr;  // its last iteration has run (connectivity starts after it)
     double t_submit = 0, t_done = 0;
 };
 
@@ -428,6 +430,18 @@ struct sslic_server {
     int error = SSLIC_OK;
     char err[256] = {0};
     std::thread worker;
+    // connectivity enforcement (Sec. 3.1 stage 3) of the requests that ask
+    // for it: a finisher thread takes them off the rounds once their
+    // iterations are done and runs it on its own stream with one context
+    // whose workspace follows the largest request so far, while the rounds of
+    // the others go on; cap_mu keeps its allocations out of a round's capture
+    std::thread finisher;
+    std::deque<Slot*> conn_q;
+    std::condition_variable cv_conn;
+    bool conn_stop = false;
+    cudaStream_t fs = nullptr;
+    sslic_ctx* conn = nullptr;
+    std::mutex cap_mu;
     // statistics
     int64_t submitted = 0, completed = 0, rejected = 0, rounds = 0;
     int max_seen = 0;
@@ -701,10 +715,12 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
         if (s->graphs.size() >= 64) drop_graphs(s);
         cudaGraph_t gr = nullptr;
         cudaGraphExec_t ex = nullptr;
+        std::unique_lock<std::mutex> cap(s->cap_mu);
         if ((e = cudaStreamBeginCapture(s->cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return server_fail(s, SSLIC_ECUDA, "begin capture", e);
         const cudaError_t ei = issue_round(s, par, seed_mask, Rf > 0, !thr.empty(), keys);
         e = cudaStreamEndCapture(s->cs, &gr);
+        cap.unlock();
         if (ei != cudaSuccess || e != cudaSuccess) {
             if (gr) cudaGraphDestroy(gr);
             return server_fail(s, SSLIC_ECUDA, "capture", ei != cudaSuccess ? ei : e);
@@ -724,8 +740,16 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
         s->thr_prev = thr;
         s->thr_prev_par = par;
     }
+    std::vector<Slot*> conn;
     for (Slot* q : fin) {
         const Geom& g = q->g;
+        if (q->p.enforce_connectivity) {
+            // labels and centres go back after connectivity (finisher thread)
+            if ((e = cudaEventRecord(q->ev_iter, s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "event", e);
+            q->state = kConnecting;
+            conn.push_back(q);
+            continue;
+        }
         if ((e = cudaMemcpyAsync(q->h_lab, q->d.a.labels, (size_t)g.V * 4, cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
             return server_fail(s, SSLIC_ECUDA, "labels to host", e);
         if (q->h_cen &&
@@ -736,7 +760,12 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
     }
     for (Slot* q : all) {
         q->iter += 1;
-        if (q->state != kFinishing) q->state = kActive;
+        if (q->state != kFinishing && q->state != kConnecting) q->state = kActive;
+    }
+    if (!conn.empty()) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (Slot* q : conn) s->conn_q.push_back(q);
+        s->cv_conn.notify_all();
     }
     if ((e = cudaEventRecord(s->round_ev[par], s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "event", e);
     s->round_pending[par] = true;
@@ -809,8 +838,9 @@ void worker_main(sslic_server* s)
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
                 continue;
             }
-            const bool finishing = std::any_of(s->live.begin(), s->live.end(),
-                                               [](Slot* q) { return q->state == kFinishing; });
+            const bool finishing = std::any_of(s->live.begin(), s->live.end(), [](Slot* q) {
+                return q->state == kFinishing || q->state == kConnecting;
+            });
             if (join.empty() && act.empty()) {
                 if (s->stop && s->pending.empty() && s->live.empty()) return;
                 if (!finishing) s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
@@ -822,6 +852,64 @@ void worker_main(sslic_server* s)
             }
         }
         run_round(s, join, act);
+    }
+}
+
+// connectivity of the requests that finished their iterations, one at a time,
+// then their labels and centres to the host; the worker reaps them as usual
+void finisher_main(sslic_server* s)
+{
+    cudaSetDevice(s->device);
+    for (;;) {
+        Slot* q = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_conn.wait(lk, [&] { return s->conn_stop || !s->conn_q.empty(); });
+            if (s->conn_q.empty()) return;
+            q = s->conn_q.front();
+            s->conn_q.pop_front();
+            if (s->error != SSLIC_OK) {
+                q->state = kFailed;
+                q->status = s->error;
+                s->cv_done.notify_all();
+                continue;
+            }
+        }
+        const Geom& g = q->g;
+        int rc = SSLIC_OK;
+        const char* what = "connectivity";
+        cudaError_t e = cudaStreamWaitEvent(s->fs, q->ev_iter, 0);
+        if (e != cudaSuccess) rc = SSLIC_ECUDA;
+        if (rc == SSLIC_OK) {
+            std::lock_guard<std::mutex> cl(s->cap_mu);
+            if (!s->conn) s->conn = conn_ctx_create(s->device, s->sms);
+            if (!s->conn) rc = SSLIC_ENOMEM;
+            else {
+                int64_t nl = 0;
+                rc = conn_ctx_run(s->conn, q->p, g, q->d.a.ctr, q->d.a.labels, s->fs, &nl);
+                if (rc != SSLIC_OK) what = s->conn->err;
+            }
+        }
+        if (rc == SSLIC_OK) {
+            e = cudaMemcpyAsync(q->h_lab, q->d.a.labels, (size_t)g.V * 4, cudaMemcpyDeviceToHost, s->fs);
+            if (e == cudaSuccess && q->h_cen)
+                e = cudaMemcpyAsync(q->h_cen, q->d.cen_out, (size_t)g.K * (g.C + g.n) * 4, cudaMemcpyDeviceToHost, s->fs);
+            if (e == cudaSuccess) e = cudaEventRecord(q->ev_done, s->fs);
+            if (e != cudaSuccess) {
+                rc = SSLIC_ECUDA;
+                what = "connectivity results to host";
+            }
+        }
+        if (rc != SSLIC_OK) server_fail(s, rc, what, e);
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (rc == SSLIC_OK) {
+            q->state = kFinishing;
+        } else {
+            q->state = kFailed;
+            q->status = rc;
+            s->cv_done.notify_all();
+        }
+        s->cv_work.notify_all();
     }
 }
 
@@ -841,6 +929,7 @@ int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, sslic_serv
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->fs, cudaStreamNonBlocking);
     s->lay.init(max_active);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMalloc(&s->tab_dev[i], s->lay.end);
@@ -856,6 +945,7 @@ int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, sslic_serv
         return rc;
     }
     s->worker = std::thread(worker_main, s);
+    s->finisher = std::thread(finisher_main, s);
     *out = s;
     return SSLIC_OK;
 }
@@ -867,7 +957,6 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     Geom g;
     int rc = make_geom(p, &g);
     if (rc) return rc;
-    if (p->enforce_connectivity) return SSLIC_EUNSUPPORTED;
     if (g.n > 3) return SSLIC_EUNSUPPORTED;  // the batched tables are laid out for up to three axes
     if (g.K + 1 > (int64_t)kBScanItems * kBScanItems) return SSLIC_EUNSUPPORTED;
     Slot* q = new (std::nothrow) Slot();
@@ -891,17 +980,25 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     q->h_lab = labels_host;
     q->h_cen = centres_host;
     if (cudaEventCreateWithFlags(&q->ev_up, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&q->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&q->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&q->ev_iter, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (q->ev_up) cudaEventDestroy(q->ev_up);
+        if (q->ev_done) cudaEventDestroy(q->ev_done);
         delete q;
         return SSLIC_ECUDA;
     }
     std::lock_guard<std::mutex> lk(s->mu);
-    if (s->error != SSLIC_OK) { cudaEventDestroy(q->ev_up); cudaEventDestroy(q->ev_done); delete q; return s->error; }
+    if (s->error != SSLIC_OK) {
+        cudaEventDestroy(q->ev_up); cudaEventDestroy(q->ev_done); cudaEventDestroy(q->ev_iter);
+        delete q;
+        return s->error;
+    }
     if (q->bytes > s->arena.size()) {
         s->rejected += 1;
         cudaEventDestroy(q->ev_up);
         cudaEventDestroy(q->ev_done);
+        cudaEventDestroy(q->ev_iter);
         delete q;
         return SSLIC_ENOMEM;  // larger than the whole budget: never admissible
     }
@@ -930,6 +1027,7 @@ int sslic_server_wait(sslic_server* s, int64_t ticket, int32_t timeout_ms, doubl
     s->tickets.erase(it);
     cudaEventDestroy(q->ev_up);
     cudaEventDestroy(q->ev_done);
+    cudaEventDestroy(q->ev_iter);
     delete q;
     return st;
 }
@@ -972,11 +1070,21 @@ void sslic_server_destroy(sslic_server* s)
         s->cv_work.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->conn_stop = true;
+        s->cv_conn.notify_all();
+    }
+    if (s->finisher.joinable()) s->finisher.join();
+    if (s->fs) cudaStreamSynchronize(s->fs);
+    conn_ctx_destroy(s->conn);
+    s->conn = nullptr;
     if (s->cs) cudaStreamSynchronize(s->cs);
     if (s->up) cudaStreamSynchronize(s->up);
     for (auto& kv : s->tickets) {
         cudaEventDestroy(kv.second->ev_up);
         cudaEventDestroy(kv.second->ev_done);
+        cudaEventDestroy(kv.second->ev_iter);
         delete kv.second;
     }
     for (int i = 0; i < 2; ++i) {
@@ -990,6 +1098,7 @@ void sslic_server_destroy(sslic_server* s)
     if (s->ovf_cnt) cudaFree(s->ovf_cnt);
     if (s->cs) cudaStreamDestroy(s->cs);
     if (s->up) cudaStreamDestroy(s->up);
+    if (s->fs) cudaStreamDestroy(s->fs);
     delete s;
 }
 

@@ -148,6 +148,7 @@ struct Workspace {
     int* tile_lists = nullptr;          // n_assign_tiles records of tile_list_stride() ints (tile kernel images)
     // connectivity
     uint16_t* lid = nullptr;            // V
+    int64_t lid_cap = 0;                // voxels lid holds
     int64_t n_ccl_tiles = 0;
     int* tile_base = nullptr;           // n_ccl_tiles: first component record of each tile
     int* tile_cnt = nullptr;            // n_ccl_tiles: component records of each tile
@@ -229,6 +230,14 @@ int launch_export_centres(sslic_ctx* c, float* out, cudaStream_t st);
 int launch_import_centres(sslic_ctx* c, const float* in, cudaStream_t st);
 int run_connectivity(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,
                      int64_t* num_labels);
+// Connectivity for the batched server: one context that owns only the
+// connectivity workspace, retargeted to each request's geometry (its
+// buffers only grow) and given the request's centres (internal layout,
+// K x CW) for the call; labels are relabelled in place on st.
+sslic_ctx* conn_ctx_create(int device, int sms);
+int conn_ctx_run(sslic_ctx* c, const sslic_params& p, const Geom& g, const float* ctr, int32_t* labels,
+                 cudaStream_t st, int64_t* num_labels);
+void conn_ctx_destroy(sslic_ctx* c);
 int scan_exclusive_u32(sslic_ctx* c, const unsigned* in, unsigned* out, int64_t n, cudaStream_t st);
 size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);

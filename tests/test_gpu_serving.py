@@ -140,9 +140,60 @@ def test_server_rejects():
         with pytest.raises(S.SSLICError) as e:
             srv.submit(S.params_for(img, (16, 16)), img, lab)   # larger than the whole budget
         assert e.value.code == -2
-        with pytest.raises(S.SSLICError) as e:
-            srv.submit(S.params_for(img, (16, 16), enforce_connectivity=True), img, lab)
+        img4 = np.zeros((6, 6, 6, 6, 1), np.uint8)
+        with pytest.raises(S.SSLICError) as e:   # the batched tables hold up to three axes
+            srv.submit(S.params_for(img4, (3, 3, 3, 3)), img4, np.empty(img4.shape[:-1], np.int32))
         assert e.value.code == -6
+
+
+def test_served_requests_with_connectivity_equal_alone():
+    """Requests that enforce connectivity (Sec. 3.1 stage 3) leave the
+    rounds when their iterations are done; a finisher thread relabels them
+    while the rounds of the others go on.  Each result equals the request run
+    alone through sslic_run bit for bit, whatever it shares the server with:
+    2-D colour and 3-D grey images, with and without connectivity, sizes that
+    rise and fall so that the connectivity workspace grows and is reused."""
+    import torch
+    from paper_1806_08741_gb300 import sslic as S
+    rng = np.random.default_rng(11)
+    reqs = []
+    for i, (w, h) in enumerate([(80, 60), (300, 220), (120, 90), (420, 330), (64, 64), (256, 300)]):
+        img = I.make_image(I.ImageSpec((w, h), 3, "u8", 400 + i, max(2, w * h // 2500), 6))
+        reqs.append((img, (16, 16) if i % 2 else (8, 8), float(rng.choice([5.0, 10.0, 20.0])), i % 3 != 2))
+    for i, side in enumerate([40, 72, 56]):
+        img = I.make_image(I.ImageSpec((side, side + 5, side - 3), 1, "u16", 500 + i, 20, 300))
+        reqs.append((img, (8, 8, 8), 10.0, True))
+    iters = 5
+    outs = []
+    with S.Server(1 << 30, max_active=6) as srv:
+        tickets = []
+        for img, grid, m, conn in reqs:
+            p = S.params_for(img, grid, m=m, max_iter=iters, enforce_connectivity=conn)
+            lab = np.empty(img.shape[:-1], np.int32)
+            K = 1
+            for n, g in zip(p.size, p.grid):
+                K *= -(-n // g)
+            cen = np.empty((K, p.channels + p.ndim), np.float32)
+            tickets.append(srv.submit(p, img, lab, cen))
+            outs.append((lab, cen))
+        for t in tickets:
+            srv.wait(t)
+        st = srv.stats()
+    assert st["status"] == 0 and st["completed"] == len(reqs)
+    for (img, grid, m, conn), (lab, cen) in zip(reqs, outs):
+        p = S.params_for(img, grid, m=m, max_iter=iters, enforce_connectivity=conn)
+        with S.Context(p) as ctx:
+            rl = torch.empty(img.shape[:-1], dtype=torch.int32, device="cuda")
+            rc = torch.empty((ctx.K, ctx.centre_width), dtype=torch.float32, device="cuda")
+            info = ctx.run(torch.from_numpy(img).cuda(), rl, rc)
+        np.testing.assert_array_equal(lab, rl.cpu().numpy())
+        np.testing.assert_array_equal(cen, rc.cpu().numpy())
+        if conn:
+            assert lab.min() >= 0 and lab.max() < info["num_labels"]
+    # the first request against the oracle's whole run, connectivity included
+    img, grid, m, conn = reqs[0]
+    ref = O.slic(O.params_for(img, grid, m=m, max_iter=iters, enforce_connectivity=conn), img)
+    np.testing.assert_array_equal(outs[0][0], ref["labels"])
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 5, 9, 11])

@@ -434,6 +434,10 @@ def run_ours(args, w):
             # a rate both forms keep up with
             "under_capacity": serving_bench(n_req=args.serve_requests_low, rate=args.serve_rate_low,
                                             max_active=args.serve_max_active, pool=pool),
+            # the same rate with connectivity enforced on every request
+            "under_capacity_connectivity": serving_bench(n_req=args.serve_requests_conn, rate=args.serve_rate_low,
+                                                         max_active=args.serve_max_active, pool=pool,
+                                                         connectivity=True),
         }
 
     cpu = None
@@ -705,12 +709,14 @@ def serving_pool(seed=1810, pool_n=12):
     return pool, host
 
 
-def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=16, pool=None):
+def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, max_active=16, pool=None,
+                  connectivity=False):
     """Poisson arrivals (rate per second) of requests over the images of
     serving_pool (2-D RGB uint8 and 3-D uint16), S in {8, 16, 32}, m in
-    {5, 10, 20}, 10 iterations.  Returns latency percentiles and throughput
-    of the served form (sslic_server_*) and of the plain form (one
-    sslic_run_host call per request, in arrival order)."""
+    {5, 10, 20}, 10 iterations, connectivity enforced on every request when
+    `connectivity` is set.  Returns latency percentiles and throughput of the
+    served form (sslic_server_*) and of the plain form (one sslic_run_host
+    call per request, in arrival order)."""
     import threading
 
     import numpy as np
@@ -733,7 +739,8 @@ def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, m
     def params(idx, grid, m):
         spec = pool[idx]
         return S.Params(size=spec.size, grid=(grid,) * spec.ndim, channels=spec.channels,
-                        dtype=S.U8 if spec.dtype == "u8" else S.U16, m=m, max_iter=10)
+                        dtype=S.U8 if spec.dtype == "u8" else S.U16, m=m, max_iter=10,
+                        enforce_connectivity=connectivity)
 
     # page-locked output buffers, made before the timed region and recycled
     lock = threading.Lock()
@@ -802,7 +809,7 @@ def serving_bench(n_req=200, rate=200.0, seed=1810, budget_gb=48.0, pool_n=12, m
     wall = time.perf_counter() - t0
     res["plain"] = {"p50_ms": float(np.percentile(lats, 50)), "p99_ms": float(np.percentile(lats, 99)),
                     "mean_ms": float(np.mean(lats)), "throughput": vox_iters / wall / 1e9, "wall_s": wall}
-    res["stream"] = {"requests": n_req, "rate_per_s": rate, "iterations": 10,
+    res["stream"] = {"requests": n_req, "rate_per_s": rate, "iterations": 10, "connectivity": connectivity,
                      "mix": "1/2 2-D RGB u8 side U[256,4096], 1/2 3-D u16 side U[128,512]; S in {8,16,32}; m in {5,10,20}",
                      "inputs": f"{2 * pool_n} pool images", "offered_gvox_iter_s": vox_iters / reqs[-1][0] / 1e9,
                      "unit": UNIT}
@@ -838,6 +845,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the overloaded stream")
     ap.add_argument("--serve-requests-low", type=int, default=1000, help="requests of the under-capacity stream")
     ap.add_argument("--serve-rate-low", type=float, default=60.0, help="arrivals per second, under capacity")
+    ap.add_argument("--serve-requests-conn", type=int, default=500,
+                    help="requests of the under-capacity stream with connectivity enforced")
     ap.add_argument("--serve-max-active", type=int, default=16, help="requests the server advances at once")
     args = ap.parse_args()
     if args.lab_only:
@@ -863,7 +872,10 @@ def main():
         out = {"overloaded": serving_bench(n_req=args.serve_requests, rate=200.0, max_active=args.serve_max_active,
                                            pool=pool),
                "under_capacity": serving_bench(n_req=args.serve_requests_low, rate=args.serve_rate_low,
-                                               max_active=args.serve_max_active, pool=pool)}
+                                               max_active=args.serve_max_active, pool=pool),
+               "under_capacity_connectivity": serving_bench(n_req=args.serve_requests_conn, rate=args.serve_rate_low,
+                                                            max_active=args.serve_max_active, pool=pool,
+                                                            connectivity=True)}
         print(json.dumps({"serving": out}), flush=True)
         return 0
     from paper_1806_08741_gb300 import inputs

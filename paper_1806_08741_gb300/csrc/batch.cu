@@ -402,6 +402,7 @@ struct sslic_server {
     int max_active = 64;
     Arena arena;
     cudaStream_t cs = nullptr, up = nullptr;  // compute, upload
+    cudaStream_t ds = nullptr;                // results to the host, off the rounds' stream
     // device + pinned staging of the round tables, double buffered
     TabLayout lay;
     unsigned char* tab_dev[2] = {nullptr, nullptr};
@@ -750,12 +751,16 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
             conn.push_back(q);
             continue;
         }
-        if ((e = cudaMemcpyAsync(q->h_lab, q->d.a.labels, (size_t)g.V * 4, cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
+        // the copies run on their own stream, so the next rounds need not wait for them
+        if ((e = cudaEventRecord(q->ev_iter, s->cs)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s->ds, q->ev_iter, 0)) != cudaSuccess)
+            return server_fail(s, SSLIC_ECUDA, "event", e);
+        if ((e = cudaMemcpyAsync(q->h_lab, q->d.a.labels, (size_t)g.V * 4, cudaMemcpyDeviceToHost, s->ds)) != cudaSuccess)
             return server_fail(s, SSLIC_ECUDA, "labels to host", e);
         if (q->h_cen &&
-            (e = cudaMemcpyAsync(q->h_cen, q->d.cen_out, (size_t)g.K * (g.C + g.n) * 4, cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
+            (e = cudaMemcpyAsync(q->h_cen, q->d.cen_out, (size_t)g.K * (g.C + g.n) * 4, cudaMemcpyDeviceToHost, s->ds)) != cudaSuccess)
             return server_fail(s, SSLIC_ECUDA, "centres to host", e);
-        if ((e = cudaEventRecord(q->ev_done, s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "event", e);
+        if ((e = cudaEventRecord(q->ev_done, s->ds)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "event", e);
         q->state = kFinishing;
     }
     for (Slot* q : all) {
@@ -930,6 +935,7 @@ int sslic_server_create(int64_t hbm_budget_bytes, int32_t max_active, sslic_serv
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->fs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->ds, cudaStreamNonBlocking);
     s->lay.init(max_active);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMalloc(&s->tab_dev[i], s->lay.end);
@@ -1077,6 +1083,7 @@ void sslic_server_destroy(sslic_server* s)
     }
     if (s->finisher.joinable()) s->finisher.join();
     if (s->fs) cudaStreamSynchronize(s->fs);
+    if (s->ds) cudaStreamSynchronize(s->ds);
     conn_ctx_destroy(s->conn);
     s->conn = nullptr;
     if (s->cs) cudaStreamSynchronize(s->cs);
@@ -1099,6 +1106,7 @@ void sslic_server_destroy(sslic_server* s)
     if (s->cs) cudaStreamDestroy(s->cs);
     if (s->up) cudaStreamDestroy(s->up);
     if (s->fs) cudaStreamDestroy(s->fs);
+    if (s->ds) cudaStreamDestroy(s->ds);
     delete s;
 }
 

@@ -372,7 +372,7 @@ static int capture_iteration(sslic_ctx* c, const void* image, int32_t* labels, i
         return rc;
     rc = build_bins(c, c->cap_stream);
     if (!rc) rc = launch_assign_update(c, image, labels, c->cap_stream);
-    if (!rc) rc = launch_finalize(c, c->cap_stream);
+    if (!rc) rc = launch_finalize(c, c->cap_stream, false);  // the residual follows the last replay
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
     *per_iter = c->launches - l0;
@@ -417,11 +417,13 @@ static int run_loop(sslic_ctx* c, const void* image, int32_t* labels, float* cen
                 if ((rc = cuda_check(c, cudaGraphLaunch(c->loop_exec, st), "graph launch"))) return rc;
                 count_launch(c, (int)per_iter);
             }
+            if ((rc = launch_residual(c, st))) return rc;
             break;
         }
         if ((rc = build_bins(c, st))) return rc;
         if ((rc = launch_assign_update(c, image, labels, st))) return rc;
-        if ((rc = launch_finalize(c, st))) return rc;
+        // without a threshold only the last iteration's residual is reported
+        if ((rc = launch_finalize(c, st, c->p.conv_threshold > 0.0 || it == c->p.max_iter - 1))) return rc;
         if (c->p.conv_threshold > 0.0) {
             if ((rc = read_residual(c, st, &res))) return rc;
             if (res < c->p.conv_threshold) { ++it; break; }
@@ -618,7 +620,7 @@ static int host_upload_first_iteration(sslic_ctx* c, const void* image_host, cud
         const Slab sl{lo, hi};
         if ((rc = launch_assign_update(c, w.img_dev, w.lab_dev, st, &sl))) return rc;
     }
-    return launch_finalize(c, st);
+    return launch_finalize(c, st, c->p.conv_threshold > 0.0 || c->p.max_iter == 1);
 }
 
 }  // namespace sslic
@@ -777,7 +779,7 @@ int sslic_run_streamed(sslic_ctx* c, const void* image_host, int32_t* labels_hos
                 if ((rc = cuda_check(c, cudaEventRecord(lab_free[i], ds), "event"))) return rc;
             }
         }
-        if ((rc = launch_finalize(c, st))) return rc;
+        if ((rc = launch_finalize(c, st, thr || it == c->p.max_iter - 1))) return rc;
         if (thr) {
             if ((rc = read_residual(c, st, &res))) return rc;
             if (res < c->p.conv_threshold) { ++it; break; }

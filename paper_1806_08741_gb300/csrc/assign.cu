@@ -160,7 +160,21 @@ __global__ void resid_final_kernel(const double* __restrict__ part, const unsign
     if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = resid_combine(part, cpart);
 }
 
-int launch_finalize(sslic_ctx* c, cudaStream_t st)
+// the residual of the last update: the per-cluster terms reduced in a fixed order
+static int residual_kernels(sslic_ctx* c, cudaStream_t st)
+{
+    const Geom& g = c->g;
+    Workspace& w = c->ws;
+    resid_partial_kernel<<<kResidParts, kRedThreads, 0, st>>>(w.resid_k, w.nonempty_k, g.K, w.resid_part,
+                                                              w.resid_cnt_part);
+    int rc = cuda_check(c, cudaGetLastError(), "resid_partial_kernel");
+    if (rc) return rc;
+    resid_final_kernel<<<1, 32, 0, st>>>(w.resid_part, w.resid_cnt_part, w.resid_out);
+    count_launch(c, 2);
+    return cuda_check(c, cudaGetLastError(), "resid_final_kernel");
+}
+
+int launch_finalize(sslic_ctx* c, cudaStream_t st, bool residual)
 {
     const Geom& g = c->g;
     Workspace& w = c->ws;
@@ -168,15 +182,20 @@ int launch_finalize(sslic_ctx* c, cudaStream_t st)
     int64_t blocks = (g.K + threads - 1) / threads;
     const int pr = prof_begin(c, SSLIC_PHASE_FINALIZE, st);
     finalize_kernel<<<blocks, threads, 0, st>>>(g, w.ctr, w.acc, w.facc, w.resid_k, w.nonempty_k);
-    count_launch(c, 3);
+    count_launch(c);
     int rc = cuda_check(c, cudaGetLastError(), "finalize_kernel");
     if (rc) return rc;
-    resid_partial_kernel<<<kResidParts, kRedThreads, 0, st>>>(w.resid_k, w.nonempty_k, g.K, w.resid_part,
-                                                              w.resid_cnt_part);
-    if ((rc = cuda_check(c, cudaGetLastError(), "resid_partial_kernel"))) return rc;
-    resid_final_kernel<<<1, 32, 0, st>>>(w.resid_part, w.resid_cnt_part, w.resid_out);
+    if (residual && (rc = residual_kernels(c, st))) return rc;
     prof_end(c, pr, st);
-    return cuda_check(c, cudaGetLastError(), "resid_final_kernel");
+    return SSLIC_OK;
+}
+
+int launch_residual(sslic_ctx* c, cudaStream_t st)
+{
+    const int pr = prof_begin(c, SSLIC_PHASE_FINALIZE, st);
+    const int rc = residual_kernels(c, st);
+    prof_end(c, pr, st);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------

@@ -225,7 +225,10 @@ namespace sslic {
 int launch_seed(sslic_ctx* c, const void* img, cudaStream_t st, const Slab* slab = nullptr);
 int build_bins(sslic_ctx* c, cudaStream_t st);
 int launch_assign_update(sslic_ctx* c, const void* img, int32_t* labels, cudaStream_t st, const Slab* slab = nullptr);
-int launch_finalize(sslic_ctx* c, cudaStream_t st);
+// residual: also reduce the per-cluster residual terms into resid_out (a
+// run without a convergence threshold needs it only after its last iteration)
+int launch_finalize(sslic_ctx* c, cudaStream_t st, bool residual = true);
+int launch_residual(sslic_ctx* c, cudaStream_t st);
 int launch_export_centres(sslic_ctx* c, float* out, cudaStream_t st);
 int launch_import_centres(sslic_ctx* c, const float* in, cudaStream_t st);
 int run_connectivity(sslic_ctx* c, const int32_t* labels_in, int32_t* labels_out, cudaStream_t st,

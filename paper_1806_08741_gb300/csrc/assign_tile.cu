@@ -80,6 +80,17 @@ int launch_tile_lists(sslic_ctx* c, int ndim, int tx, int ty, int tz, int ntx, i
     return cuda_check(c, cudaGetLastError(), "tile_lists_kernel");
 }
 
+// the batched queue's records: one warp per (request, tile) of a group
+cudaError_t launch_tile_lists_queue(int ndim, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
+                                    unsigned* ovf_count, int grid, cudaStream_t st)
+{
+    if (ndim == 3)
+        tile::tile_lists_queue_kernel<3><<<grid, tile::kListWarps * 32, 0, st>>>(reqs, tpre, nR, ovf, ovf_count);
+    else
+        tile::tile_lists_queue_kernel<2><<<grid, tile::kListWarps * 32, 0, st>>>(reqs, tpre, nR, ovf, ovf_count);
+    return cudaGetLastError();
+}
+
 // the most tiles any shape cuts the image into (sizes the crowded-tile list)
 int64_t assign_num_tiles(const Geom& g)
 {

@@ -222,10 +222,102 @@ __device__ __forceinline__ void flush_run(unsigned* pk, int cur, const FeatAcc<T
 // A tile with more than kStage gathered or kCap kept centres gets count -1
 // and goes to the crowded-tile list here.  The tile kernel then starts from
 // one coalesced load of the record instead of the chain of dependent loads,
-// shared atomics and barriers of the in-kernel gather (kept for the batched
-// queue, which has no lists).
+// shared atomics and barriers of the in-kernel gather (which a tile kernel
+// given no records still runs).  The batched queue has its own form below:
+// one warp per (request, tile) of a group, each request's records in its
+// arena block.
 constexpr int kListStride = kCap + 1;
 constexpr int kListWarps = 8;
+
+// one tile's record (the warp's work; stage / kept are the warp's scratch)
+template <int NDIM>
+__device__ __forceinline__ void list_one_tile(const Geom& g, const float* __restrict__ ctr,
+                                              const unsigned* __restrict__ bin_start,
+                                              const int* __restrict__ bin_items, int* __restrict__ lists, int64_t tile,
+                                              int ntx, int nty, int TX, int TY, int TZ, int64_t ovf_key,
+                                              int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count,
+                                              int* stage, int* kept, int lane)
+{
+    const int Tn[3] = {TX, TY, TZ};
+    const unsigned t32 = (unsigned)tile;  // tile counts stay below 2^31: 32-bit division
+    const unsigned txy = t32 / (unsigned)ntx;
+    const int T0[3] = {(int)(t32 - txy * (unsigned)ntx) * TX, (int)(txy % (unsigned)nty) * TY,
+                       (int)(txy / (unsigned)nty) * TZ};
+    int E[3], blo[3], nbd[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        E[d] = min(Tn[d], (int)g.N[d] - T0[d]);
+        blo[d] = max(0, T0[d] / g.S[d] - 1);
+        nbd[d] = min((int)g.nb[d] - 1, (T0[d] + E[d] - 1) / g.S[d] + 1) - blo[d] + 1;
+    }
+    // gather: bins 32 at a time, items placed by a prefix sum of the counts
+    const int nbins = nbd[0] * nbd[1] * nbd[2];
+    int total = 0;
+    for (int b0 = 0; b0 < nbins; b0 += 32) {
+        const int b = b0 + lane;
+        unsigned first = 0, cnt = 0;
+        if (b < nbins) {
+            const unsigned bq = (unsigned)b / (unsigned)nbd[0];
+            const int bx = blo[0] + (int)((unsigned)b - bq * (unsigned)nbd[0]),
+                      by = blo[1] + (int)(bq % (unsigned)nbd[1]), bz = blo[2] + (int)(bq / (unsigned)nbd[1]);
+            const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
+            first = bin_start[bin];
+            cnt = bin_start[bin + 1] - first;
+        }
+        unsigned inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const unsigned base = (unsigned)total + inc - cnt;
+        for (unsigned j = 0; j < cnt; ++j)
+            if (base + j < (unsigned)kStage) stage[base + j] = bin_items[first + j];
+        total += (int)__shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncwarp();
+    // filter: windows that meet the tile, compacted by ballot
+    int nc = 0;
+    if (total <= kStage) {
+        for (int i0 = 0; i0 < total; i0 += 32) {
+            const int i = i0 + lane;
+            bool hit = false;
+            int k = 0;
+            if (i < total) {
+                k = stage[i];
+                const float* pos = ctr + (int64_t)k * g.CW + g.C;
+                hit = true;
+#pragma unroll
+                for (int d = 0; d < NDIM; ++d) {
+                    const int lo = (int)ceilf(pos[d]) - g.S[d];
+                    hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            const int at = nc + __popc(m & ((1u << lane) - 1u));
+            if (hit && at < kCap) kept[at] = k;
+            nc += __popc(m);
+        }
+    }
+    __syncwarp();
+    int* rec = lists + tile * kListStride;
+    if (total > kStage || nc > kCap) {
+        for (int i = lane; i < kListStride; i += 32) rec[i] = -1;
+        if (lane == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = ovf_key;
+    } else {
+        // rank sort (the indices are distinct: a centre sits in one bin)
+        for (int i = lane; i < kCap; i += 32) {
+            int v = -1, r = i;
+            if (i < nc) {
+                v = kept[i];
+                r = 0;
+                for (int j = 0; j < nc; ++j) r += (kept[j] < v);
+            }
+            rec[1 + r] = v;
+        }
+        if (lane == 0) rec[0] = nc;
+    }
+}
 
 template <int NDIM>
 __global__ void __launch_bounds__(kListWarps * 32)
@@ -236,89 +328,38 @@ tile_lists_kernel(Geom g, const float* __restrict__ ctr, const unsigned* __restr
     __shared__ int stage_all[kListWarps][kStage];
     __shared__ int kept_all[kListWarps][kCap];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    int* const stage = stage_all[wp];
-    int* const kept = kept_all[wp];
-    const int Tn[3] = {TX, TY, TZ};
     for (int64_t tile = tile0 + (int64_t)blockIdx.x * kListWarps + wp; tile < tile0 + ntiles;
          tile += (int64_t)gridDim.x * kListWarps) {
-        const unsigned t32 = (unsigned)tile;  // tile counts stay below 2^31: 32-bit division
-        const unsigned txy = t32 / (unsigned)ntx;
-        const int T0[3] = {(int)(t32 - txy * (unsigned)ntx) * TX, (int)(txy % (unsigned)nty) * TY,
-                           (int)(txy / (unsigned)nty) * TZ};
-        int E[3], blo[3], nbd[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            E[d] = min(Tn[d], (int)g.N[d] - T0[d]);
-            blo[d] = max(0, T0[d] / g.S[d] - 1);
-            nbd[d] = min((int)g.nb[d] - 1, (T0[d] + E[d] - 1) / g.S[d] + 1) - blo[d] + 1;
-        }
-        // gather: bins 32 at a time, items placed by a prefix sum of the counts
-        const int nbins = nbd[0] * nbd[1] * nbd[2];
-        int total = 0;
-        for (int b0 = 0; b0 < nbins; b0 += 32) {
-            const int b = b0 + lane;
-            unsigned first = 0, cnt = 0;
-            if (b < nbins) {
-                const unsigned bq = (unsigned)b / (unsigned)nbd[0];
-                const int bx = blo[0] + (int)((unsigned)b - bq * (unsigned)nbd[0]),
-                          by = blo[1] + (int)(bq % (unsigned)nbd[1]), bz = blo[2] + (int)(bq / (unsigned)nbd[1]);
-                const int64_t bin = bx + g.nb[0] * (by + g.nb[1] * (int64_t)bz);
-                first = bin_start[bin];
-                cnt = bin_start[bin + 1] - first;
-            }
-            unsigned inc = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned v = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += v;
-            }
-            const unsigned base = (unsigned)total + inc - cnt;
-            for (unsigned j = 0; j < cnt; ++j)
-                if (base + j < (unsigned)kStage) stage[base + j] = bin_items[first + j];
-            total += (int)__shfl_sync(0xffffffffu, inc, 31);
-        }
+        list_one_tile<NDIM>(g, ctr, bin_start, bin_items, lists, tile, ntx, nty, TX, TY, TZ, tile, ovf_tiles, ovf_count,
+                            stage_all[wp], kept_all[wp], lane);
         __syncwarp();
-        // filter: windows that meet the tile, compacted by ballot
-        int nc = 0;
-        if (total <= kStage) {
-            for (int i0 = 0; i0 < total; i0 += 32) {
-                const int i = i0 + lane;
-                bool hit = false;
-                int k = 0;
-                if (i < total) {
-                    k = stage[i];
-                    const float* pos = ctr + (int64_t)k * g.CW + g.C;
-                    hit = true;
-#pragma unroll
-                    for (int d = 0; d < NDIM; ++d) {
-                        const int lo = (int)ceilf(pos[d]) - g.S[d];
-                        hit = hit && (lo <= T0[d] + E[d] - 1) && (lo + 2 * g.S[d] - 1 >= T0[d]);
-                    }
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, hit);
-                const int at = nc + __popc(m & ((1u << lane) - 1u));
-                if (hit && at < kCap) kept[at] = k;
-                nc += __popc(m);
-            }
+    }
+}
+
+// the same for the batched queue: one warp per (request, tile) work item of
+// the requests of one group (request r owns items [tpre[r], tpre[r + 1]));
+// crowded tiles go to the group's list as (r << 40 | tile)
+template <int NDIM>
+__global__ void __launch_bounds__(kListWarps * 32)
+tile_lists_queue_kernel(const TileArgs* __restrict__ reqs, const int64_t* __restrict__ tpre,
+                        const int* __restrict__ nR, int64_t* __restrict__ ovf_tiles, unsigned* __restrict__ ovf_count)
+{
+    __shared__ int stage_all[kListWarps][kStage];
+    __shared__ int kept_all[kListWarps][kCap];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int R = *nR;
+    const int64_t total = tpre[R];
+    for (int64_t i = (int64_t)blockIdx.x * kListWarps + wp; i < total; i += (int64_t)gridDim.x * kListWarps) {
+        int lo = 0, hi = R - 1;  // last r with tpre[r] <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tpre[mid] <= i) lo = mid;
+            else hi = mid - 1;
         }
-        __syncwarp();
-        int* rec = lists + tile * kListStride;
-        if (total > kStage || nc > kCap) {
-            for (int i = lane; i < kListStride; i += 32) rec[i] = -1;
-            if (lane == 0) ovf_tiles[atomicAdd(ovf_count, 1u)] = tile;
-        } else {
-            // rank sort (the indices are distinct: a centre sits in one bin)
-            for (int i = lane; i < kCap; i += 32) {
-                int v = -1, r = i;
-                if (i < nc) {
-                    v = kept[i];
-                    r = 0;
-                    for (int j = 0; j < nc; ++j) r += (kept[j] < v);
-                }
-                rec[1 + r] = v;
-            }
-            if (lane == 0) rec[0] = nc;
-        }
+        const TileArgs& a = reqs[lo];
+        const int64_t tile = i - tpre[lo];
+        list_one_tile<NDIM>(a.g, a.ctr, a.bin_start, a.bin_items, const_cast<int*>(a.lists), tile, a.ntx, a.nty, a.tx, a.ty, a.tz,
+                            ((int64_t)lo << 40) | tile, ovf_tiles, ovf_count, stage_all[wp], kept_all[wp], lane);
         __syncwarp();
     }
 }

@@ -502,6 +502,7 @@ void place(sslic_server* s, Slot* q)
     }
     a.bin_start = d.bin_start;
     a.bin_items = d.bin_items;
+    a.lists = q->shape >= 0 ? (int*)take((size_t)q->ntiles * tile_list_stride() * 4) : nullptr;
     a.ntx = q->ntx;
     a.nty = q->nty;
     a.tx = q->tx;
@@ -524,6 +525,10 @@ cudaError_t launch_group(sslic_server* s, int C, int n, int shape, const TileArg
         return cudaGetLastError();
     }
     if (ta && (e = cudaMemsetAsync(s->ovf_cnt + gi, 0, sizeof(unsigned), s->cs)) != cudaSuccess) return e;
+    // step 2 ahead of the queue for every tile of the group: the queue kernel
+    // then starts each tile from its record
+    if (ta && (e = launch_tile_lists_queue(n, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, s->sms * 32, s->cs)) != cudaSuccess)
+        return e;
     if constexpr (sizeof(T) == 1) {
         if (C == 3) e = n == 3 ? launch_tile_queue<uint8_t, 3, 3>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs)
                                : launch_tile_queue<uint8_t, 3, 2>(shape, ta, tp, nR, s->ovf[gi], s->ovf_cnt + gi, grid, s->cs);
@@ -981,7 +986,8 @@ int sslic_server_submit(sslic_server* s, const sslic_params* p, const void* imag
     q->group = group_key(g, q->shape);
     q->nchunks = (g.K + 1 + kBScanItems - 1) / kBScanItems;
     q->thr = p->conv_threshold > 0.0;
-    q->bytes = footprint(g) + (q->thr ? footprint_thr(g) : 0);
+    q->bytes = footprint(g) + (q->thr ? footprint_thr(g) : 0) +
+               (q->shape >= 0 ? a256((size_t)q->ntiles * tile_list_stride() * 4) : 0);
     q->h_img = image_host;
     q->h_lab = labels_host;
     q->h_cen = centres_host;

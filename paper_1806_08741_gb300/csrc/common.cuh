@@ -246,6 +246,11 @@ size_t scan_tmp_needed(int64_t n);
 int64_t ccl_num_tiles(const Geom& g);
 int64_t assign_num_tiles(const Geom& g);
 int tile_list_stride();  // ints per per-tile candidate record
+// the batched queue's per-tile records for the requests of one group (each
+// request's TileArgs::lists holds its tiles' records); crowded tiles go to ovf
+// as (request << 40 | tile)
+cudaError_t launch_tile_lists_queue(int ndim, const TileArgs* reqs, const int64_t* tpre, const int* nR, int64_t* ovf,
+                                    unsigned* ovf_count, int grid, cudaStream_t st);
 constexpr int kTileListStride = 49;  // a record: count, then up to 48 centre indices in ascending order
 // per-tile candidate records for tiles [tile0, tile0 + ntiles) of a tx x ty x tz
 // tiling (ntx x nty tiles per plane of tiles), into the workspace's list buffer

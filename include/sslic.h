@@ -383,7 +383,8 @@ typedef struct {
     double  busy_s;                          /* first admission to last completion, seconds */
     double  p50_ms, p99_ms, mean_ms;         /* latency: submission to result in host memory */
     int64_t graph_launches;                  /* rounds replayed from a captured CUDA graph */
-    int64_t graph_captures;                  /* distinct round forms captured */
+    int64_t graph_captures;                  /* round forms captured (a form is captured when it recurs) */
+    int64_t eager_rounds;                    /* rounds of a form met for the first time, launched directly */
 } sslic_server_stats;
 
 /* Start a server on the current device with a device-memory budget for

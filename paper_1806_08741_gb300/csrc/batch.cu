@@ -27,6 +27,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <set>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -415,7 +416,10 @@ struct sslic_server {
     int thr_prev_par = 0;
     // captured rounds, by (parity, joining dtypes, finishing, thresholds, groups)
     std::map<std::vector<int>, cudaGraphExec_t> graphs;
-    int64_t graph_captures = 0, graph_launches = 0;
+    // round forms met once: a form runs eagerly the first time and is
+    // captured when it comes back, so one-off forms never pay a capture
+    std::set<std::vector<int>> seen;
+    int64_t graph_captures = 0, graph_launches = 0, eager_rounds = 0;
     // crowded-tile lists, one per group slot in a round
     int64_t* ovf[kMaxGroups] = {};
     unsigned* ovf_cnt = nullptr;  // kMaxGroups counters
@@ -714,11 +718,22 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
     std::vector<int> sig{par, seed_mask, Rf > 0 ? 1 : 0, thr.empty() ? 0 : 1};
     sig.insert(sig.end(), keys.begin(), keys.end());
     auto it = s->graphs.find(sig);
+    bool eager = false;
     if (it == s->graphs.end()) {
         for (int gi = 0; gi < (int)keys.size(); ++gi)
             if ((e = group_launch(s, keys[gi], nullptr, nullptr, nullptr, gi)) != cudaSuccess)
                 return server_fail(s, SSLIC_ECUDA, "kernel attributes", e);
-        if (s->graphs.size() >= 64) drop_graphs(s);
+        if (s->seen.insert(sig).second) {
+            if (s->seen.size() > 4096) s->seen.clear();
+            eager = true;
+        }
+    }
+    if (eager) {
+        if ((e = issue_round(s, par, seed_mask, Rf > 0, !thr.empty(), keys)) != cudaSuccess)
+            return server_fail(s, SSLIC_ECUDA, "round", e);
+        s->eager_rounds += 1;
+    } else if (it == s->graphs.end()) {
+        if (s->graphs.size() >= 256) drop_graphs(s);
         cudaGraph_t gr = nullptr;
         cudaGraphExec_t ex = nullptr;
         std::unique_lock<std::mutex> cap(s->cap_mu);
@@ -737,8 +752,10 @@ int run_round(sslic_server* s, std::vector<Slot*>& join, std::vector<Slot*>& act
         it = s->graphs.emplace(sig, ex).first;
         s->graph_captures += 1;
     }
-    if ((e = cudaGraphLaunch(it->second, s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "round launch", e);
-    s->graph_launches += 1;
+    if (!eager) {
+        if ((e = cudaGraphLaunch(it->second, s->cs)) != cudaSuccess) return server_fail(s, SSLIC_ECUDA, "round launch", e);
+        s->graph_launches += 1;
+    }
     if (!thr.empty()) {
         if ((e = cudaMemcpyAsync(H + L.res, s->tab_dev[par] + L.res, thr.size() * sizeof(double),
                                  cudaMemcpyDeviceToHost, s->cs)) != cudaSuccess)
@@ -836,9 +853,22 @@ void worker_main(sslic_server* s)
                 s->live.push_back(q);
             }
             s->max_seen = std::max(s->max_seen, (int)s->live.size());
+            // a request joins the round after its upload has landed, so that
+            // no round waits for another request's copy
+            bool uploading = false;
             for (Slot* q : s->live) {
-                if (q->state == kUploading) join.push_back(q);
-                else if (q->state == kActive) act.push_back(q);
+                if (q->state == kUploading) {
+                    const cudaError_t eq = cudaEventQuery(q->ev_up);
+                    if (eq == cudaSuccess) join.push_back(q);
+                    else if (eq == cudaErrorNotReady) uploading = true;
+                    else {
+                        lk.unlock();
+                        server_fail(s, SSLIC_ECUDA, "upload", eq);
+                        lk.lock();
+                    }
+                } else if (q->state == kActive) {
+                    act.push_back(q);
+                }
             }
             if (s->error != SSLIC_OK) {
                 for (Slot* q : s->live) { q->state = kFailed; q->status = s->error; }
@@ -848,7 +878,7 @@ void worker_main(sslic_server* s)
                 s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
                 continue;
             }
-            const bool finishing = std::any_of(s->live.begin(), s->live.end(), [](Slot* q) {
+            const bool finishing = uploading || std::any_of(s->live.begin(), s->live.end(), [](Slot* q) {
                 return q->state == kFinishing || q->state == kConnecting;
             });
             if (join.empty() && act.empty()) {
@@ -1068,6 +1098,7 @@ int sslic_server_stats_get(sslic_server* s, sslic_server_stats* out)
         out->mean_ms = sum / (double)v.size();
     }
     out->graph_launches = s->graph_launches;
+    out->eager_rounds = s->eager_rounds;
     out->graph_captures = s->graph_captures;
     out->status = s->error;
     return SSLIC_OK;

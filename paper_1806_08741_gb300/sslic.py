@@ -82,6 +82,7 @@ class _ServerStats(ctypes.Structure):
         ("mean_ms", ctypes.c_double),
         ("graph_launches", ctypes.c_int64),
         ("graph_captures", ctypes.c_int64),
+        ("eager_rounds", ctypes.c_int64),
     ]
 
 

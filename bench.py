@@ -47,10 +47,10 @@ UNIT = "Gvoxel-iter/s"
 # a changed kernel reports null until it is profiled again.
 TRAFFIC_BYTES = {
     # ncu capture of the tile kernel on the 67.1 M-voxel profiling workload
-    # (rgb3d_512x512x256): 205.9 MB read + 225.1 MB written per launch,
+    # (rgb3d_512x512x256): 206.2 MB read + 225.5 MB written per launch,
     # scaled by the voxel ratio (69.4x) to the 4.66 G-voxel launch
-    ("rgb3d_2048x1216x1871", "4854178835fabb824ded47f024aaac48adf2635bc0709e2613ef1b0262af0745"):
-        (205.899008e6 + 225.086464e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
+    ("rgb3d_2048x1216x1871", "bc81787ef88466b1964886573ecca2996ff0453c8da63d6ecedb5a6a778b0edb"):
+        (206.220032e6 + 225.464576e6) * (2048 * 1216 * 1871) / (512 * 512 * 256),
 }
 
 # thread instructions per voxel of the dominant kernel (ncu
@@ -58,7 +58,7 @@ TRAFFIC_BYTES = {
 # the SHA-256 of the kernel's source file like TRAFFIC_BYTES
 INST_PER_VOXEL = {
     # 493,095,965 warp instructions x 32 / 67,108,864 voxels (the capture above)
-    "4854178835fabb824ded47f024aaac48adf2635bc0709e2613ef1b0262af0745": 493095965 * 32 / (512 * 512 * 256),
+    "bc81787ef88466b1964886573ecca2996ff0453c8da63d6ecedb5a6a778b0edb": 493095965 * 32 / (512 * 512 * 256),
 }
 
 

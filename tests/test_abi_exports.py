@@ -142,3 +142,50 @@ def test_srgb_to_lab_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert f(0x10000, 0x10000 + 8, 4, None) == -1            # output starts inside the input
     assert f(0x10000 + 40, 0x10000, 4, None) == -1           # input starts inside the output
     assert f(0x10000, 0x10000, 1 << 62, None) == -1          # byte count overflows
+
+
+_CTYPES = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "float": ctypes.c_float, "double": ctypes.c_double}
+
+
+def _header_structs():
+    """Every `typedef struct { ... } name;` of include/*.h as [(field, ctype), ...]."""
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        for body, name in re.findall(r"typedef\s+struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+            fields = []
+            for decl in body.split(";"):
+                decl = decl.strip()
+                if not decl:
+                    continue
+                m = re.match(r"(\w+)\s+(.*)$", decl, flags=re.S)
+                ctype = _CTYPES[m.group(1)]
+                for part in m.group(2).split(","):
+                    part = part.strip()
+                    arr = re.match(r"(\w+)\s*\[\s*(\d+)\s*\]$", part)
+                    if arr:
+                        fields.append((arr.group(1), ctype * int(arr.group(2))))
+                    else:
+                        fields.append((part, ctype))
+            out[name] = fields
+    return out
+
+
+def test_binding_structs_match_header():
+    """The ctypes structures of the binding have the header's fields, types
+    and order, so the layouts agree (a field added on one side only fails)."""
+    from paper_1806_08741_gb300 import sslic as S
+    structs = _header_structs()
+    pairs = {"sslic_params": S._Params, "sslic_result": S._Result, "sslic_profile": S._Profile,
+             "sslic_server_stats": S._ServerStats}
+    assert set(pairs) <= set(structs)
+    for name, cls in pairs.items():
+        want = structs[name]
+        got = list(cls._fields_)
+        assert [f for f, _ in got] == [f for f, _ in want], name
+        for (f, a), (_, b) in zip(got, want):
+            assert ctypes.sizeof(a) == ctypes.sizeof(b) and ctypes.alignment(a) == ctypes.alignment(b), (name, f)
+            assert getattr(a, "_type_", a) == getattr(b, "_type_", b) or a == b, (name, f)

@@ -53,3 +53,24 @@ def test_gpu_generator_matches_cpu(spec):
     I.make_image_device(spec, out.data_ptr(), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy(), I.make_image(spec))
+
+
+def test_spec_struct_matches_header():
+    """The generator's ctypes spec has synth.h's fields, types and order."""
+    import ctypes
+    import os
+    import re
+    from paper_1806_08741_gb300 import inputs as Inp
+    ct = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64}
+    text = open(os.path.join(os.path.dirname(Inp.__file__), "synth.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    body = re.search(r"typedef\s+struct\s*\{(.*?)\}\s*synth_spec\s*;", text, flags=re.S).group(1)
+    want = []
+    for decl in filter(None, (d.strip() for d in body.split(";"))):
+        t, name = decl.split(None, 1)
+        arr = re.match(r"(\w+)\s*\[\s*(\d+)\s*\]$", name.strip())
+        want.append((arr.group(1), ct[t] * int(arr.group(2))) if arr else (name.strip(), ct[t]))
+    got = list(Inp._Spec._fields_)
+    assert [f for f, _ in got] == [f for f, _ in want]
+    for (f, a), (_, b) in zip(got, want):
+        assert ctypes.sizeof(a) == ctypes.sizeof(b) and getattr(a, "_type_", a) == getattr(b, "_type_", b), f

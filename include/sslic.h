@@ -121,7 +121,9 @@ SSLIC_API int sslic_run_from(sslic_ctx* c, const void* image_dev, const float* i
  * upload runs on a copy stream of the context in pieces -- first the planes
  * seeding reads, then slabs of 64 planes -- and seeding and each slab's first
  * assignment start as soon as their planes are in; the results are those of
- * the single copy (bit for bit for integer images). */
+ * the single copy (bit for bit for integer images).  With connectivity
+ * enforcement (2-D and 3-D), the final relabel pass runs in slabs of planes and
+ * each slab's labels are copied to labels_host as soon as it is relabelled. */
 SSLIC_API int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host,
                    float* centres_host, void* stream, sslic_result* out);
 

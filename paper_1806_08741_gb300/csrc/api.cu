@@ -657,8 +657,18 @@ int sslic_run_host(sslic_ctx* c, const void* image_host, int32_t* labels_host, f
         if ((rc = launch_seed(c, w.img_dev, st))) return rc;
     }
     sslic_result r;
-    if ((rc = run_loop(c, w.img_dev, w.lab_dev, centres_host ? w.cen_dev : nullptr, st, &r, first))) return rc;
-    if ((rc = cuda_check(c, cudaMemcpyAsync(labels_host, w.lab_dev, lab_bytes, cudaMemcpyDeviceToHost, st), "D2H")))
+    // with connectivity the relabel pass sends the labels itself, slab by slab
+    c->relabel_host = c->p.enforce_connectivity && (g.n == 2 || g.n == 3) ? labels_host : nullptr;
+    c->relabel_sent = 0;
+    rc = run_loop(c, w.img_dev, w.lab_dev, centres_host ? w.cen_dev : nullptr, st, &r, first);
+    c->relabel_host = nullptr;
+    if (c->relabel_sent) {
+        const int rs = cuda_check(c, cudaStreamSynchronize(w.down_stream), "sync");
+        if (!rc) rc = rs;
+    }
+    if (rc) return rc;
+    if (!c->relabel_sent &&
+        (rc = cuda_check(c, cudaMemcpyAsync(labels_host, w.lab_dev, lab_bytes, cudaMemcpyDeviceToHost, st), "D2H")))
         return rc;
     if (centres_host &&
         (rc = cuda_check(c, cudaMemcpyAsync(centres_host, w.cen_dev, cen_bytes, cudaMemcpyDeviceToHost, st), "D2H")))

@@ -1081,12 +1081,47 @@ static int connectivity_impl(sslic_ctx* c, const int32_t* labels_in, int32_t* la
     if ((rc = cuda_check(c, cudaGetLastError(), "ccl_faces_kernel"))) return rc;
     int64_t Mn = 0;
     if ((rc = conn_resolve_records<NDIM>(c, labels_in, rk, M, st, &Mn))) return rc;
-    conn_relabel_kernel<NDIM><<<t.ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,
-                                                                w.out_label, w.comp_label, labels_out,
-                                                                labels_in == labels_out ? 1 : 0, t.ntx, t.nty, t.ntz,
-                                                                0);
-    count_launch(c);
-    if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
+    if (c->relabel_host && (NDIM == 2 || NDIM == 3)) {
+        // slabs of tile planes along the last axis, each relabelled and then
+        // copied to the host on the download stream while the next is relabelled
+        if (!w.down_stream &&
+            (rc = cuda_check(c, cudaStreamCreateWithFlags(&w.down_stream, cudaStreamNonBlocking), "copy stream")))
+            return rc;
+        if (!w.slab_ev[4] &&
+            (rc = cuda_check(c, cudaEventCreateWithFlags(&w.slab_ev[4], cudaEventDisableTiming), "event")))
+            return rc;
+        const int64_t depth = NDIM == 3 ? CclCfg<3>::TZ : CclCfg<2>::TY;  // planes per layer of tiles
+        const int64_t layer = NDIM == 3 ? t.ntx * t.nty : t.ntx;         // tiles per layer
+        const int64_t nlayers = t.ntiles / layer;
+        const int64_t per = imax64(1, (nlayers + 7) / 8);                  // layers per slab: about 8 slabs
+        const int ax = NDIM - 1;
+        int64_t plane = 1;
+        for (int d = 0; d < ax; ++d) plane *= g.N[d];
+        for (int64_t l0 = 0; l0 < nlayers; l0 += per) {
+            const int64_t l1 = imin64(nlayers, l0 + per);
+            conn_relabel_kernel<NDIM><<<(unsigned)((l1 - l0) * layer), kCclThreads, 0, st>>>(
+                g, w.lid, w.tile_base, w.tile_cnt, w.gparent, w.out_label, w.comp_label, labels_out,
+                labels_in == labels_out ? 1 : 0, t.ntx, t.nty, t.ntz, l0 * layer);
+            count_launch(c);
+            if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
+            const int64_t p0 = l0 * depth, p1 = imin64(g.N[ax], l1 * depth);
+            if ((rc = cuda_check(c, cudaEventRecord(w.slab_ev[4], st), "event")) ||
+                (rc = cuda_check(c, cudaStreamWaitEvent(w.down_stream, w.slab_ev[4], 0), "wait")) ||
+                (rc = cuda_check(c, cudaMemcpyAsync(c->relabel_host + p0 * plane, labels_out + p0 * plane,
+                                                    (size_t)((p1 - p0) * plane) * sizeof(int32_t),
+                                                    cudaMemcpyDeviceToHost, w.down_stream),
+                                 "labels to host")))
+                return rc;
+        }
+        c->relabel_sent = 1;
+    } else {
+        conn_relabel_kernel<NDIM><<<t.ntiles, kCclThreads, 0, st>>>(g, w.lid, w.tile_base, w.tile_cnt, w.gparent,
+                                                                    w.out_label, w.comp_label, labels_out,
+                                                                    labels_in == labels_out ? 1 : 0, t.ntx, t.nty,
+                                                                    t.ntz, 0);
+        count_launch(c);
+        if ((rc = cuda_check(c, cudaGetLastError(), "conn_relabel_kernel"))) return rc;
+    }
     if ((rc = conn_status(c, st))) return rc;
     prof_end(c, pr, st);
     if (num_labels) *num_labels = g.K + Mn;

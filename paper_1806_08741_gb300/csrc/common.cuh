@@ -213,6 +213,11 @@ struct sslic_ctx {
     int loop_graph = 1;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t loop_exec = nullptr;
+    // sslic_run_host with connectivity: the relabel pass runs in slabs of
+    // tile planes and each slab's final labels go to this host buffer on the
+    // download stream right after it (relabel_sent records that it happened)
+    int32_t* relabel_host = nullptr;
+    int relabel_sent = 0;
     // tracing
     int prof_on = 0;
     int64_t launches = 0;
